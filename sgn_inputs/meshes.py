@@ -1,0 +1,217 @@
+"""Structured meshes and seeded problem instances.
+
+Workload shapes follow the paper's inverse elastic design example (Sec. 5,
+"Inverse Elastic Design"): an elastic body clamped on one side, loaded, whose
+equilibrium is pulled towards a target shape by per-element material
+parameters.  The paper's own meshes are not available; these generators stand
+in for them with structured triangle / tetrahedron grids.
+
+Only geometry, connectivity, boundary conditions, loads, targets and random
+draws live here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from itertools import permutations
+
+import numpy as np
+
+
+def grid2d(n: int):
+    """n x n nodes on [0,1]^2; every grid square is split along its
+    (i,j)->(i+1,j+1) diagonal into two counter-clockwise triangles.
+
+    Returns X (n*n, 2) float64 and tri (2*(n-1)^2, 3) int32.  Node (i, j)
+    (i along x, j along y) has index j*n + i.
+    """
+    if n < 2:
+        raise ValueError("grid2d needs n >= 2")
+    h = 1.0 / (n - 1)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    X = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    i, j = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    i = i.ravel(); j = j.ravel()
+    v00 = j * n + i
+    v10 = j * n + i + 1
+    v01 = (j + 1) * n + i
+    v11 = (j + 1) * n + i + 1
+    t1 = np.stack([v00, v10, v11], axis=1)
+    t2 = np.stack([v00, v11, v01], axis=1)
+    tri = np.empty((2 * len(v00), 3), dtype=np.int32)
+    tri[0::2] = t1
+    tri[1::2] = t2
+    return X, tri
+
+
+def kuhn3d(n: int):
+    """n^3 nodes on [0,1]^3; every cube is split into the six tetrahedra of
+    the Kuhn (Freudenthal) triangulation around its (0,0,0)->(1,1,1)
+    diagonal, the same split in every cube, so the mesh is conforming and
+    every interior node has 14 neighbours.  All tets are positively oriented.
+
+    Returns X (n^3, 3) float64 and tet (6*(n-1)^3, 4) int32.  Node (i,j,k)
+    has index (k*n + j)*n + i.
+    """
+    if n < 2:
+        raise ValueError("kuhn3d needs n >= 2")
+    h = 1.0 / (n - 1)
+    kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    X = np.stack([ii.ravel() * h, jj.ravel() * h, kk.ravel() * h], axis=1).astype(np.float64)
+    k, j, i = np.meshgrid(np.arange(n - 1), np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    base = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)  # cube corner
+    unit = np.eye(3, dtype=np.int64)
+    tets = []
+    for perm in permutations(range(3)):
+        c0 = base
+        c1 = c0 + unit[perm[0]]
+        c2 = c1 + unit[perm[1]]
+        c3 = c2 + unit[perm[2]]
+        # orientation sign of the path e_p0, e_p1, e_p2 is the permutation parity
+        inv = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b])
+        verts = [c0, c1, c2, c3] if inv % 2 == 0 else [c0, c2, c1, c3]
+        idx = [(v[:, 2] * n + v[:, 1]) * n + v[:, 0] for v in verts]
+        tets.append(np.stack(idx, axis=1))
+    tet = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return X, tet
+
+
+@dataclass
+class Problem:
+    """One equilibrium-constrained design instance.
+
+    dim         2 or 3
+    X           rest positions, (n_nodes, dim) float64
+    conn        element connectivity, (n_elem, dim+1) int32
+    fixed_node  1 where the node is Dirichlet-fixed (all its DOFs), uint8
+    fext        external nodal force, (n_nodes, dim) float64
+    track_dof   global DOF ids node*dim+comp of the tracked coordinates
+    target      target value of each tracked coordinate
+    weight      weight of each tracked coordinate (objective 1/2 sum w r^2)
+    alpha       Tikhonov weight on p (objective alpha/2 ||p||^2)
+    E0, nu      reference Young's modulus and Poisson ratio
+    p0          design vector: per-element log-modulus, E_e = E0 exp(p_e)
+    """
+    name: str
+    dim: int
+    X: np.ndarray
+    conn: np.ndarray
+    fixed_node: np.ndarray
+    fext: np.ndarray
+    track_dof: np.ndarray
+    target: np.ndarray
+    weight: np.ndarray
+    alpha: float
+    E0: float
+    nu: float
+    p0: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def n_elem(self) -> int:
+        return self.conn.shape[0]
+
+    @property
+    def n_free(self) -> int:
+        return int(np.count_nonzero(self.fixed_node == 0))
+
+
+def _lumped_body_load_2d(X, tri, load_per_area):
+    """Body load (0, -load_per_area) per unit area, lumped equally (area/3)
+    onto the three vertices of each triangle."""
+    a = X[tri[:, 1]] - X[tri[:, 0]]
+    b = X[tri[:, 2]] - X[tri[:, 0]]
+    area = 0.5 * np.abs(a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0])
+    f = np.zeros_like(X)
+    for v in range(3):
+        np.add.at(f[:, 1], tri[:, v], -load_per_area * area / 3.0)
+    return f
+
+
+def problem_2d(n: int = 21, seed: int = 0, E0: float = 1e4, nu: float = 0.3,
+               body_load: float = 10.0, shift=(0.0, -0.05), alpha: float = 1e-4,
+               p_sigma: float = 0.1, name: str | None = None) -> Problem:
+    """Plane-strain bar on the unit square: left edge clamped, uniform
+    downward body load, right-edge nodes tracked towards their rest position
+    shifted by `shift`; p drawn i.i.d. N(0, p_sigma^2) with `seed`."""
+    X, tri = grid2d(n)
+    fixed = (np.abs(X[:, 0]) < 1e-12).astype(np.uint8)
+    fext = _lumped_body_load_2d(X, tri, body_load)
+    right = np.nonzero(np.abs(X[:, 0] - 1.0) < 1e-12)[0]
+    track_dof = np.stack([right * 2, right * 2 + 1], axis=1).ravel().astype(np.int64)
+    target = (X[right] + np.asarray(shift, dtype=np.float64)[None, :]).ravel()
+    rng = np.random.default_rng(seed)
+    p0 = rng.normal(0.0, p_sigma, size=tri.shape[0]) if p_sigma > 0 else np.zeros(tri.shape[0])
+    return Problem(name or f"grid2d_{n}", 2, X, tri, fixed, fext, track_dof, target,
+                   np.ones(track_dof.shape[0]), alpha, E0, nu, p0.astype(np.float64),
+                   meta={"n": n, "seed": seed})
+
+
+def _smooth_target_height(XY, rng, n_waves=8, amplitude=0.02):
+    """Sum of `n_waves` sinusoids sin(2 pi (a X + b Y) + phi), a, b ~ U{1,2,3},
+    phi ~ U[0, 2 pi), scaled to max |.| = amplitude on the given points."""
+    a = rng.integers(1, 4, size=n_waves)
+    b = rng.integers(1, 4, size=n_waves)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n_waves)
+    h = np.zeros(XY.shape[0])
+    for k in range(n_waves):
+        h += np.sin(2.0 * np.pi * (a[k] * XY[:, 0] + b[k] * XY[:, 1]) + phi[k])
+    return amplitude * h / np.max(np.abs(h))
+
+
+def problem_3d(n: int = 40, seed: int = 0, E0: float = 1e4, nu: float = 0.3,
+               alpha: float = 1e-4, p_sigma: float = 0.0, load_scale: float = 1.0,
+               name: str | None = None) -> Problem:
+    """Kuhn-tet cube: bottom face (z=0) clamped, top-face nodes loaded by
+    -z * u_i * load_scale with u_i ~ U[0,1]; all three coordinates of the
+    top-face nodes tracked towards rest + (0, 0, g(X, Y)) with g a seeded
+    sum of 8 sinusoids of amplitude 0.02; p = 0 unless p_sigma > 0."""
+    X, tet = kuhn3d(n)
+    rng = np.random.default_rng(seed)
+    fixed = (np.abs(X[:, 2]) < 1e-12).astype(np.uint8)
+    top = np.nonzero(np.abs(X[:, 2] - 1.0) < 1e-12)[0]
+    fext = np.zeros_like(X)
+    fext[top, 2] = -load_scale * rng.uniform(0.0, 1.0, size=top.shape[0])
+    g = _smooth_target_height(X[top, :2], rng)
+    target = X[top].copy()
+    target[:, 2] += g
+    track_dof = np.stack([top * 3, top * 3 + 1, top * 3 + 2], axis=1).ravel().astype(np.int64)
+    p0 = rng.normal(0.0, p_sigma, size=tet.shape[0]) if p_sigma > 0 else np.zeros(tet.shape[0])
+    return Problem(name or f"kuhn3d_{n}", 3, X, tet, fixed, fext, track_dof, target.ravel(),
+                   np.ones(track_dof.shape[0]), alpha, E0, nu, p0.astype(np.float64),
+                   meta={"n": n, "seed": seed})
+
+
+def problem_tiny_2d(n: int = 4, seed: int = 1, p_sigma: float = 0.2) -> Problem:
+    """A few-element 2D instance for finite-difference and brute-force pins."""
+    return problem_2d(n=n, seed=seed, p_sigma=p_sigma, name=f"tiny2d_{n}")
+
+
+def problem_tiny_3d(n: int = 3, seed: int = 1, p_sigma: float = 0.2) -> Problem:
+    """A few-element 3D instance for finite-difference and brute-force pins."""
+    return problem_3d(n=n, seed=seed, p_sigma=p_sigma, name=f"tiny3d_{n}")
+
+
+PRESETS = {
+    # 21x21 plane-strain grid, 800 triangles, p ~ N(0, 0.1^2)
+    "grid2d_21": lambda seed=0: problem_2d(21, seed=seed),
+    # 40^3 Kuhn tets, 355,914 elements, p = 0
+    "kuhn3d_40": lambda seed=0: problem_3d(40, seed=seed),
+    # 80^3 Kuhn tets, 2,958,234 elements
+    "kuhn3d_80": lambda seed=0: problem_3d(80, seed=seed),
+}
+
+
+def make_preset(name: str, seed: int = 0) -> Problem:
+    if name in PRESETS:
+        return PRESETS[name](seed)
+    # "kuhn3d_<n>" / "grid2d_<n>" for any n
+    kind, _, size = name.rpartition("_")
+    if kind == "kuhn3d":
+        return problem_3d(int(size), seed=seed)
+    if kind == "grid2d":
+        return problem_2d(int(size), seed=seed)
+    raise KeyError(name)
