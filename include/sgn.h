@@ -1,0 +1,230 @@
+/*
+ * sgn.h -- C ABI of the GB300 Sparse Gauss-Newton (SGN) library (libsgn.so).
+ *
+ * Problem (Zehnder, Coros, Thomaszewski, "SGN: Sparse Gauss-Newton for
+ * Accelerated Sensitivity Analysis", ACM TOG 2021; Sec. 3, Eq. optProb):
+ *     min_{x,p} f(x, p)   s.t.   c(x, p) = 0,   n_c = n_x,  dc/dx full rank,
+ * where x are the free node positions of an elastic body, p one log-Young's
+ * modulus per element (E_e = E0 exp(p_e)), c = dPi/dx the equilibrium
+ * residual of the compressible neo-Hookean potential
+ *     Pi = sum_e vol_e Psi(F_e) - f_ext . x,
+ *     Psi(F) = mu/2 (tr F^T F - d) - mu ln J + lambda/2 (ln J)^2,
+ * and f the nonlinear least-squares objective (Eq. leastSquaresObjective)
+ *     f = 1/2 sum_t w_t (x_t - target_t)^2 + alpha/2 ||p||^2.
+ *
+ * The SGN step (Sec. 4, Eq. sparseSystemGN) solves the sparse saddle-point
+ * system
+ *     [ A   B^T  K^T  ] [dx]        with A = d2f/dx2 = diag(w) on tracked DOFs,
+ *     [ B   C    cp^T ] [dp] = rhs       B = d2f/dp dx = 0, C = alpha I,
+ *     [ K   cp   0    ] [dl]             K = dc/dx, cp = dc/dp,
+ * whose dp equals the dense Gauss-Newton step H_GN dp = -df/dp^T
+ * (Eq. newtonStep; Theorem 1 of Appendix A).
+ *
+ * Conventions for every call below
+ *  - Arrays named *_h are host memory, *_d device memory on the device that
+ *    was current at sgn_bind.  Device pointers are borrowed: the caller owns
+ *    them and keeps them alive until the stream has passed the call.
+ *  - Node-major layouts: positions, forces, dx and dlambda are [n_nodes][dim]
+ *    doubles (fixed nodes: their prescribed position / zero step); p and dp
+ *    are [n_elem] doubles.
+ *  - Device work is enqueued on the stream given to sgn_bind / sgn_set_stream
+ *    and is asynchronous unless a report is requested (reports synchronise).
+ *  - Every call returns an sgn_status; a device-detected error (an inverted
+ *    element, a non-finite value) is returned by the next call that
+ *    synchronises.  sgn_strerror() gives a message.  No call aborts.
+ *  - No call allocates device memory: the caller provides one device buffer
+ *    of sgn_device_bytes() bytes at sgn_bind and the library carves its
+ *    matrices, factors and workspaces out of it.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SGN_OK = 0,
+  SGN_EINVAL = 1,     /* bad argument (sizes, pointers, a partially fixed node ...) */
+  SGN_ECUDA = 2,      /* a CUDA runtime call failed */
+  SGN_ENOMEM = 3,     /* the bound device buffer is too small / host allocation failed */
+  SGN_EINVERTED = 4,  /* an element has det F <= 0 at the given positions */
+  SGN_ENEWTON = 5,    /* equilibrium Newton did not converge */
+  SGN_EPIVOT = 6,     /* a pivot had to be perturbed and refinement did not recover */
+  SGN_EREFINE = 7,    /* iterative refinement did not reach its tolerance */
+  SGN_ESTATE = 8,     /* call out of order (e.g. solve before factor) */
+  SGN_ENONFINITE = 9  /* a NaN or Inf reached a reduction */
+} sgn_status;
+
+/* Precisions of the numeric factorization (sgn_factor). */
+typedef enum {
+  SGN_FP64 = 0,       /* fronts, pivots and Schur updates in FP64 (DFMA) */
+  SGN_MIXED = 1       /* fronts in FP32 with FP32 Schur updates; FP64 pivot
+                         decisions, FP64 residuals and FP64 refinement */
+} sgn_precision;
+
+/* Right-hand side of Eq. sparseSystemGN (sgn_solve). */
+typedef enum {
+  SGN_RHS_KKT = 0,    /* [-f_x; -f_p; 0]: Newton-KKT form (Appendix A, Thm 2) */
+  SGN_RHS_PAPER = 1   /* [0; -g; 0] with g = df/dp given by the caller (Eq. sparseSystemGN) */
+} sgn_rhs_mode;
+
+/* Device storage classes requested at sgn_device_bytes / sgn_bind. */
+enum {
+  SGN_STORE_FP64 = 1,   /* FP64 saddle-point fronts (SGN_FP64 factor) */
+  SGN_STORE_MIXED = 2,  /* FP32 saddle-point fronts (SGN_MIXED factor) */
+  SGN_STORE_KFACT = 4   /* FP64 fronts of K alone (sgn_equilibrium, sgn_gradient) */
+};
+
+typedef struct sgn_ctx *sgn_t;
+
+/* Mesh and material (host arrays, copied by sgn_setup). */
+typedef struct {
+  int32_t dim;               /* 2 (plane-strain triangles) or 3 (tetrahedra) */
+  int32_t n_nodes;
+  int32_t n_elem;
+  const double *X_h;         /* [n_nodes][dim] rest positions */
+  const int32_t *conn_h;     /* [n_elem][dim+1] node ids, positively oriented */
+  const uint8_t *fixed_h;    /* [n_nodes]: 1 = Dirichlet-fixed node (all of its DOFs) */
+  double E0;                 /* reference Young's modulus, E_e = E0 exp(p_e) */
+  double nu;                 /* Poisson ratio */
+} sgn_mesh;
+
+/* Symbolic-phase options; zero-initialise for defaults. */
+typedef struct {
+  int32_t leaf_nodes;        /* nested dissection stops at <= leaf_nodes nodes (0: 16) */
+  int32_t panel;             /* pivot panel width, even, 8..64 (0: 32) */
+} sgn_setup_opts;
+
+/* Least-squares objective (host arrays, copied by sgn_set_objective). */
+typedef struct {
+  int32_t n_track;
+  const int64_t *track_dof_h; /* global DOF ids node*dim+comp; must be free DOFs */
+  const double *target_h;     /* [n_track] */
+  const double *weight_h;     /* [n_track] w_t > 0 */
+  double alpha;               /* Tikhonov weight, > 0 (C = alpha I) */
+} sgn_objective;
+
+typedef struct {
+  int64_t n_nodes, n_free, n_elem;
+  int64_t n_x, n_p, n_kkt;        /* n_kkt = 2 n_x + n_p */
+  int64_t nnz_kkt;                /* nonzeros of the full symmetric saddle-point matrix without A
+                                     (A adds one diagonal entry per tracked DOF) */
+  int64_t n_supernodes, n_levels;
+  int64_t max_front;              /* largest front order (reduced saddle-point system) */
+  int64_t nnz_factor;             /* entries of L incl. diagonal (reduced saddle-point system) */
+  double factor_flops;            /* flops of one numeric factorization (reduced system) */
+  double kfactor_flops;           /* flops of one factorization of K alone */
+  double setup_seconds;           /* wall time of the host symbolic phase */
+} sgn_info;
+
+typedef struct {
+  int64_t n_pos, n_neg, n_zero;   /* inertia of the saddle-point matrix (incl. p pivots) */
+  int64_t n_2x2;                  /* 2x2 Bunch-Kaufman pivots */
+  int64_t n_perturbed;            /* pivots replaced by the static-pivot threshold */
+  double seconds;                 /* device time of the factorization */
+} sgn_factor_report;
+
+typedef struct {
+  int32_t max_refine;             /* FP64 refinement steps (default 0 -> 2 FP64 / 30 mixed) */
+  double tol;                     /* stop at ||b - M z|| <= tol ||b|| (default 0 -> 1e-13) */
+} sgn_solve_opts;
+
+typedef struct {
+  int32_t refine_steps;           /* refinement steps taken */
+  double residual;                /* final ||b - M z|| / ||b|| in FP64 */
+  double seconds;
+} sgn_solve_report;
+
+typedef struct {
+  int32_t max_iter;               /* default 0 -> 50 */
+  double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10) */
+} sgn_newton_opts;
+
+typedef struct {
+  int32_t iters;
+  int32_t converged;
+  double residual;                /* final ||c|| / ||f_ext|| */
+  double initial_residual;
+  double seconds;
+} sgn_newton_report;
+
+/* ---- set-up -------------------------------------------------------------
+ * sgn_setup: host-only symbolic phase (Sec. 4: the sparsity of Eq.
+ * sparseSystemGN is fixed by the mesh): free-node numbering, nested
+ * dissection of the node graph, elimination tree, supernodes, front index
+ * maps, the fixed block pattern of K and its element slot map.  Copies the
+ * mesh.  EINVAL on bad sizes/indices; ENOMEM on host allocation failure. */
+sgn_status sgn_setup(const sgn_mesh *mesh, const sgn_setup_opts *opts, sgn_t *out);
+sgn_status sgn_get_info(sgn_t h, sgn_info *out);
+/* Bytes of device memory needed for the given SGN_STORE_* mask. */
+sgn_status sgn_device_bytes(sgn_t h, int32_t stores, size_t *bytes);
+/* Carves dev_buf (>= sgn_device_bytes, 256-byte aligned) and uploads the
+ * static symbolic data on `stream` (a cudaStream_t, NULL = default stream).
+ * The buffer stays owned by the caller and must outlive h's use. */
+sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *stream);
+sgn_status sgn_set_stream(sgn_t h, void *stream);
+/* Objective of Eq. leastSquaresObjective (tracked coordinates + Tikhonov). */
+sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj);
+void sgn_destroy(sgn_t h);
+const char *sgn_strerror(sgn_status s);
+
+/* ---- hot path ------------------------------------------------------------
+ * sgn_assemble: element kernels evaluate, at positions x_d and parameters
+ * p_d, the blocks of Eq. sparseSystemGN: K = dc/dx (Sec. 3.1), cp = dc/dp
+ * (Eq. dcdp; column e is element e's force since Psi is linear in E), and
+ * the Schur complement cp C^{-1} cp^T of the p block; all are scattered into
+ * the fixed pattern without atomics.  EINVERTED (at the next synchronising
+ * call) if det F <= 0 anywhere. */
+sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d);
+/* sgn_factor: numeric LDL^T of the assembled saddle-point matrix.  The p
+ * unknowns (C = alpha I diagonal) are eliminated first; the remaining
+ * (x, lambda) system is factored supernode by supernode (multifrontal) with
+ * Bunch-Kaufman 1x1/2x2 pivots restricted to each panel of the fully-summed
+ * block.  report may be NULL (no synchronisation). */
+sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *report);
+/* sgn_solve: (dx, dp, dl) of Eq. sparseSystemGN by forward, diagonal and
+ * backward substitution with the factor, followed by FP64 iterative
+ * refinement against the assembled matrix.  g_d = df/dp for SGN_RHS_PAPER
+ * (ignored otherwise).  Any of dx_d / dl_d may be NULL. */
+sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d,
+                     double *dp_d, double *dl_d, const sgn_solve_opts *opts,
+                     sgn_solve_report *report);
+/* sgn_step_host: sgn_assemble + sgn_factor + sgn_solve(SGN_RHS_KKT) on host
+ * buffers, including the host->device copy of x_h, p_h and the
+ * device->host copy of the step.  Synchronises. */
+sgn_status sgn_step_host(sgn_t h, sgn_precision prec, const double *x_h, const double *p_h,
+                         double *dx_h, double *dp_h, double *dl_h, sgn_solve_report *report);
+
+/* sgn_export_kkt: copies the assembled saddle-point matrix of Eq.
+ * sparseSystemGN (the last sgn_assemble) to host COO arrays, both triangles.
+ * Unknown ids: x_{node,a} -> node*dim + a, p_e -> n_nodes*dim + e,
+ * lambda_{node,a} -> n_nodes*dim + n_elem + node*dim + a (fixed nodes have no
+ * entries).  Call with rows_h == NULL to get the entry count in *nnz; else
+ * rows_h / cols_h / vals_h must hold *nnz entries.  Synchronises. */
+sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows_h, int64_t *cols_h, double *vals_h);
+
+/* ---- forward simulation and gradient -------------------------------------
+ * sgn_equilibrium: Newton's method on Pi(x; p) with a backtracking line
+ * search that keeps Pi monotone and rejects inverted elements (Sec. 5,
+ * "Computing Equilibrium States"); K is factored with the same multifrontal
+ * machinery (needs SGN_STORE_KFACT).  x_d: initial guess in, equilibrium
+ * out.  fext_d: [n_nodes][dim] external forces.  Synchronises. */
+sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, double *x_d,
+                           const sgn_newton_opts *opts, sgn_newton_report *report);
+/* sgn_gradient: total gradient df/dp = f_p + cp^T lambda_adj with the
+ * adjoint lambda_adj = -K^{-T} f_x (Eq. totalGradient and the remark after
+ * it: one linear solve, here with the K factor of sgn_factor_k).  Uses the
+ * blocks and f_x, f_p of the last sgn_assemble; ESTATE if K is not factored
+ * at that point.  g_d: [n_elem]. */
+sgn_status sgn_gradient(sgn_t h, double *g_d);
+/* sgn_factor_k: factor K alone at the assembled (x, p) (FP64). */
+sgn_status sgn_factor_k(sgn_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGN_H */

@@ -1,0 +1,130 @@
+"""ctypes binding of libsgn (include/sgn.h): argument marshalling only.
+
+Every step of the SGN path runs in the library's CUDA kernels; this module
+allocates the caller-owned device buffer with PyTorch, passes raw pointers
+and the current CUDA stream, and raises on non-OK status.  There is no CPU
+fallback: if libsgn.so is missing or cannot load, importing it fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsgn.so")
+
+# status codes (sgn_status)
+OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINITE = range(10)
+FP64, MIXED = 0, 1
+RHS_KKT, RHS_PAPER = 0, 1
+STORE_FP64, STORE_MIXED, STORE_KFACT = 1, 2, 4
+
+EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
+            "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
+            "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
+            "sgn_export_kkt"]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_nodes", C.c_int32), ("n_elem", C.c_int32),
+                ("X_h", C.POINTER(C.c_double)), ("conn_h", C.POINTER(C.c_int32)),
+                ("fixed_h", C.POINTER(C.c_uint8)), ("E0", C.c_double), ("nu", C.c_double)]
+
+
+class SetupOpts(C.Structure):
+    _fields_ = [("leaf_nodes", C.c_int32), ("panel", C.c_int32)]
+
+
+class Objective(C.Structure):
+    _fields_ = [("n_track", C.c_int32), ("track_dof_h", C.POINTER(C.c_int64)),
+                ("target_h", C.POINTER(C.c_double)), ("weight_h", C.POINTER(C.c_double)),
+                ("alpha", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_free", C.c_int64), ("n_elem", C.c_int64),
+                ("n_x", C.c_int64), ("n_p", C.c_int64), ("n_kkt", C.c_int64), ("nnz_kkt", C.c_int64),
+                ("n_supernodes", C.c_int64), ("n_levels", C.c_int64), ("max_front", C.c_int64),
+                ("nnz_factor", C.c_int64), ("factor_flops", C.c_double), ("kfactor_flops", C.c_double),
+                ("setup_seconds", C.c_double)]
+
+
+class FactorReport(C.Structure):
+    _fields_ = [("n_pos", C.c_int64), ("n_neg", C.c_int64), ("n_zero", C.c_int64),
+                ("n_2x2", C.c_int64), ("n_perturbed", C.c_int64), ("seconds", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_refine", C.c_int32), ("tol", C.c_double)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("refine_steps", C.c_int32), ("residual", C.c_double), ("seconds", C.c_double)]
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double)]
+
+
+class NewtonReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
+                ("initial_residual", C.c_double), ("seconds", C.c_double)]
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libsgn.so not built ({path}); run `python -m paper_2107_03285_gb300.build`")
+    lib = C.CDLL(path)
+    P, VP = C.POINTER, C.c_void_p
+    dp = P(C.c_double)
+    sig = {
+        "sgn_setup": (C.c_int, [P(Mesh), P(SetupOpts), P(VP)]),
+        "sgn_get_info": (C.c_int, [VP, P(Info)]),
+        "sgn_device_bytes": (C.c_int, [VP, C.c_int32, P(C.c_size_t)]),
+        "sgn_bind": (C.c_int, [VP, VP, C.c_size_t, C.c_int32, VP]),
+        "sgn_set_stream": (C.c_int, [VP, VP]),
+        "sgn_set_objective": (C.c_int, [VP, P(Objective)]),
+        "sgn_destroy": (None, [VP]),
+        "sgn_strerror": (C.c_char_p, [C.c_int]),
+        "sgn_assemble": (C.c_int, [VP, VP, VP]),
+        "sgn_factor": (C.c_int, [VP, C.c_int, P(FactorReport)]),
+        "sgn_solve": (C.c_int, [VP, C.c_int, VP, VP, VP, VP, P(SolveOpts), P(SolveReport)]),
+        "sgn_step_host": (C.c_int, [VP, C.c_int, dp, dp, dp, dp, dp, P(SolveReport)]),
+        "sgn_equilibrium": (C.c_int, [VP, VP, VP, VP, P(NewtonOpts), P(NewtonReport)]),
+        "sgn_gradient": (C.c_int, [VP, VP]),
+        "sgn_factor_k": (C.c_int, [VP]),
+        "sgn_export_kkt": (C.c_int, [VP, P(C.c_int64), P(C.c_int64), P(C.c_int64), dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+class SGNError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: status {code} ({msg})")
+        self.code = code
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(code, where):
+    if code != OK:
+        raise SGNError(code, where, lib().sgn_strerror(code).decode())
+    return code
+
+
+def _dptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))

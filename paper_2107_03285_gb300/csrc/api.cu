@@ -1,0 +1,624 @@
+// C ABI of libsgn: set-up, device binding, and the orchestration of the hot
+// path (assemble -> factor -> solve + FP64 refinement), forward simulation and
+// the adjoint gradient.  All device memory comes from the caller's buffer.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace sgn;
+
+struct sgn_ctx : public Ctx {};
+
+namespace {
+
+thread_local std::string g_err;
+
+#define CUDA_TRY(h, call)                                                   \
+  do {                                                                      \
+    cudaError_t _e = (call);                                                \
+    if (_e != cudaSuccess) {                                                \
+      (h)->last_error = std::string(#call) + ": " + cudaGetErrorString(_e); \
+      return SGN_ECUDA;                                                     \
+    }                                                                       \
+  } while (0)
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(char *b) : base(b) {}
+  template <typename T>
+  T *take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += std::max<size_t>(n, 1) * sizeof(T);
+    return p;
+  }
+};
+
+struct Upload {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+
+void store_offsets(Ctx &c, Store &s, int dpn) {
+  const int nb = c.S.opts.panel;
+  s.dpn = dpn;
+  const int n_sn = (int)c.S.sn.size();
+  s.h_front_off.assign(n_sn, 0); s.h_w_off.assign(n_sn, 0);
+  s.h_rhs_off.assign(n_sn, 0); s.h_piv_off.assign(n_sn, 0);
+  int64_t fo = 0, wo = 0, ro = 0, po = 0;
+  for (int i = 0; i < n_sn; ++i) {
+    int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
+    s.h_front_off[i] = fo; fo += f * f;
+    s.h_w_off[i] = wo; wo += f * nb;
+    s.h_rhs_off[i] = ro; ro += f;
+    s.h_piv_off[i] = po; po += ns;
+  }
+  s.front_elems = fo; s.w_elems = wo; s.rhs_elems = ro; s.piv_elems = po;
+}
+
+// lays out (base == nullptr: only measures) every device array
+size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
+  Carver cv(base);
+  Symbolic &S = c.S;
+  const int d = S.dim, nv = d + 1;
+  const int64_t ne = S.n_elem, nf = S.n_free, nx = nf * d;
+  auto st_up = [&](auto *&dst, const auto &vec) {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    T *p = cv.take<T>(vec.size());
+    dst = p;
+    if (up && p) up->push_back({p, vec.data(), vec.size() * sizeof(T)});
+  };
+  DevSym &ds = c.ds;
+  ds.dim = d; ds.n_nodes = S.n_nodes; ds.n_elem = S.n_elem; ds.n_free = S.n_free;
+  ds.n_sn = (int)S.sn.size(); ds.panel = S.opts.panel;
+  // static symbolic data
+  static thread_local std::vector<int32_t> sn_first, sn_nown, sn_nstruct, sn_child_off, sn_nchild, lvl_fronts,
+      item_sn, item_P;
+  static thread_local std::vector<int64_t> sn_struct_off;
+  sn_first.clear(); sn_nown.clear(); sn_nstruct.clear(); sn_child_off.clear(); sn_nchild.clear();
+  sn_struct_off.clear(); lvl_fronts.clear(); item_sn.clear(); item_P.clear();
+  for (auto &s : S.sn) {
+    sn_first.push_back(s.first); sn_nown.push_back(s.nown); sn_nstruct.push_back(s.nstruct);
+    sn_child_off.push_back(s.child_off); sn_nchild.push_back(s.nchild); sn_struct_off.push_back(s.struct_off);
+  }
+  c.h_lvl_ptr.assign(1, 0); c.h_item_ptr.assign(1, 0);
+  for (int L = 0; L < S.n_levels; ++L) {
+    for (int s : S.level_fronts[L]) {
+      lvl_fronts.push_back(s);
+      for (int P = 0; P < S.sn[s].fnodes(); ++P) { item_sn.push_back(s); item_P.push_back(P); }
+    }
+    c.h_lvl_ptr.push_back((int64_t)lvl_fronts.size());
+    c.h_item_ptr.push_back((int64_t)item_sn.size());
+  }
+  const int32_t *cp;
+  const double *cd;
+  const int64_t *c64;
+#define UP32(field, vec) do { int32_t *p_; st_up(p_, vec); ds.field = p_; } while (0)
+#define UPD(field, vec) do { double *p_; st_up(p_, vec); ds.field = p_; } while (0)
+#define UP64(field, vec) do { int64_t *p_; st_up(p_, vec); ds.field = p_; } while (0)
+  (void)cp; (void)cd; (void)c64;
+  UP32(elem_node, S.elem_node); UP32(elem_rank, S.elem_rank);
+  UPD(elem_B, S.elem_B); UPD(elem_vol, S.elem_vol);
+  UP32(node_rank, S.node_rank); UP32(rank_node, S.rank_node);
+  UP32(bsr_ptr, S.bsr_ptr); UP32(bsr_col, S.bsr_col); UP32(bsr_orig_pos, S.bsr_orig_pos);
+  UP32(up_slot, S.up_slot); UP32(up_slot_t, S.up_slot_t); UP32(up_ptr, S.up_ptr); UP32(up_contrib, S.up_contrib);
+  UP32(inc_ptr, S.inc_ptr); UP32(inc, S.inc);
+  UP32(sn_first, sn_first); UP32(sn_nown, sn_nown); UP32(sn_nstruct, sn_nstruct);
+  UP32(sn_child_off, sn_child_off); UP32(sn_nchild, sn_nchild); UP64(sn_struct_off, sn_struct_off);
+  UP32(struct_ranks, S.struct_ranks); UP32(relpos, S.relpos); UP32(children, S.children);
+  UP64(cmap_off, S.cmap_off); UP32(cmap, S.cmap);
+  UP32(lvl_fronts, lvl_fronts); UP32(item_sn, item_sn); UP32(item_P, item_P);
+#undef UP32
+#undef UPD
+#undef UP64
+  // dynamic arrays
+  c.n_state = 3 + nv * d;
+  c.st = cv.take<double>((size_t)c.n_state * ne);
+  c.cpv = cv.take<double>((size_t)nv * d * ne);
+  c.Kv = cv.take<double>(S.bsr_col.size() * d * d);
+  c.Gv = cv.take<double>(S.bsr_col.size() * d * d);
+  c.wA = cv.take<double>(nx); c.tgt = cv.take<double>(nx);
+  c.fx = cv.take<double>(nx); c.fp = cv.take<double>(ne); c.xr = cv.take<double>(nx);
+  c.bx = cv.take<double>(nx); c.bp = cv.take<double>(ne); c.bl = cv.take<double>(nx);
+  c.zx = cv.take<double>(nx); c.zp = cv.take<double>(ne); c.zl = cv.take<double>(nx);
+  c.rx = cv.take<double>(nx); c.rp = cv.take<double>(ne); c.rl = cv.take<double>(nx);
+  c.red = cv.take<double>(2 * nx * 2);  // reduced rhs and solution
+  c.n_partial = 1024;
+  c.partial = cv.take<double>(c.n_partial);
+  c.status = cv.take<int>(4);
+  c.counters = cv.take<int64_t>(8);
+  const size_t nn = (size_t)S.n_nodes * d;
+  c.eq = cv.take<double>(4 * nx);
+  c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx);
+  c.hx = cv.take<double>(nn); c.hdx = cv.take<double>(nn); c.hdl = cv.take<double>(nn);
+  c.hp = cv.take<double>(ne); c.hdp = cv.take<double>(ne);
+  auto store = [&](Store &s, bool on, int dpn, bool kkt, bool fp32) {
+    s.enabled = on;
+    s.kkt = kkt; s.fp32 = fp32;
+    store_offsets(c, s, dpn);
+    if (!on) return;
+    size_t es = fp32 ? 4 : 8;
+    s.F = cv.take<char>((size_t)s.front_elems * es);
+    s.W = cv.take<char>((size_t)s.w_elems * es);
+    s.rhs = cv.take<double>(s.rhs_elems);
+    s.piv_type = cv.take<int32_t>(s.piv_elems); s.piv_perm = cv.take<int32_t>(s.piv_elems);
+    s.D0 = cv.take<double>(s.piv_elems); s.D1 = cv.take<double>(s.piv_elems);
+    int64_t *p;
+    st_up(p, s.h_front_off); s.front_off = p;
+    st_up(p, s.h_w_off); s.w_off = p;
+    st_up(p, s.h_rhs_off); s.rhs_off = p;
+    st_up(p, s.h_piv_off); s.piv_off = p;
+  };
+  store(c.kkt64, (stores & SGN_STORE_FP64) != 0, 2 * d, true, false);
+  store(c.kkt32, (stores & SGN_STORE_MIXED) != 0, 2 * d, true, true);
+  store(c.kf, (stores & SGN_STORE_KFACT) != 0, d, false, false);
+  return cv.off + 256;
+}
+
+sgn_status check_status(sgn_ctx *h) {
+  int st = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (st) {
+    CUDA_TRY(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    if (st & DEV_INVERTED) { h->last_error = "inverted element (det F <= 0)"; return SGN_EINVERTED; }
+    h->last_error = "non-finite value in element evaluation";
+    return SGN_ENONFINITE;
+  }
+  return SGN_OK;
+}
+
+sgn_status launch_check(sgn_ctx *h) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    h->last_error = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return SGN_ECUDA;
+  }
+  return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sgn_strerror(sgn_status s) {
+  switch (s) {
+    case SGN_OK: return "ok";
+    case SGN_EINVAL: return g_err.empty() ? "invalid argument" : g_err.c_str();
+    case SGN_ECUDA: return g_err.empty() ? "CUDA error" : g_err.c_str();
+    case SGN_ENOMEM: return "device buffer too small or host allocation failed";
+    case SGN_EINVERTED: return "inverted element (det F <= 0)";
+    case SGN_ENEWTON: return "equilibrium Newton did not converge";
+    case SGN_EPIVOT: return "perturbed pivot not recovered by refinement";
+    case SGN_EREFINE: return "iterative refinement did not reach its tolerance";
+    case SGN_ESTATE: return "call out of order";
+    case SGN_ENONFINITE: return "non-finite value";
+  }
+  return "unknown status";
+}
+
+sgn_status sgn_setup(const sgn_mesh *mesh, const sgn_setup_opts *opts, sgn_t *out) {
+  if (!mesh || !out) return SGN_EINVAL;
+  *out = nullptr;
+  sgn_ctx *h = new (std::nothrow) sgn_ctx();
+  if (!h) return SGN_ENOMEM;
+  SymbolicOptions so;
+  if (opts) { so.leaf_nodes = opts->leaf_nodes; so.panel = opts->panel; }
+  if (so.leaf_nodes <= 0) so.leaf_nodes = 16;
+  if (so.panel <= 0) so.panel = 32;
+  if (!(mesh->nu > -1.0 && mesh->nu < 0.5) || !(mesh->E0 > 0.0)) {
+    g_err = "material: need E0 > 0 and -1 < nu < 0.5";
+    delete h;
+    return SGN_EINVAL;
+  }
+  std::string err;
+  try {
+    err = analyze(mesh->dim, mesh->n_nodes, mesh->n_elem, mesh->X_h, mesh->conn_h, mesh->fixed_h, so, h->S);
+  } catch (const std::bad_alloc &) {
+    delete h;
+    return SGN_ENOMEM;
+  }
+  if (!err.empty()) {
+    g_err = err;
+    delete h;
+    return SGN_EINVAL;
+  }
+  h->E0 = mesh->E0; h->nu = mesh->nu;
+  *out = h;
+  return SGN_OK;
+}
+
+sgn_status sgn_get_info(sgn_t h, sgn_info *o) {
+  if (!h || !o) return SGN_EINVAL;
+  const Symbolic &S = h->S;
+  o->n_nodes = S.n_nodes; o->n_free = S.n_free; o->n_elem = S.n_elem;
+  o->n_x = (int64_t)S.n_free * S.dim; o->n_p = S.n_elem; o->n_kkt = 2 * o->n_x + o->n_p;
+  // full symmetric saddle point without A: 2 (K) + 2 (cp) + C diag
+  int64_t nnzK = (int64_t)S.bsr_col.size() * S.dim * S.dim;
+  int64_t nnzcp = 0;
+  for (int64_t i = 0; i < (int64_t)S.elem_rank.size(); ++i) nnzcp += S.elem_rank[i] >= 0 ? S.dim : 0;
+  o->nnz_kkt = 2 * nnzK + 2 * nnzcp + o->n_p;
+  o->n_supernodes = (int64_t)S.sn.size(); o->n_levels = S.n_levels;
+  o->max_front = S.max_front_nodes * 2 * S.dim;
+  o->nnz_factor = S.nnz_factor_kkt;
+  o->factor_flops = S.flops_kkt; o->kfactor_flops = S.flops_k;
+  o->setup_seconds = S.seconds;
+  return SGN_OK;
+}
+
+sgn_status sgn_device_bytes(sgn_t h, int32_t stores, size_t *bytes) {
+  if (!h || !bytes) return SGN_EINVAL;
+  *bytes = carve(*h, nullptr, stores, nullptr);
+  return SGN_OK;
+}
+
+sgn_status sgn_set_stream(sgn_t h, void *stream) {
+  if (!h) return SGN_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return SGN_OK;
+}
+
+sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *stream) {
+  if (!h || !dev_buf) return SGN_EINVAL;
+  if (((uintptr_t)dev_buf & 255) != 0) { g_err = "device buffer must be 256-byte aligned"; return SGN_EINVAL; }
+  size_t need = carve(*h, nullptr, stores, nullptr);
+  if (bytes < need) return SGN_ENOMEM;
+  h->stream = (cudaStream_t)stream;
+  CUDA_TRY(h, cudaGetDevice(&h->device));
+  std::vector<Upload> ups;
+  h->base = (char *)dev_buf;
+  h->bytes = bytes;
+  carve(*h, h->base, stores, &ups);
+  for (auto &u : ups) CUDA_TRY(h, cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
+  // uploads read host vectors owned by h->S or by the carve's thread-local
+  // staging; wait for them before those can change
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->stores = stores;
+  h->bound = true;
+  h->assembled = false;
+  h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
+  return SGN_OK;
+}
+
+sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
+  if (!h || !obj || !h->bound) return h ? (h->bound ? SGN_EINVAL : SGN_ESTATE) : SGN_EINVAL;
+  if (!(obj->alpha > 0.0) || obj->n_track < 0) { g_err = "objective: need alpha > 0"; return SGN_EINVAL; }
+  const Symbolic &S = h->S;
+  const int d = S.dim;
+  std::vector<double> w((size_t)S.n_free * d, 0.0), t((size_t)S.n_free * d, 0.0);
+  for (int i = 0; i < obj->n_track; ++i) {
+    int64_t g = obj->track_dof_h[i];
+    if (g < 0 || g >= (int64_t)S.n_nodes * d) { g_err = "tracked DOF out of range"; return SGN_EINVAL; }
+    int r = S.node_rank[g / d];
+    if (r < 0) { g_err = "tracked DOF is fixed"; return SGN_EINVAL; }
+    if (!(obj->weight_h[i] >= 0.0)) { g_err = "negative weight"; return SGN_EINVAL; }
+    int64_t rd = (int64_t)r * d + g % d;
+    // repeated DOFs add up: sum_t w_t (x - target_t)^2 = (sum w)(x - wavg)^2 + const
+    double wn = w[rd] + obj->weight_h[i];
+    t[rd] = wn > 0 ? (w[rd] * t[rd] + obj->weight_h[i] * obj->target_h[i]) / wn : 0.0;
+    w[rd] = wn;
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->wA, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->tgt, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->alpha = obj->alpha;
+  h->have_objective = true;
+  h->assembled = false;
+  return SGN_OK;
+}
+
+void sgn_destroy(sgn_t h) { delete h; }
+
+sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d) {
+  if (!h || !x_d || !p_d) return SGN_EINVAL;
+  if (!h->bound || !h->have_objective) return SGN_ESTATE;
+  launch_elem_state(*h, x_d, p_d);
+  launch_slot_gather(*h, true);
+  launch_objective_terms(*h, x_d, p_d);
+  h->assembled = true;
+  h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
+  return launch_check(h);
+}
+
+sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *rep) {
+  if (!h) return SGN_EINVAL;
+  if (!h->assembled) return SGN_ESTATE;
+  Store &st = prec == SGN_MIXED ? h->kkt32 : h->kkt64;
+  if (!st.enabled) { g_err = "store for this precision was not bound"; return SGN_ESTATE; }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rep) {
+    CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
+    CUDA_TRY(h, cudaEventRecord(e0, h->stream));
+  }
+  factor_store(*h, st);
+  h->active = &st;
+  sgn_status s = launch_check(h);
+  if (s != SGN_OK) return s;
+  if (rep) {
+    CUDA_TRY(h, cudaEventRecord(e1, h->stream));
+    pivot_counts(*h, st);
+    int64_t ctr[8];
+    CUDA_TRY(h, cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    rep->n_perturbed = ctr[0]; rep->n_2x2 = ctr[1];
+    rep->n_pos = ctr[2] + h->S.n_elem;  // p pivots: C = alpha I > 0
+    rep->n_neg = ctr[3]; rep->n_zero = ctr[4];
+    rep->seconds = ms * 1e-3;
+    s = check_status(h);
+    if (s != SGN_OK) return s;
+  }
+  return SGN_OK;
+}
+
+sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d, double *dp_d, double *dl_d,
+                     const sgn_solve_opts *opts, sgn_solve_report *rep) {
+  if (!h || !dp_d) return SGN_EINVAL;
+  if (mode == SGN_RHS_PAPER && !g_d) return SGN_EINVAL;
+  Store *stp = (h->active && h->active->factored) ? h->active : nullptr;
+  if (!stp) return SGN_ESTATE;
+  Store &st = *stp;
+  Ctx &c = *h;
+  const int64_t nx = (int64_t)c.S.n_free * c.S.dim, ne = c.S.n_elem;
+  int max_refine = opts && opts->max_refine > 0 ? opts->max_refine : (st.fp32 ? 30 : 2);
+  double tol = opts && opts->tol > 0 ? opts->tol : 1e-13;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rep) {
+    CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
+    CUDA_TRY(h, cudaEventRecord(e0, c.stream));
+  }
+  // right-hand side b = [b_x; b_p; b_l]
+  if (mode == SGN_RHS_KKT) {
+    CUDA_TRY(h, cudaMemsetAsync(c.bx, 0, nx * sizeof(double), c.stream));
+    launch_axpy(c, c.bx, c.fx, -1.0, nx);
+    CUDA_TRY(h, cudaMemsetAsync(c.bp, 0, ne * sizeof(double), c.stream));
+    launch_axpy(c, c.bp, c.fp, -1.0, ne);
+  } else {
+    CUDA_TRY(h, cudaMemsetAsync(c.bx, 0, nx * sizeof(double), c.stream));
+    CUDA_TRY(h, cudaMemsetAsync(c.bp, 0, ne * sizeof(double), c.stream));
+    launch_axpy(c, c.bp, g_d, -1.0, ne);
+  }
+  CUDA_TRY(h, cudaMemsetAsync(c.bl, 0, nx * sizeof(double), c.stream));
+  double *red_b = c.red, *red_x = c.red + 2 * nx;
+  // z = M^{-1} b
+  launch_reduce_rhs(c, c.bx, c.bp, c.bl, red_b, 2 * c.S.dim);
+  solve_store(c, st, red_b, red_x);
+  launch_recover(c, red_x, c.bp, c.zx, c.zp, c.zl);
+  double bn = std::sqrt(device_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx));
+  double rn = 0.0;
+  int steps = 0;
+  for (;;) {
+    launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
+    rn = std::sqrt(device_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx));
+    if (!(rn == rn)) { h->last_error = "non-finite residual"; return SGN_ENONFINITE; }
+    if (rn <= tol * bn || steps >= max_refine) break;
+    launch_reduce_rhs(c, c.rx, c.rp, c.rl, red_b, 2 * c.S.dim);
+    solve_store(c, st, red_b, red_x);
+    // d = M^{-1} r, recovered into (rx, rp, rl) scratch then added
+    launch_recover(c, red_x, c.rp, c.rx, c.rp, c.rl);
+    launch_axpy(c, c.zx, c.rx, 1.0, nx);
+    launch_axpy(c, c.zp, c.rp, 1.0, ne);
+    launch_axpy(c, c.zl, c.rl, 1.0, nx);
+    ++steps;
+  }
+  if (dx_d) launch_to_nodes_plain(c, c.zx, dx_d);
+  if (dl_d) launch_to_nodes_plain(c, c.zl, dl_d);
+  CUDA_TRY(h, cudaMemcpyAsync(dp_d, c.zp, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  sgn_status s = launch_check(h);
+  if (s != SGN_OK) return s;
+  if (rep) {
+    CUDA_TRY(h, cudaEventRecord(e1, c.stream));
+    CUDA_TRY(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    rep->refine_steps = steps;
+    rep->residual = bn > 0 ? rn / bn : rn;
+    rep->seconds = ms * 1e-3;
+  }
+  if (bn > 0 && rn > 1e3 * tol * bn && st.fp32) return SGN_EREFINE;
+  return SGN_OK;
+}
+
+sgn_status sgn_step_host(sgn_t h, sgn_precision prec, const double *x_h, const double *p_h, double *dx_h,
+                         double *dp_h, double *dl_h, sgn_solve_report *rep) {
+  if (!h || !x_h || !p_h || !dp_h) return SGN_EINVAL;
+  if (!h->bound) return SGN_ESTATE;
+  Ctx &c = *h;
+  const int64_t nn = (int64_t)c.S.n_nodes * c.S.dim, ne = c.S.n_elem;
+  double *xd = c.hx, *dxd = c.hdx, *dld = c.hdl, *pd = c.hp, *dpd = c.hdp;
+  CUDA_TRY(h, cudaMemcpyAsync(xd, x_h, nn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(h, cudaMemcpyAsync(pd, p_h, ne * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  sgn_status s = sgn_assemble(h, xd, pd);
+  if (s != SGN_OK) return s;
+  s = sgn_factor(h, prec, nullptr);
+  if (s != SGN_OK) return s;
+  s = sgn_solve(h, SGN_RHS_KKT, nullptr, dxd, dpd, dld, nullptr, rep);
+  if (s != SGN_OK && s != SGN_EREFINE) return s;
+  sgn_status s2 = s;
+  CUDA_TRY(h, cudaMemcpyAsync(dp_h, dpd, ne * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (dx_h) CUDA_TRY(h, cudaMemcpyAsync(dx_h, dxd, nn * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (dl_h) CUDA_TRY(h, cudaMemcpyAsync(dl_h, dld, nn * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(h, cudaStreamSynchronize(c.stream));
+  s = check_status(h);
+  return s != SGN_OK ? s : s2;
+}
+
+sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows, int64_t *cols, double *vals) {
+  if (!h || !nnz) return SGN_EINVAL;
+  if (!h->assembled) return SGN_ESTATE;
+  const Symbolic &S = h->S;
+  const int d = S.dim, nv = d + 1;
+  const int64_t ne = S.n_elem, nx = (int64_t)S.n_free * d, nnd = (int64_t)S.n_nodes * d;
+  std::vector<double> wA(nx), Kv(S.bsr_col.size() * d * d), cpv((size_t)nv * d * ne);
+  CUDA_TRY(h, cudaMemcpyAsync(wA.data(), h->wA, wA.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(Kv.data(), h->Kv, Kv.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(cpv.data(), h->cpv, cpv.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int64_t n = 0;
+  auto put = [&](int64_t r, int64_t c, double v) {
+    if (rows) { rows[n] = r; cols[n] = c; vals[n] = v; }
+    ++n;
+  };
+  auto xid = [&](int rank, int a) { return (int64_t)S.rank_node[rank] * d + a; };
+  const int64_t pbase = nnd, lbase = nnd + ne;
+  for (int r = 0; r < S.n_free; ++r)
+    for (int a = 0; a < d; ++a)
+      if (wA[(int64_t)r * d + a] != 0.0) put(xid(r, a), xid(r, a), wA[(int64_t)r * d + a]);
+  for (int r = 0; r < S.n_free; ++r)
+    for (int k = S.bsr_ptr[r]; k < S.bsr_ptr[r + 1]; ++k) {
+      int c = S.bsr_col[k];
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+          double v = Kv[(size_t)k * d * d + a * d + b];
+          put(xid(r, a), lbase + xid(c, b), v);  // (x, lambda) block: K^T
+          put(lbase + xid(r, a), xid(c, b), v);  // (lambda, x) block: K
+        }
+    }
+  for (int64_t e = 0; e < ne; ++e) {
+    put(pbase + e, pbase + e, h->alpha);
+    for (int a = 0; a < nv; ++a) {
+      int r = S.elem_rank[(size_t)a * ne + e];
+      if (r < 0) continue;
+      for (int i = 0; i < d; ++i) {
+        double v = cpv[(size_t)(a * d + i) * ne + e];
+        put(lbase + xid(r, i), pbase + e, v);
+        put(pbase + e, lbase + xid(r, i), v);
+      }
+    }
+  }
+  if (rows && n != *nnz) return SGN_EINVAL;
+  *nnz = n;
+  return SGN_OK;
+}
+
+sgn_status sgn_factor_k(sgn_t h) {
+  if (!h) return SGN_EINVAL;
+  if (!h->assembled) return SGN_ESTATE;
+  if (!h->kf.enabled) { g_err = "K store was not bound"; return SGN_ESTATE; }
+  factor_store(*h, h->kf);
+  return launch_check(h);
+}
+
+sgn_status sgn_gradient(sgn_t h, double *g_d) {
+  if (!h || !g_d) return SGN_EINVAL;
+  if (!h->assembled || !h->kf.factored) return SGN_ESTATE;
+  Ctx &c = *h;
+  const int64_t nx = (int64_t)c.S.n_free * c.S.dim;
+  double *b = c.eq, *lam = c.eq + nx;
+  CUDA_TRY(h, cudaMemsetAsync(b, 0, nx * sizeof(double), c.stream));
+  launch_axpy(c, b, c.fx, -1.0, nx);
+  solve_store(c, c.kf, b, lam);  // lam = -K^{-1} f_x (K symmetric)
+  launch_gradient_finish(c, lam, g_d);
+  return launch_check(h);
+}
+
+sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, double *x_d,
+                           const sgn_newton_opts *opts, sgn_newton_report *rep) {
+  if (!h || !p_d || !fext_d || !x_d) return SGN_EINVAL;
+  if (!h->bound || !h->kf.enabled) return SGN_ESTATE;
+  Ctx &c = *h;
+  auto t0 = std::chrono::steady_clock::now();
+  const int d = c.S.dim;
+  const int64_t nx = (int64_t)c.S.n_free * d, nn = (int64_t)c.S.n_nodes * d;
+  const int max_iter = opts && opts->max_iter > 0 ? opts->max_iter : 50;
+  const double tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
+  double *fr = c.eq, *cr = fr + nx, *dxr = cr + nx, *tmp = dxr + nx;
+  double *xsave = c.xsave, *xr_tmp = c.xrt;
+  launch_from_nodes(c, fext_d, fr);
+  const double fnorm = std::sqrt(device_sumsq3(c, fr, nx, nullptr, 0, nullptr, 0));
+  const double scale = fnorm > 0 ? fnorm : 1.0;
+  auto potential = [&](const double *x, bool *valid) -> double {
+    int nbk = energy_blocks(c);
+    launch_energy_partials(c, x, p_d, c.partial, nbk);
+    std::vector<double> hp(nbk);
+    cudaMemcpyAsync(hp.data(), c.partial, nbk * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    double e = 0.0;
+    for (double v : hp) e += v;
+    *valid = std::isfinite(e);
+    launch_from_nodes(c, x, xr_tmp);
+    double w = device_dot(c, fr, xr_tmp, nx);
+    return e - w;
+  };
+  auto residual = [&](const double *x) -> double {
+    launch_elem_state(c, x, p_d);
+    launch_internal_force(c, cr);
+    launch_axpy(c, cr, fr, -1.0, nx);
+    return std::sqrt(device_sumsq3(c, cr, nx, nullptr, 0, nullptr, 0));
+  };
+  bool valid = true;
+  double Pi = potential(x_d, &valid);
+  if (!valid) { c.last_error = "initial guess has an inverted element"; return SGN_EINVERTED; }
+  double cn = residual(x_d);
+  double init = cn / scale;
+  int it = 0;
+  bool conv = false;
+  for (;; ++it) {
+    if (cn <= tol * scale) { conv = true; break; }
+    if (it >= max_iter) break;
+    // Newton direction: K dx = -c
+    launch_slot_gather(c, false);
+    c.assembled = true;
+    factor_store(c, c.kf);
+    CUDA_TRY(h, cudaMemsetAsync(tmp, 0, nx * sizeof(double), c.stream));
+    launch_axpy(c, tmp, cr, -1.0, nx);
+    solve_store(c, c.kf, tmp, dxr);
+    double slope = device_dot(c, cr, dxr, nx);
+    CUDA_TRY(h, cudaMemcpyAsync(xsave, x_d, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    double t = 1.0, Pit = 0.0;
+    bool acc = false;
+    for (int hv = 0; hv < 40; ++hv) {
+      launch_positions_update(c, xsave, dxr, t, x_d);
+      bool ok = true;
+      Pit = potential(x_d, &ok);
+      if (ok) {
+        if (Pit <= Pi + 1e-4 * t * slope) { acc = true; break; }
+        if (std::fabs(t * slope) <= 1e-13 * std::max(std::fabs(Pi), 1e-300)) {
+          double cnt = residual(x_d);
+          if (cnt < cn) { acc = true; break; }
+        }
+      }
+      t *= 0.5;
+    }
+    if (!acc) {
+      launch_positions_update(c, xsave, dxr, 1.0, x_d);
+      bool ok = true;
+      Pit = potential(x_d, &ok);
+      if (!ok) {
+        CUDA_TRY(h, cudaMemcpyAsync(x_d, xsave, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        break;
+      }
+    }
+    Pi = Pit;
+    cn = residual(x_d);
+  }
+  c.kf.factored = false;  // K factor belongs to an earlier iterate
+  c.assembled = false;
+  if (c.active) c.active->factored = false;
+  sgn_status s = launch_check(h);
+  if (s != SGN_OK) return s;
+  CUDA_TRY(h, cudaStreamSynchronize(c.stream));
+  if (rep) {
+    rep->iters = it; rep->converged = conv ? 1 : 0;
+    rep->residual = cn / scale; rep->initial_residual = init;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  int stw = 0;
+  CUDA_TRY(h, cudaMemcpy(&stw, c.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (stw) CUDA_TRY(h, cudaMemset(c.status, 0, sizeof(int)));
+  return conv ? SGN_OK : SGN_ENEWTON;
+}
+
+}  // extern "C"

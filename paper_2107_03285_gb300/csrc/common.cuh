@@ -1,0 +1,134 @@
+// Internal declarations of libsgn: the context, device views of the symbolic
+// data, and the kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sgn.h"
+#include "symbolic.h"
+
+namespace sgn {
+
+// device status word bits (sticky until read by a synchronising call)
+enum : int {
+  DEV_INVERTED = 1,
+  DEV_NONFINITE = 2,
+};
+
+// device views of the static symbolic data
+struct DevSym {
+  int dim = 0, n_nodes = 0, n_elem = 0, n_free = 0, n_sn = 0, panel = 32;
+  const int32_t *elem_node = nullptr, *elem_rank = nullptr;
+  const double *elem_B = nullptr, *elem_vol = nullptr;
+  const int32_t *node_rank = nullptr, *rank_node = nullptr;
+  const int32_t *bsr_ptr = nullptr, *bsr_col = nullptr, *bsr_orig_pos = nullptr;
+  const int32_t *up_slot = nullptr, *up_slot_t = nullptr, *up_ptr = nullptr, *up_contrib = nullptr;
+  const int32_t *inc_ptr = nullptr, *inc = nullptr;
+  const int32_t *sn_first = nullptr, *sn_nown = nullptr, *sn_nstruct = nullptr;
+  const int32_t *sn_child_off = nullptr, *sn_nchild = nullptr;
+  const int64_t *sn_struct_off = nullptr;
+  const int32_t *struct_ranks = nullptr, *relpos = nullptr, *children = nullptr;
+  const int64_t *cmap_off = nullptr;
+  const int32_t *cmap = nullptr;
+  const int32_t *lvl_fronts = nullptr;     // concatenated per-level lists (sorted by nown desc)
+  const int32_t *item_sn = nullptr, *item_P = nullptr;  // per-level (front, node column) items
+};
+
+// one multifrontal store: fronts + pivots + solve buffers of one kind
+struct Store {
+  bool enabled = false;
+  int dpn = 0;              // DOFs per node: 2d (saddle point) or d (K alone)
+  bool kkt = true;          // saddle-point system (else K alone)
+  bool fp32 = false;        // element type of the fronts
+  void *F = nullptr;        // fronts, column-major f x f each
+  void *W = nullptr;        // W = L21 D workspace, f x panel per front
+  double *rhs = nullptr;    // per-front solve buffers (f each)
+  int32_t *piv_type = nullptr, *piv_perm = nullptr;  // per fully-summed DOF
+  double *D0 = nullptr, *D1 = nullptr;
+  const int64_t *front_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
+  std::vector<int64_t> h_front_off, h_w_off, h_rhs_off, h_piv_off;
+  int64_t front_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0;
+  bool factored = false;
+};
+
+struct Ctx {
+  Symbolic S;
+  double E0 = 0.0, nu = 0.0;
+  int stores = 0;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+  bool bound = false;
+
+  // carving
+  char *base = nullptr;
+  size_t bytes = 0;
+
+  DevSym ds;
+  // host copies needed for launches
+  std::vector<int64_t> h_lvl_ptr;   // level -> offset into lvl_fronts
+  std::vector<int64_t> h_item_ptr;  // level -> offset into items
+  std::vector<std::vector<int32_t>> h_lvl_ns_nodes;  // per level: nown of each front in order
+
+  // dynamic arrays
+  int n_state = 0;                  // element state doubles per element
+  double *st = nullptr;             // [n_state][n_elem]
+  double *cpv = nullptr;            // [(d+1)*d][n_elem] element forces = columns of dc/dp
+  double *Kv = nullptr, *Gv = nullptr;   // [nnzb][d*d]
+  double *wA = nullptr, *tgt = nullptr;  // [n_x] tracked weight / target (rank-DOF layout)
+  double *fx = nullptr, *fp = nullptr;   // df/dx [n_x], df/dp [n_elem] at the last assembly
+  double *xr = nullptr;             // [n_x] positions at the last assembly (rank-DOF)
+  double alpha = 0.0;
+  bool have_objective = false, assembled = false;
+
+  // refinement vectors (rank-DOF for x and lambda, element order for p)
+  double *bx = nullptr, *bp = nullptr, *bl = nullptr;
+  double *zx = nullptr, *zp = nullptr, *zl = nullptr;
+  double *rx = nullptr, *rp = nullptr, *rl = nullptr;
+  double *red = nullptr;            // reduced rhs / solution [n_free * 2d]
+  double *partial = nullptr;        // reduction scratch
+  int n_partial = 0;
+  int *status = nullptr;            // device status word
+  int64_t *counters = nullptr;      // pivot counters (perturbed, 2x2, pos, neg, zero)
+  double *eq = nullptr;             // equilibrium scratch: [4][n_x]
+  double *xsave = nullptr, *xrt = nullptr;   // [n_nodes*d], [n_x]
+  double *hx = nullptr, *hdx = nullptr, *hdl = nullptr;  // host-call staging [n_nodes*d]
+  double *hp = nullptr, *hdp = nullptr;                  // host-call staging [n_elem]
+
+  Store kkt64, kkt32, kf;
+  Store *active = nullptr;          // saddle-point factor of the last sgn_factor
+
+  std::string last_error;
+};
+
+// ---- launchers (assemble.cu)
+void launch_elem_state(Ctx &c, const double *x, const double *p);
+void launch_slot_gather(Ctx &c, bool with_G);
+void launch_objective_terms(Ctx &c, const double *x, const double *p);
+void launch_reduce_rhs(Ctx &c, const double *bx, const double *bp, const double *bl, double *red, int dpn_kkt);
+void launch_recover(Ctx &c, const double *red, const double *bp, double *zx, double *zp, double *zl);
+void launch_residual(Ctx &c, const double *bx, const double *bp, const double *bl, const double *zx,
+                     const double *zp, const double *zl, double *rx, double *rp, double *rl);
+// returns sum of squares of the concatenation of (a, na), (b, nb), (c2, nc) on the host (synchronises)
+double device_dot(Ctx &c, const double *a, const double *b, int64_t n);
+double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64_t nb, const double *c2, int64_t nc);
+void launch_axpy(Ctx &c, double *y, const double *x, double a, int64_t n);
+void launch_to_nodes(Ctx &c, const double *vr, double *out_nodes, double fixed_value_from_X);
+void launch_to_nodes_plain(Ctx &c, const double *vr, double *out_nodes);
+void launch_from_nodes(Ctx &c, const double *nodes, double *vr);
+// equilibrium helpers
+void launch_internal_force(Ctx &c, double *fr);      // f_int in rank-DOF layout from cpv
+void launch_energy_partials(Ctx &c, const double *x, const double *p, double *partials, int nblocks);
+void launch_positions_update(Ctx &c, const double *x0, const double *dxr, double t, double *x);
+int energy_blocks(Ctx &c);
+void launch_gradient_finish(Ctx &c, const double *lam_r, double *g);
+
+// ---- launchers (front.cu)
+void factor_store(Ctx &c, Store &s);
+void solve_store(Ctx &c, Store &s, const double *b_red, double *x_red);
+void pivot_counts(Ctx &c, Store &s);  // fills c.counters (device)
+
+}  // namespace sgn

@@ -1,0 +1,730 @@
+// Multifrontal LDL^T of the (p-eliminated) saddle-point system and of K, and
+// the matching forward / diagonal / backward solves.
+//
+// Fronts are processed level by level of the elimination tree (all fronts of
+// a level are independent).  A front of order f with ns fully-summed DOFs is
+// a dense column-major f x f matrix (lower triangle used).  It is assembled
+// by pulling (no atomics) the original entries of its own columns and the
+// trailing (update) blocks of its children, then partially factored panel by
+// panel (width nb, even):
+//   1. diag:   Bunch-Kaufman (1x1 / 2x2, alpha = (1 + sqrt 17) / 8) on the
+//              nb x nb diagonal block in FP64, pivot search restricted to the
+//              panel; symmetric swaps are applied to the panel and to the
+//              already factored rows of the front.
+//   2. trsm:   W = F21 P^T L11^{-T} (= L21 D) and L21 = W D^{-1}, row-parallel.
+//   3. update: F22 -= W L21^T on the lower triangle (tiled GEMM).
+// Restricting the pivot search to a panel never needs delayed pivots here:
+// every panel starts at an even DOF of the pair-interleaved order, so the
+// matrix eliminated so far is a principal submatrix over whole (x, lambda)
+// pairs, and every such submatrix [[A, K], [K, -G]] (K SPD, A, G PSD) is
+// nonsingular; hence each panel's trailing block is nonsingular too.
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace sgn {
+
+namespace {
+
+constexpr int MAXNB = 64;
+
+struct SV {  // store view passed to kernels
+  void *F;
+  void *W;
+  double *rhs;
+  int32_t *piv_type, *piv_perm;
+  double *D0, *D1;
+  const int64_t *front_off, *w_off, *rhs_off, *piv_off;
+  int dpn;
+  int kkt;
+};
+
+SV view(Store &s) {
+  SV v;
+  v.F = s.F; v.W = s.W; v.rhs = s.rhs; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
+  v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
+  v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
+  return v;
+}
+
+__device__ __forceinline__ int front_order(const DevSym &d, int s, int dpn) {
+  return (d.sn_nown[s] + d.sn_nstruct[s]) * dpn;
+}
+
+// ---------------------------------------------------------------- assembly
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t item_base,
+                                                        const double *__restrict__ Kv,
+                                                        const double *__restrict__ Gv,
+                                                        const double *__restrict__ wA) {
+  const int64_t item = item_base + blockIdx.x;
+  const int s = d.item_sn[item], P = d.item_P[item];
+  const int dpn = sv.dpn;
+  const int nown = d.sn_nown[s];
+  const int f = (nown + d.sn_nstruct[s]) * dpn;
+  T *F = (T *)sv.F + sv.front_off[s];
+  const int col0 = P * dpn;
+  const int64_t len = f - col0;
+  for (int64_t idx = threadIdx.x; idx < len * dpn; idx += blockDim.x) {
+    int k = (int)(idx / len);
+    int64_t i = col0 + idx % len;
+    F[i + (int64_t)(col0 + k) * f] = T(0);
+  }
+  __syncthreads();
+  if (P < nown) {
+    const int r = d.sn_first[s] + P;
+    const int k0 = d.bsr_ptr[r], nsl = d.bsr_ptr[r + 1] - k0;
+    for (int idx = threadIdx.x; idx < nsl * D * D; idx += blockDim.x) {
+      int sl = idx / (D * D), ab = idx - sl * D * D;
+      int a = ab / D, b = ab - a * D;
+      int kk = k0 + sl;
+      int Q = d.bsr_orig_pos[kk];
+      if (Q < 0) continue;
+      double kv = Kv[(int64_t)kk * D * D + b * D + a];  // K[(c,a),(r,b)]
+      if (sv.kkt) {
+        int rx = Q * dpn + 2 * a, cx = P * dpn + 2 * b;
+        double gv = Gv[(int64_t)kk * D * D + b * D + a];
+        if (rx >= cx + 1) F[rx + (int64_t)(cx + 1) * f] += T(kv);        // (x row, lambda col)
+        if (rx + 1 >= cx) F[(rx + 1) + (int64_t)cx * f] += T(kv);        // (lambda row, x col)
+        if (rx + 1 >= cx + 1) F[(rx + 1) + (int64_t)(cx + 1) * f] += T(-gv);
+        if (Q == P && a == b) F[rx + (int64_t)cx * f] += T(wA[(int64_t)r * D + a]);
+      } else {
+        int ri = Q * D + a, ci = P * D + b;
+        if (ri >= ci) F[ri + (int64_t)ci * f] += T(kv);
+      }
+    }
+  }
+  __syncthreads();
+  const int coff = d.sn_child_off[s], nch = d.sn_nchild[s];
+  for (int j = 0; j < nch; ++j) {
+    const int c = d.children[coff + j];
+    const int q = d.cmap[d.cmap_off[coff + j] + P];
+    if (q >= 0) {
+      const int nownc = d.sn_nown[c], nstc = d.sn_nstruct[c];
+      const int nsc = nownc * dpn, fc = (nownc + nstc) * dpn;
+      const T *Fc = (const T *)sv.F + sv.front_off[c];
+      const int32_t *relc = d.relpos + d.sn_struct_off[c];
+      const int nq = nstc - q;
+      const int64_t rows = (int64_t)nq * dpn;
+      for (int64_t idx = threadIdx.x; idx < rows * dpn; idx += blockDim.x) {
+        int k = (int)(idx / rows);
+        int64_t rem = idx - (int64_t)k * rows;
+        int qq = q + (int)(rem / dpn), kp = (int)(rem % dpn);
+        int64_t ic = nsc + (int64_t)qq * dpn + kp, jc = nsc + (int64_t)q * dpn + k;
+        if (ic >= jc) F[(int64_t)relc[qq] * dpn + kp + (int64_t)(col0 + k) * f] += Fc[ic + jc * fc];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- Bunch-Kaufman panel
+template <typename T>
+__global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                  int nb, double eps_rel, unsigned long long *counters) {
+  __shared__ double a[MAXNB][MAXNB + 1];  // a[j][i] = A(i, j), column j
+  __shared__ double sD0[MAXNB], sD1[MAXNB];
+  __shared__ int sperm[MAXNB], stype[MAXNB];
+  __shared__ int s_kp, s_kstep;
+  __shared__ double s_bmax;
+  const int s = fronts[blockIdx.x];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  T *F = (T *)sv.F + sv.front_off[s];
+  const int tid = threadIdx.x;
+  const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int j = idx / w, i = idx - j * w;
+    a[j][i] = (i >= j) ? (double)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : 0.0;
+  }
+  if (tid < w) { sperm[tid] = tid; stype[tid] = 0; sD1[tid] = 0.0; }
+  __syncthreads();
+  if (tid < 32) {
+    double m = 0.0;
+    for (int idx = tid; idx < w * w; idx += 32) {
+      int j = idx / w, i = idx - j * w;
+      if (i >= j) m = fmax(m, fabs(a[j][i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) s_bmax = m;
+  }
+  __syncthreads();
+  const double thresh = eps_rel * fmax(s_bmax, 1e-300);
+  int j = 0;
+  while (j < w) {
+    if (tid < 32) {
+      // column max below the diagonal (restricted to the panel)
+      double cm = -1.0;
+      int ci = w;
+      for (int i = j + 1 + tid; i < w; i += 32) {
+        double v = fabs(a[j][i]);
+        if (v > cm) { cm = v; ci = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, cm, o);
+        int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+        if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
+      }
+      double colmax = fmax(cm, 0.0);
+      int imax = ci;
+      double absakk = fabs(a[j][j]);
+      int kstep = 1, kp = j;
+      if (!(fmax(absakk, colmax) > thresh)) {
+        kstep = 1; kp = j;  // (near-)zero column: static pivot below
+      } else if (absakk >= alpha * colmax) {
+        kstep = 1; kp = j;
+      } else {
+        double rm = 0.0;
+        for (int t = j + tid; t < w; t += 32) {
+          if (t == imax) continue;
+          double v = t < imax ? fabs(a[t][imax]) : fabs(a[imax][t]);
+          rm = fmax(rm, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        double rowmax = rm;
+        if (absakk >= alpha * colmax * (colmax / rowmax)) { kstep = 1; kp = j; }
+        else if (fabs(a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
+        else { kstep = 2; kp = imax; }
+      }
+      if (tid == 0) { s_kp = kp; s_kstep = kstep; }
+    }
+    __syncthreads();
+    const int kstep = s_kstep, kp = s_kp;
+    const int kk = j + kstep - 1;
+    if (kp != kk) {
+      // symmetric interchange of kk and kp in the trailing lower triangle and
+      // of the already eliminated part of both rows
+      int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
+      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += blockDim.x) {
+        if (idx == 0) {
+          double t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
+          int tp = sperm[kk]; sperm[kk] = sperm[kp]; sperm[kp] = tp;
+        } else if (idx <= n1) {
+          int i = kp + idx;
+          double t0 = a[kk][i]; a[kk][i] = a[kp][i]; a[kp][i] = t0;
+        } else if (idx <= n1 + n2) {
+          int i = kk + (idx - n1);
+          double t0 = a[kk][i]; a[kk][i] = a[i][kp]; a[i][kp] = t0;
+        } else {
+          int cc = idx - n1 - n2 - 1;
+          double t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
+        }
+      }
+      __syncthreads();
+    }
+    if (kstep == 1) {
+      if (tid == 0) {
+        double dj = a[j][j];
+        if (!(fabs(dj) > thresh)) {
+          dj = (dj >= 0.0) ? thresh : -thresh;
+          a[j][j] = dj;
+          atomicAdd(counters + 0, 1ull);
+        }
+        sD0[j] = dj; stype[j] = 0;
+      }
+      __syncthreads();
+      const double rd = 1.0 / a[j][j];
+      const int m = w - j - 1;
+      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        int cc = j + 1 + idx / m, i = j + 1 + idx % m;
+        if (i >= cc) a[cc][i] -= a[j][i] * a[j][cc] * rd;
+      }
+      __syncthreads();
+      for (int i = j + 1 + tid; i < w; i += blockDim.x) a[j][i] *= rd;
+      __syncthreads();
+    } else {
+      const double d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
+      const double det = d11 * d22 - d21 * d21;
+      const double i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
+      const int m = w - j - 2;
+      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        int cc = j + 2 + idx / m, i = j + 2 + idx % m;
+        if (i >= cc) {
+          double l1 = a[j][i] * i11 + a[j + 1][i] * i21;
+          double l2 = a[j][i] * i21 + a[j + 1][i] * i22;
+          a[cc][i] -= l1 * a[j][cc] + l2 * a[j + 1][cc];
+        }
+      }
+      __syncthreads();
+      for (int i = j + 2 + tid; i < w; i += blockDim.x) {
+        double w1 = a[j][i], w2 = a[j + 1][i];
+        a[j][i] = w1 * i11 + w2 * i21;
+        a[j + 1][i] = w1 * i21 + w2 * i22;
+      }
+      if (tid == 0) {
+        sD0[j] = d11; sD1[j] = d21; sD0[j + 1] = d22;
+        stype[j] = 1; stype[j + 1] = 2;
+        a[j][j + 1] = 0.0;
+        atomicAdd(counters + 1, 1ull);
+      }
+      __syncthreads();
+    }
+    j += kstep;
+  }
+  // write back L11 (unit lower; diagonal holds D0) and pivot data
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int jj = idx / w, i = idx - jj * w;
+    if (i >= jj) F[(int64_t)(k + i) + (int64_t)(k + jj) * f] = T(i == jj ? sD0[jj] : a[jj][i]);
+  }
+  const int64_t po = sv.piv_off[s] + k;
+  if (tid < w) {
+    sv.piv_type[po + tid] = stype[tid];
+    sv.piv_perm[po + tid] = sperm[tid];
+    sv.D0[po + tid] = sD0[tid];
+    sv.D1[po + tid] = sD1[tid];
+  }
+  // apply the panel permutation to the factored rows left of the panel
+  // (the panel buffer a[][] is free again and serves as staging)
+  for (int c0 = 0; c0 < k; c0 += MAXNB) {
+    int cw = min(MAXNB, k - c0);
+    __syncthreads();
+    for (int idx = tid; idx < w * cw; idx += blockDim.x) {
+      int cc = idx / w, t = idx - cc * w;
+      a[cc][t] = (double)F[(int64_t)(k + sperm[t]) + (int64_t)(c0 + cc) * f];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < w * cw; idx += blockDim.x) {
+      int cc = idx / w, t = idx - cc * w;
+      F[(int64_t)(k + t) + (int64_t)(c0 + cc) * f] = T(a[cc][t]);
+    }
+  }
+}
+
+// rows below the panel: W = F21 P^T L11^{-T}, L21 = W D^{-1}
+template <typename T>
+__global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                     int nb) {
+  extern __shared__ double smem[];
+  double *Ls = smem;                     // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
+  double *xs = smem + MAXNB * MAXNB;     // [MAXNB][128]
+  __shared__ double sD0[MAXNB], sD1[MAXNB];
+  __shared__ int sperm[MAXNB], stype[MAXNB];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const int r0 = k + w;
+  const int nrows = f - r0;
+  if (blockIdx.x * 128 >= nrows) return;
+  T *F = (T *)sv.F + sv.front_off[s];
+  T *W = (T *)sv.W + sv.w_off[s];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int t = idx / w, c = idx - t * w;
+    Ls[t * MAXNB + c] = (c < t) ? (double)F[(int64_t)(k + t) + (int64_t)(k + c) * f] : 0.0;
+  }
+  const int64_t po = sv.piv_off[s] + k;
+  if (tid < w) {
+    sD0[tid] = sv.D0[po + tid]; sD1[tid] = sv.D1[po + tid];
+    sperm[tid] = sv.piv_perm[po + tid]; stype[tid] = sv.piv_type[po + tid];
+  }
+  __syncthreads();
+  const int il = blockIdx.x * 128 + tid;
+  if (il >= nrows) return;
+  const int64_t i = r0 + il;
+  for (int t = 0; t < w; ++t) xs[t * 128 + tid] = (double)F[i + (int64_t)(k + sperm[t]) * f];
+  for (int c = 0; c < w; ++c) {
+    double xc = xs[c * 128 + tid];
+    for (int t = c + 1; t < w; ++t) xs[t * 128 + tid] -= Ls[t * MAXNB + c] * xc;
+  }
+  for (int t = 0; t < w; ++t) {
+    double xt = xs[t * 128 + tid];
+    W[il + (int64_t)t * nrows] = T(xt);
+    double l;
+    if (stype[t] == 0) {
+      l = xt / sD0[t];
+    } else if (stype[t] == 1) {
+      double det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
+      l = (xt * sD0[t + 1] - xs[(t + 1) * 128 + tid] * sD1[t]) / det;
+    } else {
+      double det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
+      l = (xt * sD0[t - 1] - xs[(t - 1) * 128 + tid] * sD1[t - 1]) / det;
+    }
+    F[i + (int64_t)(k + t) * f] = T(l);
+  }
+}
+
+// F22 -= W L21^T on the lower triangle; 64 x 64 tiles, 4 x 4 per thread
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                 int nb) {
+  constexpr int KC = 32;  // K chunk staged in shared memory
+  __shared__ T As[KC][64];
+  __shared__ T Bs[KC][64];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const int r0 = k + w;
+  const int nrows = f - r0;
+  const int nt = (nrows + 63) / 64;
+  const int tile = blockIdx.x;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  while (bi * (bi + 1) / 2 > tile) --bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  T *F = (T *)sv.F + sv.front_off[s];
+  const T *W = (const T *)sv.W + sv.w_off[s];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n) acc[m][n] = T(0);
+  for (int t0 = 0; t0 < w; t0 += KC) {
+    const int kc = min(KC, w - t0);
+    __syncthreads();
+    for (int idx = tid; idx < kc * 64; idx += 256) {
+      int t = idx >> 6, ii = idx & 63;
+      int ra = bi * 64 + ii, rb = bj * 64 + ii;
+      As[t][ii] = ra < nrows ? W[ra + (int64_t)(t0 + t) * nrows] : T(0);
+      Bs[t][ii] = rb < nrows ? F[(int64_t)(r0 + rb) + (int64_t)(k + t0 + t) * f] : T(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < kc; ++t) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) av[m] = As[t][tx + 16 * m];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) bv[n] = Bs[t][ty + 16 * n];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc[m][n] = fma(av[m], bv[n], acc[m][n]);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    int jl = bj * 64 + ty + 16 * n;
+    if (jl >= nrows) continue;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int il = bi * 64 + tx + 16 * m;
+      if (il < nrows && il >= jl) F[(int64_t)(r0 + il) + (int64_t)(r0 + jl) * f] -= acc[m][n];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ solves
+__global__ void k_fwd_gather(DevSym d, SV sv, int64_t item_base, int64_t n, const double *__restrict__ b) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int dpn = sv.dpn;
+  const int64_t item = item_base + idx / dpn;
+  const int kd = (int)(idx % dpn);
+  const int s = d.item_sn[item], P = d.item_P[item];
+  const int nown = d.sn_nown[s];
+  double v = P < nown ? b[(int64_t)(d.sn_first[s] + P) * dpn + kd] : 0.0;
+  const int coff = d.sn_child_off[s], nch = d.sn_nchild[s];
+  for (int j = 0; j < nch; ++j) {
+    int c = d.children[coff + j];
+    int q = d.cmap[d.cmap_off[coff + j] + P];
+    if (q >= 0) v += sv.rhs[sv.rhs_off[c] + (int64_t)d.sn_nown[c] * dpn + (int64_t)q * dpn + kd];
+  }
+  sv.rhs[sv.rhs_off[s] + (int64_t)P * dpn + kd] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_fwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb) {
+  __shared__ double y[MAXNB];
+  const int s = fronts[blockIdx.x];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  const int64_t po = sv.piv_off[s] + k;
+  const int t = threadIdx.x;
+  if (t < w) y[t] = rhs[k + sv.piv_perm[po + t]];
+  __syncthreads();
+  for (int c = 0; c < w; ++c) {
+    double yc = y[c];
+    if (t > c && t < w) y[t] -= (double)F[(int64_t)(k + t) + (int64_t)(k + c) * f] * yc;
+    __syncthreads();
+  }
+  if (t < w) rhs[k + t] = y[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                     int nb) {
+  __shared__ double y[MAXNB];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const int r0 = k + w;
+  const int nrows = f - r0;
+  if (blockIdx.x * 256 >= nrows) return;
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  if (threadIdx.x < w) y[threadIdx.x] = rhs[k + threadIdx.x];
+  __syncthreads();
+  const int il = blockIdx.x * 256 + threadIdx.x;
+  if (il >= nrows) return;
+  const int64_t i = r0 + il;
+  double acc = 0.0;
+  for (int t = 0; t < w; ++t) acc = fma((double)F[i + (int64_t)(k + t) * f], y[t], acc);
+  rhs[i] -= acc;
+}
+
+__global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns) return;
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  const int64_t po = sv.piv_off[s];
+  int ty = sv.piv_type[po + t];
+  if (ty == 0) {
+    rhs[t] = rhs[t] / sv.D0[po + t];
+  } else if (ty == 1) {
+    double d11 = sv.D0[po + t], d21 = sv.D1[po + t], d22 = sv.D0[po + t + 1];
+    double det = d11 * d22 - d21 * d21;
+    double y1 = rhs[t], y2 = rhs[t + 1];
+    rhs[t] = (d22 * y1 - d21 * y2) / det;
+    rhs[t + 1] = (d11 * y2 - d21 * y1) / det;
+  }
+}
+
+// v_own -= L21^T x_struct (warp per own column)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t *__restrict__ fronts,
+                                                   const double *__restrict__ sol) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int nown = d.sn_nown[s];
+  const int ns = nown * dpn;
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
+  double acc = 0.0;
+  for (int i = ns + lane; i < f; i += 32) {
+    int q = i / dpn - nown, kd = i % dpn;
+    acc = fma((double)F[(int64_t)i + (int64_t)t * f], sol[(int64_t)sr[q] * dpn + kd], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) sv.rhs[sv.rhs_off[s] + t] -= acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_bwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb,
+                                                  double *__restrict__ sol) {
+  __shared__ double v[MAXNB];
+  const int s = fronts[blockIdx.x];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  const int t = threadIdx.x;
+  if (t < w) v[t] = rhs[k + t];
+  __syncthreads();
+  for (int c = w - 1; c >= 0; --c) {
+    double xc = v[c];
+    if (t < c) v[t] -= (double)F[(int64_t)(k + c) + (int64_t)(k + t) * f] * xc;
+    __syncthreads();
+  }
+  if (t < w) {
+    rhs[k + t] = v[t];
+    const int64_t po = sv.piv_off[s] + k;
+    sol[(int64_t)d.sn_first[s] * dpn + k + sv.piv_perm[po + t]] = v[t];
+  }
+}
+
+// columns left of the panel: v[c] -= sum_t L(k+t, c) x_t (warp per column)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                     int nb) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= k) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  double acc = 0.0;
+  for (int t = lane; t < w; t += 32) acc = fma((double)F[(int64_t)(k + t) + (int64_t)c * f], rhs[k + t], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) rhs[c] -= acc;
+}
+
+__global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
+                               const double *__restrict__ D1, unsigned long long *counters) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int ty = type[t];
+  unsigned long long pos = 0, neg = 0, zer = 0;
+  if (ty == 0) {
+    double v = D0[t];
+    if (v > 0) pos = 1; else if (v < 0) neg = 1; else zer = 1;
+  } else if (ty == 1) {
+    double det = D0[t] * D0[t + 1] - D1[t] * D1[t];
+    if (det < 0) { pos = 1; neg = 1; }
+    else if (det > 0) { if (D0[t] > 0) pos = 2; else neg = 2; }
+    else zer = 2;
+  }
+  if (pos) atomicAdd(counters + 2, pos);
+  if (neg) atomicAdd(counters + 3, neg);
+  if (zer) atomicAdd(counters + 4, zer);
+}
+
+// host helpers ---------------------------------------------------------------
+struct LevelInfo {
+  int64_t f0, f1;          // range in lvl_fronts
+  int64_t i0, i1;          // item range
+  std::vector<int> ns, f;  // per front (sorted order)
+};
+
+LevelInfo level_info(Ctx &c, int L, int dpn) {
+  LevelInfo li;
+  li.f0 = c.h_lvl_ptr[L]; li.f1 = c.h_lvl_ptr[L + 1];
+  li.i0 = c.h_item_ptr[L]; li.i1 = c.h_item_ptr[L + 1];
+  for (int s : c.S.level_fronts[L]) {
+    li.ns.push_back(c.S.sn[s].nown * dpn);
+    li.f.push_back(c.S.sn[s].fnodes() * dpn);
+  }
+  return li;
+}
+
+int n_active(const LevelInfo &li, int k) {
+  int n = 0;
+  while (n < (int)li.ns.size() && li.ns[n] > k) ++n;
+  return n;
+}
+
+template <typename T>
+void factor_impl(Ctx &c, Store &st) {
+  SV sv = view(st);
+  const int nb = c.S.opts.panel;
+  const int D = c.S.dim;
+  const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
+  unsigned long long *ctr = (unsigned long long *)c.counters;
+  cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
+  const size_t trsm_smem = (MAXNB * MAXNB + MAXNB * 128) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+    cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+    attr_set = true;
+  }
+  for (int L = 0; L < c.S.n_levels; ++L) {
+    LevelInfo li = level_info(c, L, st.dpn);
+    int64_t nitems = li.i1 - li.i0;
+    if (D == 2)
+      k_front_assemble<T, 2><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+    else
+      k_front_assemble<T, 3><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+    const int32_t *fronts = c.ds.lvl_fronts + li.f0;
+    int max_ns = li.ns.empty() ? 0 : li.ns[0];
+    for (int k = 0; k < max_ns; k += nb) {
+      int na = n_active(li, k);
+      int max_rows = 0;
+      for (int q = 0; q < na; ++q) {
+        int w = std::min(nb, li.ns[q] - k);
+        max_rows = std::max(max_rows, li.f[q] - k - w);
+      }
+      k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
+      if (max_rows > 0) {
+        dim3 gt((max_rows + 127) / 128, na);
+        k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb);
+        int nt = (max_rows + 63) / 64;
+        dim3 gu(nt * (nt + 1) / 2, na);
+        k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      }
+    }
+  }
+  st.factored = true;
+}
+
+template <typename T>
+void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
+  SV sv = view(st);
+  const int nb = c.S.opts.panel;
+  const int dpn = st.dpn;
+  for (int L = 0; L < c.S.n_levels; ++L) {
+    LevelInfo li = level_info(c, L, dpn);
+    int64_t n = (li.i1 - li.i0) * dpn;
+    k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, li.i0, n, b);
+    const int32_t *fronts = c.ds.lvl_fronts + li.f0;
+    int max_ns = li.ns.empty() ? 0 : li.ns[0];
+    for (int k = 0; k < max_ns; k += nb) {
+      int na = n_active(li, k);
+      int max_rows = 0;
+      for (int q = 0; q < na; ++q) {
+        int w = std::min(nb, li.ns[q] - k);
+        max_rows = std::max(max_rows, li.f[q] - k - w);
+      }
+      k_fwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      if (max_rows > 0) {
+        dim3 g((max_rows + 255) / 256, na);
+        k_fwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      }
+    }
+    int nf = (int)(li.f1 - li.f0);
+    dim3 gd((max_ns + 255) / 256, nf);
+    if (max_ns > 0) k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts);
+  }
+  for (int L = c.S.n_levels - 1; L >= 0; --L) {
+    LevelInfo li = level_info(c, L, dpn);
+    const int32_t *fronts = c.ds.lvl_fronts + li.f0;
+    int nf = (int)(li.f1 - li.f0);
+    int max_ns = li.ns.empty() ? 0 : li.ns[0];
+    if (max_ns == 0) continue;
+    dim3 gi((max_ns + 7) / 8, nf);
+    k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x);
+    int last = ((max_ns - 1) / nb) * nb;
+    for (int k = last; k >= 0; k -= nb) {
+      int na = n_active(li, k);
+      k_bwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb, x);
+      if (k > 0) {
+        dim3 g((k + 7) / 8, na);
+        k_bwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void factor_store(Ctx &c, Store &s) {
+  if (s.fp32) factor_impl<float>(c, s);
+  else factor_impl<double>(c, s);
+}
+
+void solve_store(Ctx &c, Store &s, const double *b, double *x) {
+  if (s.fp32) solve_impl<float>(c, s, b, x);
+  else solve_impl<double>(c, s, b, x);
+}
+
+void pivot_counts(Ctx &c, Store &s) {
+  int64_t n = s.piv_elems;
+  k_pivot_counts<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, s.piv_type, s.D0, s.D1,
+                                                                     (unsigned long long *)c.counters);
+}
+
+}  // namespace sgn

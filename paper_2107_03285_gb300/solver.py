@@ -1,0 +1,164 @@
+"""Python front end of libsgn: one SGN context bound to one CUDA device.
+
+PyTorch provides the device buffer the library carves its matrices, fronts and
+workspaces from, and the stream the kernels run on.  All arithmetic of the
+SGN step (element evaluation, assembly, factorization, solves, refinement,
+Newton equilibrium, adjoint gradient) runs in libsgn's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import binding as B
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class SGN:
+    """Sparse Gauss-Newton context for one mesh (Sec. 4, Eq. sparseSystemGN)."""
+
+    def __init__(self, dim, X, conn, fixed_node, E0, nu, stores=B.STORE_FP64 | B.STORE_KFACT,
+                 leaf_nodes=0, panel=0, device="cuda", stream=None):
+        import torch
+        self._torch = torch
+        self.lib = B.lib()
+        self.dim = int(dim)
+        self.X = _f64(X).reshape(-1, self.dim)
+        self.conn = np.ascontiguousarray(conn, dtype=np.int32)
+        self.fixed = np.ascontiguousarray(fixed_node, dtype=np.uint8)
+        self.n_nodes, self.n_elem = self.X.shape[0], self.conn.shape[0]
+        mesh = B.Mesh(self.dim, self.n_nodes, self.n_elem, B._dptr(self.X, C.c_double),
+                      B._dptr(self.conn, C.c_int32), B._dptr(self.fixed, C.c_uint8), float(E0), float(nu))
+        opts = B.SetupOpts(int(leaf_nodes), int(panel))
+        h = C.c_void_p()
+        B._check(self.lib.sgn_setup(C.byref(mesh), C.byref(opts), C.byref(h)), "sgn_setup")
+        self.h = h
+        self.info = B.Info()
+        B._check(self.lib.sgn_get_info(self.h, C.byref(self.info)), "sgn_get_info")
+        self.stores = int(stores)
+        nbytes = C.c_size_t()
+        B._check(self.lib.sgn_device_bytes(self.h, self.stores, C.byref(nbytes)), "sgn_device_bytes")
+        self.device = torch.device(device)
+        self.buf = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        B._check(self.lib.sgn_bind(self.h, C.c_void_p(self.buf.data_ptr()), int(nbytes.value), self.stores,
+                                   C.c_void_p(self.stream.cuda_stream)), "sgn_bind")
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        s = cls(prob.dim, prob.X, prob.conn, prob.fixed_node, prob.E0, prob.nu, **kw)
+        s.set_objective(prob.track_dof, prob.target, prob.weight, prob.alpha)
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._torch.cuda.synchronize(self.device)
+            self.lib.sgn_destroy(self.h)
+            self.h = None
+            self.buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def _dev(self, a, shape):
+        t = self._torch
+        if isinstance(a, t.Tensor):
+            if a.device.type != "cuda" or a.dtype != t.float64 or not a.is_contiguous():
+                raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+            return a
+        return t.as_tensor(_f64(a).reshape(shape), device=self.device)
+
+    def _empty(self, *shape):
+        return self._torch.empty(*shape, dtype=self._torch.float64, device=self.device)
+
+    @staticmethod
+    def _p(t):
+        return C.c_void_p(t.data_ptr()) if t is not None else None
+
+    # ---------------------------------------------------------------- C ABI
+    def set_objective(self, track_dof, target, weight, alpha):
+        self._track = np.ascontiguousarray(track_dof, dtype=np.int64)
+        self._target = _f64(target)
+        self._weight = _f64(weight)
+        obj = B.Objective(self._track.shape[0], B._dptr(self._track, C.c_int64),
+                          B._dptr(self._target, C.c_double), B._dptr(self._weight, C.c_double), float(alpha))
+        B._check(self.lib.sgn_set_objective(self.h, C.byref(obj)), "sgn_set_objective")
+
+    def assemble(self, x, p):
+        self._x = self._dev(x, (self.n_nodes, self.dim))
+        self._pv = self._dev(p, (self.n_elem,))
+        B._check(self.lib.sgn_assemble(self.h, self._p(self._x), self._p(self._pv)), "sgn_assemble")
+
+    def factor(self, precision=B.FP64, report=True):
+        rep = B.FactorReport() if report else None
+        B._check(self.lib.sgn_factor(self.h, int(precision), C.byref(rep) if report else None), "sgn_factor")
+        return rep
+
+    def solve(self, mode=B.RHS_KKT, g=None, max_refine=0, tol=0.0, report=True, out=None):
+        dx, dp, dl = out if out is not None else (self._empty(self.n_nodes, self.dim), self._empty(self.n_elem),
+                                                   self._empty(self.n_nodes, self.dim))
+        gd = self._dev(g, (self.n_elem,)) if g is not None else None
+        opts = B.SolveOpts(int(max_refine), float(tol))
+        rep = B.SolveReport() if report else None
+        B._check(self.lib.sgn_solve(self.h, int(mode), self._p(gd), self._p(dx), self._p(dp), self._p(dl),
+                                    C.byref(opts), C.byref(rep) if report else None), "sgn_solve")
+        return dx, dp, dl, rep
+
+    def step(self, x, p, precision=B.FP64, mode=B.RHS_KKT, g=None):
+        self.assemble(x, p)
+        frep = self.factor(precision)
+        dx, dp, dl, srep = self.solve(mode, g)
+        return dx, dp, dl, frep, srep
+
+    def step_host(self, x, p, precision=B.FP64):
+        """Host buffers in and out (H2D / D2H copies inside the call)."""
+        xh = _f64(x).reshape(self.n_nodes, self.dim)
+        ph = _f64(p).reshape(self.n_elem)
+        dx = np.empty_like(xh)
+        dl = np.empty_like(xh)
+        dp = np.empty_like(ph)
+        rep = B.SolveReport()
+        dptr = lambda a: B._dptr(a, C.c_double)
+        code = self.lib.sgn_step_host(self.h, int(precision), dptr(xh), dptr(ph), dptr(dx), dptr(dp), dptr(dl),
+                                      C.byref(rep))
+        if code not in (B.OK, B.EREFINE):
+            B._check(code, "sgn_step_host")
+        return dx, dp, dl, rep
+
+    def equilibrium(self, p, fext, x0=None, max_iter=0, tol=0.0):
+        pd = self._dev(p, (self.n_elem,))
+        fd = self._dev(fext, (self.n_nodes, self.dim))
+        x = self._dev(self.X if x0 is None else x0, (self.n_nodes, self.dim)).clone()
+        rep = B.NewtonReport()
+        code = self.lib.sgn_equilibrium(self.h, self._p(pd), self._p(fd), self._p(x),
+                                        C.byref(B.NewtonOpts(int(max_iter), float(tol))), C.byref(rep))
+        if code != B.OK:
+            B._check(code, "sgn_equilibrium")
+        return x, rep
+
+    def export_kkt(self):
+        """Assembled saddle-point matrix as (rows, cols, vals) host COO arrays."""
+        n = C.c_int64()
+        B._check(self.lib.sgn_export_kkt(self.h, C.byref(n), None, None, None), "sgn_export_kkt")
+        rows = np.empty(n.value, dtype=np.int64)
+        cols = np.empty(n.value, dtype=np.int64)
+        vals = np.empty(n.value, dtype=np.float64)
+        B._check(self.lib.sgn_export_kkt(self.h, C.byref(n), B._dptr(rows, C.c_int64), B._dptr(cols, C.c_int64),
+                                         B._dptr(vals, C.c_double)), "sgn_export_kkt")
+        return rows, cols, vals
+
+    def factor_k(self):
+        B._check(self.lib.sgn_factor_k(self.h), "sgn_factor_k")
+
+    def gradient(self):
+        g = self._empty(self.n_elem)
+        B._check(self.lib.sgn_gradient(self.h, self._p(g)), "sgn_gradient")
+        return g

@@ -1,0 +1,107 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every
+symbol include/sgn.h declares, and its host-only calls (symbolic set-up,
+info, device sizing, argument validation) behave.  No GPU needed."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from sgn_inputs import problem_2d, problem_3d, problem_tiny_3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2107_03285_gb300 import build as build_mod
+    build_mod.build()
+    from paper_2107_03285_gb300 import binding
+    return binding
+
+
+def _declared_symbols():
+    out = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", name)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            out |= set(re.findall(r"\b(sgn_[a-z0-9_]+)\s*\(", txt))
+    return out
+
+
+def test_library_exports_every_declared_symbol(B):
+    lib = B.load_library()
+    declared = _declared_symbols()
+    assert declared, "no declarations found"
+    for sym in sorted(declared):
+        assert hasattr(lib, sym), sym
+    assert declared == set(B.EXPORTED)
+
+
+def _setup(B, prob, leaf=0, panel=0):
+    lib = B.load_library()
+    X = np.ascontiguousarray(prob.X, dtype=np.float64)
+    conn = np.ascontiguousarray(prob.conn, dtype=np.int32)
+    fixed = np.ascontiguousarray(prob.fixed_node, dtype=np.uint8)
+    mesh = B.Mesh(prob.dim, X.shape[0], conn.shape[0], B._dptr(X, C.c_double), B._dptr(conn, C.c_int32),
+                  B._dptr(fixed, C.c_uint8), prob.E0, prob.nu)
+    h = C.c_void_p()
+    code = lib.sgn_setup(C.byref(mesh), C.byref(B.SetupOpts(leaf, panel)), C.byref(h))
+    return lib, code, h, (X, conn, fixed)
+
+
+@pytest.mark.parametrize("which", ["grid2d_21", "kuhn3d_5"])
+def test_setup_sizes_match_the_oracle_pattern(B, which):
+    from oracle import equilibrium as EQ
+    from oracle import system as S
+    prob = problem_2d() if which == "grid2d_21" else problem_3d(5, p_sigma=0.1)
+    lib, code, h, keep = _setup(B, prob)
+    assert code == B.OK
+    info = B.Info()
+    assert lib.sgn_get_info(h, C.byref(info)) == B.OK
+    n_x = prob.n_free * prob.dim
+    assert info.n_x == n_x and info.n_p == prob.n_elem and info.n_kkt == 2 * n_x + prob.n_elem
+    x, _ = EQ.newton(prob, prob.p0)
+    M = S.kkt_matrix(S.blocks(prob, x, prob.p0))
+    assert info.nnz_kkt + len(np.unique(prob.track_dof)) == M.nnz
+    assert info.factor_flops > 0 and info.nnz_factor > 0 and info.n_levels >= 1
+    nbytes = C.c_size_t()
+    assert lib.sgn_device_bytes(h, B.STORE_FP64 | B.STORE_MIXED | B.STORE_KFACT, C.byref(nbytes)) == B.OK
+    assert nbytes.value > 8 * info.nnz_factor
+    lib.sgn_destroy(h)
+
+
+def test_setup_rejects_bad_meshes(B):
+    prob = problem_tiny_3d()
+    bad = problem_tiny_3d()
+    bad.conn = bad.conn.copy()
+    bad.conn[0, 0] = bad.n_nodes + 5
+    _, code, _, _ = _setup(B, bad)
+    assert code == B.EINVAL
+    bad2 = problem_tiny_3d()
+    bad2.conn = bad2.conn.copy()
+    bad2.conn[0, 1] = bad2.conn[0, 0]   # degenerate element
+    _, code, _, _ = _setup(B, bad2)
+    assert code == B.EINVAL
+    allfixed = problem_tiny_3d()
+    allfixed.fixed_node = np.ones_like(allfixed.fixed_node)
+    _, code, _, _ = _setup(B, allfixed)
+    assert code == B.EINVAL
+    _, code, _, _ = _setup(B, prob, panel=7)
+    assert code == B.EINVAL
+    lib = B.load_library()
+    assert lib.sgn_setup(None, None, None) == B.EINVAL
+    assert lib.sgn_strerror(B.EINVERTED).decode().startswith("inverted")
+
+
+def test_calls_before_bind_are_rejected(B):
+    prob = problem_tiny_3d()
+    lib, code, h, keep = _setup(B, prob)
+    assert code == B.OK
+    assert lib.sgn_assemble(h, None, None) == B.EINVAL
+    one = C.c_void_p(1)
+    assert lib.sgn_assemble(h, one, one) == B.ESTATE
+    assert lib.sgn_factor(h, B.FP64, None) == B.ESTATE
+    lib.sgn_destroy(h)
