@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""SGN steps/sec on GB300: assemble + factor + solve (+ FP64 refinement).
+
+A step is one pass of the SGN hot path at an equilibrium state: element
+evaluation and no-atomic assembly of the saddle-point matrix of
+Eq. sparseSystemGN, its multifrontal LDL^T, and the solves for (dx, dp,
+dlambda) with FP64 iterative refinement.  The default workload is the 3D
+Kuhn-tet cube with 40^3 nodes (355,914 tets, 730,314 saddle-point unknowns);
+the headline precision is the mixed path (FP32 fronts, FP64 pivots,
+residuals and refinement), checked against the plain FP64 GPU path.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the factorization of one mesh is not sharded); value = all ranks' steps /
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SGN steps/sec (assemble+factor+solve)"
+UNIT = "steps/s"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 / FP64 pipe peaks measured on this machine's GB300 with an FMA-chain
+# kernel (152 SMs; the derivation is in the design doc)
+FP32_SIMT_TFLOPS = 70.0
+FP64_TFLOPS = 1.20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kuhn3d_40")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", default="kuhn3d_12", help="oracle sample workload")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_step_rate(sample: str, seconds: float, seed: int):
+    """The CPU oracle, as it stands: element blocks + SuperLU solve of the
+    saddle-point system, on a smaller mesh of the same family."""
+    from oracle import equilibrium as EQ
+    from oracle import system as S
+    from sgn_inputs import make_preset
+    prob = make_preset(sample, seed=seed)
+    x, _ = EQ.newton(prob, prob.p0)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        b = S.blocks(prob, x, prob.p0)
+        S.sgn_step(b, "kkt")
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    N = 2 * prob.n_free * prob.dim + prob.n_elem
+    return n / dt, {"kind": "oracle", "cores": os.cpu_count(),
+                    "sample": f"{sample}: {prob.n_elem} elements, N={N}; {n} steps in {dt:.1f} s "
+                              f"(NumPy elements + SciPy SuperLU, host cores)"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    from sgn_inputs import make_preset
+    rate_w = None
+    for _ in range(max(args.warmup, 0)):
+        rate_w, _ = oracle_step_rate(args.cpu_sample, 0.0, args.seed)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        r, info = oracle_step_rate(args.cpu_sample, 0.0, args.seed)
+        n += 1
+    dt = time.perf_counter() - t0
+    value = n / dt
+    info["value"] = value
+    info["unit"] = UNIT
+    prob = make_preset(args.workload)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(n, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample": args.cpu_sample,
+                       "note": "the oracle cannot factor the full workload in minutes; each step runs the sample"},
+            "cpu_baseline": info,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2107_03285_gb300 as P
+    from sgn_inputs import make_preset
+
+    prob = make_preset(args.workload, seed=args.seed)
+    prec = P.MIXED if args.precision == "mixed" else P.FP64
+    stores = P.STORE_KFACT | P.STORE_FP64 | (P.STORE_MIXED if prec == P.MIXED else 0)
+    t_setup = time.perf_counter()
+    s = P.SGN.from_problem(prob, stores=stores)
+    t_setup = time.perf_counter() - t_setup
+    info = s.info
+    # forward simulation to the equilibrium the step is taken at (reported separately)
+    xeq, nrep = s.equilibrium(prob.p0, prob.fext)
+    p = torch.as_tensor(prob.p0, device=dev)
+    out = (torch.empty_like(xeq), torch.empty_like(p), torch.empty_like(xeq))
+
+    def step(precision):
+        s.assemble(xeq, p)
+        s.factor(precision, report=False)
+        return s.solve(P.RHS_KKT, report=False, out=out)
+
+    # plain FP64 GPU path: reference accuracy and its own rate
+    fp64 = None
+    dp64 = None
+    if args.fp64_steps > 0 or prec == P.FP64:
+        step(P.FP64)
+        torch.cuda.synchronize()
+        dp64 = out[1].clone()
+        if args.fp64_steps > 0 and prec != P.FP64:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.fp64_steps):
+                step(P.FP64)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.fp64_steps
+            fp64 = {"steps_per_s": 1e3 / ms, "ms_per_step": ms,
+                    "factor_tflops": info.factor_flops / (ms * 1e-3) / 1e12}
+
+    for _ in range(args.warmup):
+        step(prec)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    launches0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step(prec)
+        e1.record()
+        torch.cuda.synchronize()
+    launches = s.launch_count() - launches0
+    prof = s.profile_read()
+    s.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = ws * 1e3 / ms
+    dp = out[1].clone()
+    dp_err = float(torch.linalg.norm(dp - dp64) / torch.linalg.norm(dp64)) if dp64 is not None else None
+    _, _, _, srep = s.solve(P.RHS_KKT, report=True, out=out)
+
+    # end to end through the C ABI with host buffers (H2D of x, p; D2H of dx, dp, dl)
+    xh = torch.empty(tuple(xeq.shape), dtype=torch.float64, pin_memory=True)
+    xh.copy_(xeq)
+    ph = torch.empty(tuple(p.shape), dtype=torch.float64, pin_memory=True)
+    ph.copy_(p)
+    xnp, pnp = xh.numpy(), ph.numpy()
+    s.step_host(xnp, pnp, prec)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.step_host(xnp, pnp, prec)
+    e2e_dt = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
+    e2e = {"value": ws / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(xnp.nbytes + pnp.nbytes),
+           "d2h_bytes_per_step": int(2 * xnp.nbytes + pnp.nbytes)}
+
+    if rank != 0:
+        s.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    fp32 = prec == P.MIXED
+    achieved = prof.flops / prof.seconds / 1e12 if prof.seconds > 0 else None
+    peak = FP32_SIMT_TFLOPS if fp32 else FP64_TFLOPS
+    roofline = {"kernel": "k_update (front Schur update, " + ("FP32 SIMT" if fp32 else "FP64 DFMA") + ")",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": "measured FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)",
+                "launches_per_step": prof.launches / args.steps,
+                "share_of_step": prof.seconds / (ms * 1e-3 * args.steps)}
+    cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
+    cpu_info["value"] = cpu_rate
+    cpu_info["unit"] = UNIT
+    N = int(info.n_kkt)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {prob.n_elem} tets, {prob.n_nodes} nodes, N={N} saddle-point "
+                               f"unknowns, p = per-tet log-modulus",
+                   "precision": args.precision, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                   "l2": f"not flushed: the step's working set ({s.buf.numel() / 1e9:.1f} GB) exceeds L2",
+                   "dp_rel_err_vs_fp64_gpu": dp_err, "refine_steps": srep.refine_steps,
+                   "kkt_residual": srep.residual, "factor_flops": info.factor_flops,
+                   "nnz_factor": info.nnz_factor, "fp64_path": fp64,
+                   "setup_s": info.setup_seconds, "bind_s": t_setup,
+                   "equilibrium": {"iters": nrep.iters, "residual": nrep.residual, "seconds": nrep.seconds}},
+        "roofline": roofline,
+        "cpu_baseline": cpu_info,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+    s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -224,6 +224,23 @@ sgn_status sgn_gradient(sgn_t h, double *g_d);
 /* sgn_factor_k: factor K alone at the assembled (x, p) (FP64). */
 sgn_status sgn_factor_k(sgn_t h);
 
+/* ---- measurement support (no counterpart in the paper) ------------------
+ * sgn_profile(h, 1) resets and enables CUDA-event timing of every launch of
+ * the front Schur-update kernel (the dominant kernel of sgn_factor) on the
+ * context's stream; sgn_profile(h, 0) disables it.  sgn_profile_read
+ * synchronises and returns the launches, summed device seconds and summed
+ * algorithmic flops (2 * rows * cols * k per lower-triangle update) since
+ * the last reset. */
+typedef struct {
+  int64_t launches;
+  double seconds;
+  double flops;
+} sgn_kernel_profile;
+sgn_status sgn_profile(sgn_t h, int32_t enable);
+sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *update_kernel);
+/* Number of CUDA kernels this context has launched since sgn_bind. */
+int64_t sgn_launch_count(sgn_t h);
+
 #ifdef __cplusplus
 }
 #endif

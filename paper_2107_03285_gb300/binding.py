@@ -24,7 +24,7 @@ STORE_FP64, STORE_MIXED, STORE_KFACT = 1, 2, 4
 EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
-            "sgn_export_kkt"]
+            "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count"]
 
 
 class Mesh(C.Structure):
@@ -64,6 +64,10 @@ class SolveReport(C.Structure):
     _fields_ = [("refine_steps", C.c_int32), ("residual", C.c_double), ("seconds", C.c_double)]
 
 
+class KernelProfile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("seconds", C.c_double), ("flops", C.c_double)]
+
+
 class NewtonOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double)]
 
@@ -96,6 +100,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_gradient": (C.c_int, [VP, VP]),
         "sgn_factor_k": (C.c_int, [VP]),
         "sgn_export_kkt": (C.c_int, [VP, P(C.c_int64), P(C.c_int64), P(C.c_int64), dp]),
+        "sgn_profile": (C.c_int, [VP, C.c_int32]),
+        "sgn_profile_read": (C.c_int, [VP, P(KernelProfile)]),
+        "sgn_launch_count": (C.c_int64, [VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -316,7 +316,11 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
   return SGN_OK;
 }
 
-void sgn_destroy(sgn_t h) { delete h; }
+void sgn_destroy(sgn_t h) {
+  if (!h) return;
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  delete h;
+}
 
 sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d) {
   if (!h || !x_d || !p_d) return SGN_EINVAL;
@@ -427,7 +431,10 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     rep->residual = bn > 0 ? rn / bn : rn;
     rep->seconds = ms * 1e-3;
   }
-  if (bn > 0 && rn > 1e3 * tol * bn && st.fp32) return SGN_EREFINE;
+  if (bn > 0 && rn > 1e-8 * bn) {
+    h->last_error = "refinement left a residual above 1e-8 relative";
+    return SGN_EREFINE;
+  }
   return SGN_OK;
 }
 
@@ -502,6 +509,31 @@ sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows, int64_t *cols, d
   *nnz = n;
   return SGN_OK;
 }
+
+sgn_status sgn_profile(sgn_t h, int32_t enable) {
+  if (!h) return SGN_EINVAL;
+  h->prof = enable != 0;
+  h->prof_used = 0;
+  h->prof_flops = 0.0;
+  return SGN_OK;
+}
+
+sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out) {
+  if (!h || !out) return SGN_EINVAL;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  double s = 0.0;
+  for (int64_t i = 0; i + 1 < h->prof_used; i += 2) {
+    float ms = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->prof_ev[i], h->prof_ev[i + 1]));
+    s += ms * 1e-3;
+  }
+  out->launches = h->prof_used / 2;
+  out->seconds = s;
+  out->flops = h->prof_flops;
+  return SGN_OK;
+}
+
+int64_t sgn_launch_count(sgn_t h) { return h ? h->launches : -1; }
 
 sgn_status sgn_factor_k(sgn_t h) {
   if (!h) return SGN_EINVAL;

@@ -449,6 +449,7 @@ __global__ void k_positions(int n_free, const int32_t *__restrict__ rank_node, c
   do {                                                                            \
     if ((c).S.dim == 2) KERNEL<2><<<GRID, BLOCK, SMEM, (c).stream>>>(__VA_ARGS__); \
     else KERNEL<3><<<GRID, BLOCK, SMEM, (c).stream>>>(__VA_ARGS__);               \
+    (c).count();                                                                  \
   } while (0)
 
 void launch_elem_state(Ctx &c, const double *x, const double *p) {
@@ -470,6 +471,7 @@ void launch_objective_terms(Ctx &c, const double *x, const double *p) {
   SGN_DISPATCH_D(c, k_objective, nblk((int64_t)d.n_free * d.dim), TPB, 0, d.n_free, d.rank_node, x, c.wA,
                  c.tgt, c.fx, c.xr);
   k_scale<<<nblk(d.n_elem), TPB, 0, c.stream>>>(d.n_elem, p, c.alpha, c.fp);
+  c.count();
 }
 
 void launch_reduce_rhs(Ctx &c, const double *bx, const double *bp, const double *bl, double *red, int) {
@@ -497,6 +499,7 @@ double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64
                      int64_t nc) {
   int blocks = c.n_partial;
   k_sumsq3<<<blocks, TPB, 0, c.stream>>>(a, na, b, nb, c2, nc, c.partial);
+  c.count();
   std::vector<double> h(blocks);
   cudaMemcpyAsync(h.data(), c.partial, sizeof(double) * blocks, cudaMemcpyDeviceToHost, c.stream);
   cudaStreamSynchronize(c.stream);
@@ -508,6 +511,7 @@ double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64
 double device_dot(Ctx &c, const double *a, const double *b, int64_t n) {
   int blocks = c.n_partial;
   k_dot<<<blocks, TPB, 0, c.stream>>>(a, b, n, c.partial);
+  c.count();
   std::vector<double> h(blocks);
   cudaMemcpyAsync(h.data(), c.partial, sizeof(double) * blocks, cudaMemcpyDeviceToHost, c.stream);
   cudaStreamSynchronize(c.stream);
@@ -518,6 +522,7 @@ double device_dot(Ctx &c, const double *a, const double *b, int64_t n) {
 
 void launch_axpy(Ctx &c, double *y, const double *x, double a, int64_t n) {
   k_axpy<<<nblk(n), TPB, 0, c.stream>>>(y, x, a, n);
+  c.count();
 }
 
 void launch_to_nodes_plain(Ctx &c, const double *vr, double *out) {

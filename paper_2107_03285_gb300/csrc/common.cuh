@@ -102,6 +102,17 @@ struct Ctx {
   Store *active = nullptr;          // saddle-point factor of the last sgn_factor
 
   std::string last_error;
+
+  // measurement support
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
+  int64_t prof_used = 0;              // events used (2 per launch)
+  double prof_flops = 0.0;
+  std::string prof_err;
+  void count(int n = 1) { launches += n; }
+  // returns the event pair to bracket one profiled launch (nullptr if off)
+  cudaEvent_t *prof_pair();
 };
 
 // ---- launchers (assemble.cu)

@@ -434,6 +434,25 @@ __global__ void k_fwd_gather(DevSym d, SV sv, int64_t item_base, int64_t n, cons
   sv.rhs[sv.rhs_off[s] + (int64_t)P * dpn + kd] = v;
 }
 
+// the factor holds L rows in their final pivoted order (later panels also
+// permute the rows of earlier L columns), so the fully-summed right-hand
+// side is permuted once, panel by panel, before the forward substitution
+__global__ void __launch_bounds__(64) k_fwd_permute(DevSym d, SV sv, const int32_t *__restrict__ fronts, int nb) {
+  __shared__ double y[MAXNB];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  const int k = blockIdx.x * nb;
+  if (k >= ns) return;
+  const int w = min(nb, ns - k);
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  const int64_t po = sv.piv_off[s] + k;
+  const int t = threadIdx.x;
+  if (t < w) y[t] = rhs[k + sv.piv_perm[po + t]];
+  __syncthreads();
+  if (t < w) rhs[k + t] = y[t];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(64) k_fwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb) {
   __shared__ double y[MAXNB];
@@ -447,7 +466,8 @@ __global__ void __launch_bounds__(64) k_fwd_diag(DevSym d, SV sv, const int32_t 
   double *rhs = sv.rhs + sv.rhs_off[s];
   const int64_t po = sv.piv_off[s] + k;
   const int t = threadIdx.x;
-  if (t < w) y[t] = rhs[k + sv.piv_perm[po + t]];
+  (void)po;
+  if (t < w) y[t] = rhs[k + t];
   __syncthreads();
   for (int c = 0; c < w; ++c) {
     double yc = y[c];
@@ -639,6 +659,7 @@ void factor_impl(Ctx &c, Store &st) {
       k_front_assemble<T, 2><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
     else
       k_front_assemble<T, 3><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+    c.count();
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     for (int k = 0; k < max_ns; k += nb) {
@@ -649,12 +670,23 @@ void factor_impl(Ctx &c, Store &st) {
         max_rows = std::max(max_rows, li.f[q] - k - w);
       }
       k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
+      c.count();
       if (max_rows > 0) {
         dim3 gt((max_rows + 127) / 128, na);
         k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb);
         int nt = (max_rows + 63) / 64;
         dim3 gu(nt * (nt + 1) / 2, na);
+        cudaEvent_t *ev = c.prof_pair();
+        if (ev) {
+          cudaEventRecord(ev[0], c.stream);
+          for (int q = 0; q < na; ++q) {
+            double w = std::min(nb, li.ns[q] - k), nr = li.f[q] - k - w;
+            c.prof_flops += nr * (nr + 1.0) * w;  // 2 flops x lower triangle x w
+          }
+        }
         k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+        if (ev) cudaEventRecord(ev[1], c.stream);
+        c.count(2);
       }
     }
   }
@@ -670,8 +702,14 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     LevelInfo li = level_info(c, L, dpn);
     int64_t n = (li.i1 - li.i0) * dpn;
     k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, li.i0, n, b);
+    c.count();
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
+    if (max_ns > 0) {
+      dim3 gp((max_ns + nb - 1) / nb, (unsigned)(li.f1 - li.f0));
+      k_fwd_permute<<<gp, 64, 0, c.stream>>>(c.ds, sv, fronts, nb);
+      c.count();
+    }
     for (int k = 0; k < max_ns; k += nb) {
       int na = n_active(li, k);
       int max_rows = 0;
@@ -680,14 +718,19 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
         max_rows = std::max(max_rows, li.f[q] - k - w);
       }
       k_fwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      c.count();
       if (max_rows > 0) {
         dim3 g((max_rows + 255) / 256, na);
         k_fwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+        c.count();
       }
     }
     int nf = (int)(li.f1 - li.f0);
     dim3 gd((max_ns + 255) / 256, nf);
-    if (max_ns > 0) k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts);
+    if (max_ns > 0) {
+      k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts);
+      c.count();
+    }
   }
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
     LevelInfo li = level_info(c, L, dpn);
@@ -697,19 +740,36 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     if (max_ns == 0) continue;
     dim3 gi((max_ns + 7) / 8, nf);
     k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x);
+    c.count();
     int last = ((max_ns - 1) / nb) * nb;
     for (int k = last; k >= 0; k -= nb) {
       int na = n_active(li, k);
       k_bwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb, x);
+      c.count();
       if (k > 0) {
         dim3 g((k + 7) / 8, na);
         k_bwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+        c.count();
       }
     }
   }
 }
 
 }  // namespace
+
+cudaEvent_t *Ctx::prof_pair() {
+  if (!prof) return nullptr;
+  if (prof_used + 2 > (int64_t)prof_ev.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { prof = false; prof_err = "event pool"; return nullptr; }
+      prof_ev.push_back(e);
+    }
+  }
+  cudaEvent_t *p = prof_ev.data() + prof_used;
+  prof_used += 2;
+  return p;
+}
 
 void factor_store(Ctx &c, Store &s) {
   if (s.fp32) factor_impl<float>(c, s);
@@ -725,6 +785,7 @@ void pivot_counts(Ctx &c, Store &s) {
   int64_t n = s.piv_elems;
   k_pivot_counts<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, s.piv_type, s.D0, s.D1,
                                                                      (unsigned long long *)c.counters);
+  c.count();
 }
 
 }  // namespace sgn

@@ -155,6 +155,17 @@ class SGN:
                                          B._dptr(vals, C.c_double)), "sgn_export_kkt")
         return rows, cols, vals
 
+    def profile(self, enable=True):
+        B._check(self.lib.sgn_profile(self.h, 1 if enable else 0), "sgn_profile")
+
+    def profile_read(self):
+        prof = B.KernelProfile()
+        B._check(self.lib.sgn_profile_read(self.h, C.byref(prof)), "sgn_profile_read")
+        return prof
+
+    def launch_count(self):
+        return int(self.lib.sgn_launch_count(self.h))
+
     def factor_k(self):
         B._check(self.lib.sgn_factor_k(self.h), "sgn_factor_k")
 
