@@ -292,7 +292,9 @@ def main():
                    "precision": args.precision, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "l2": f"not flushed: the step's working set ({s.buf.numel() / 1e9:.1f} GB) exceeds L2",
                    "dp_rel_err_vs_fp64_gpu": dp_err, "refine_steps": srep.refine_steps,
-                   "kkt_residual": srep.residual, "factor_flops": info.factor_flops,
+                   "kkt_residual": srep.residual,
+                   "refine_history": [float(v) for v in list(srep.history)[:srep.refine_steps + 1]],
+                   "factor_flops": info.factor_flops,
                    "nnz_factor": info.nnz_factor, "fp64_path": fp64,
                    "setup_s": info.setup_seconds, "bind_s": t_setup,
                    "equilibrium": {"iters": nrep.iters, "residual": nrep.residual, "seconds": nrep.seconds}},

@@ -137,6 +137,7 @@ typedef struct {
   int32_t refine_steps;           /* refinement steps taken */
   double residual;                /* final ||b - M z|| / ||b|| in FP64 */
   double seconds;
+  double history[32];             /* ||b - M z|| / ||b|| after each of the first 32 solves */
 } sgn_solve_report;
 
 typedef struct {

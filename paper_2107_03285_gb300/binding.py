@@ -61,7 +61,8 @@ class SolveOpts(C.Structure):
 
 
 class SolveReport(C.Structure):
-    _fields_ = [("refine_steps", C.c_int32), ("residual", C.c_double), ("seconds", C.c_double)]
+    _fields_ = [("refine_steps", C.c_int32), ("residual", C.c_double), ("seconds", C.c_double),
+                ("history", C.c_double * 32)]
 
 
 class KernelProfile(C.Structure):

@@ -151,6 +151,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     s.rhs = cv.take<double>(s.rhs_elems);
     s.piv_type = cv.take<int32_t>(s.piv_elems); s.piv_perm = cv.take<int32_t>(s.piv_elems);
     s.D0 = cv.take<double>(s.piv_elems); s.D1 = cv.take<double>(s.piv_elems);
+    s.yz = cv.take<double>(s.piv_elems);
     int64_t *p;
     st_up(p, s.h_front_off); s.front_off = p;
     st_up(p, s.h_w_off); s.w_off = p;
@@ -402,9 +403,11 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   double bn = std::sqrt(device_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx));
   double rn = 0.0;
   int steps = 0;
+  double hist[32];
   for (;;) {
     launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
     rn = std::sqrt(device_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx));
+    if (steps < 32) hist[steps] = bn > 0 ? rn / bn : rn;
     if (!(rn == rn)) { h->last_error = "non-finite residual"; return SGN_ENONFINITE; }
     if (rn <= tol * bn || steps >= max_refine) break;
     launch_reduce_rhs(c, c.rx, c.rp, c.rl, red_b, 2 * c.S.dim);
@@ -429,6 +432,7 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     rep->refine_steps = steps;
     rep->residual = bn > 0 ? rn / bn : rn;
+    for (int i = 0; i < 32; ++i) rep->history[i] = i <= steps ? hist[i] : 0.0;
     rep->seconds = ms * 1e-3;
   }
   if (bn > 0 && rn > 1e-8 * bn) {

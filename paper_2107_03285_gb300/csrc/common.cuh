@@ -47,6 +47,7 @@ struct Store {
   void *F = nullptr;        // fronts, column-major f x f each
   void *W = nullptr;        // W = L21 D workspace, f x panel per front
   double *rhs = nullptr;    // per-front solve buffers (f each)
+  double *yz = nullptr;     // per fully-summed DOF: y, then z = D^{-1} y, then v (solves)
   int32_t *piv_type = nullptr, *piv_perm = nullptr;  // per fully-summed DOF
   double *D0 = nullptr, *D1 = nullptr;
   const int64_t *front_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;

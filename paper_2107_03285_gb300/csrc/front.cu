@@ -453,79 +453,93 @@ __global__ void __launch_bounds__(64) k_fwd_permute(DevSym d, SV sv, const int32
   if (t < w) rhs[k + t] = y[t];
 }
 
+constexpr int SB = 128;  // solve block width (independent of the pivot panel width)
+
+// loads the strict lower triangle of the w x w diagonal block starting at
+// (k, k) into shared memory, Ld[t * (SB + 1) + c] = L(k + t, k + c), c < t
 template <typename T>
-__global__ void __launch_bounds__(64) k_fwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb) {
-  __shared__ double y[MAXNB];
-  const int s = fronts[blockIdx.x];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  const int64_t po = sv.piv_off[s] + k;
-  const int t = threadIdx.x;
-  (void)po;
-  if (t < w) y[t] = rhs[k + t];
-  __syncthreads();
-  for (int c = 0; c < w; ++c) {
-    double yc = y[c];
-    if (t > c && t < w) y[t] -= (double)F[(int64_t)(k + t) + (int64_t)(k + c) * f] * yc;
-    __syncthreads();
+__device__ __forceinline__ void load_diag_block(const T *__restrict__ F, int f, int k, int w, T *Ld) {
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    int c = idx / w, t = idx - c * w;
+    if (t > c) Ld[t * (SB + 1) + c] = F[(int64_t)(k + t) + (int64_t)(k + c) * f];
   }
-  if (t < w) rhs[k + t] = y[t];
 }
 
+// forward block step: y_b = L_bb^{-1} r_b (every CTA solves the small block
+// itself, so no second launch is needed), then r_i -= L_ib y_b for the rows
+// of this CTA's chunk.  CTA 0 records y_b.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int nb) {
-  __shared__ double y[MAXNB];
+__global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                    double *__restrict__ yz) {
+  extern __shared__ unsigned char smraw[];
+  T *Ld = reinterpret_cast<T *>(smraw);
+  __shared__ double y[SB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
   if (k >= ns) return;
   const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const int r0 = k + w;
-  const int nrows = f - r0;
-  if (blockIdx.x * 256 >= nrows) return;
+  const int w = min(SB, ns - k);
+  const int r0 = k + w, nrows = f - r0;
+  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= nrows) return;
   const T *F = (const T *)sv.F + sv.front_off[s];
   double *rhs = sv.rhs + sv.rhs_off[s];
-  if (threadIdx.x < w) y[threadIdx.x] = rhs[k + threadIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31;
+  load_diag_block<T>(F, f, k, w, Ld);
+  if (tid < w) y[tid] = rhs[k + tid];
   __syncthreads();
-  const int il = blockIdx.x * 256 + threadIdx.x;
-  if (il >= nrows) return;
-  const int64_t i = r0 + il;
-  double acc = 0.0;
-  for (int t = 0; t < w; ++t) acc = fma((double)F[i + (int64_t)(k + t) * f], y[t], acc);
-  rhs[i] -= acc;
+  for (int q = 0; q < w; q += 32) {
+    const int wq = min(32, w - q);
+    if (tid < 32) {
+      double yl = lane < wq ? y[q + lane] : 0.0;
+      for (int c = 0; c < wq; ++c) {
+        double yc = __shfl_sync(0xffffffffu, yl, c);
+        if (lane > c && lane < wq) yl -= (double)Ld[(q + lane) * (SB + 1) + q + c] * yc;
+      }
+      if (lane < wq) y[q + lane] = yl;
+    }
+    __syncthreads();
+    for (int t = q + wq + tid; t < w; t += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < wq; ++c) acc = fma((double)Ld[t * (SB + 1) + q + c], y[q + c], acc);
+      y[t] -= acc;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && tid < w) yz[sv.piv_off[s] + k + tid] = y[tid];
+  const int il = blockIdx.x * 256 + tid;
+  if (il < nrows) {
+    const int64_t i = r0 + il;
+    double acc = 0.0;
+    for (int t = 0; t < w; ++t) acc = fma((double)F[i + (int64_t)(k + t) * f], y[t], acc);
+    rhs[i] -= acc;
+  }
 }
 
-__global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts) {
+__global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts, double *__restrict__ yz) {
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ns) return;
-  double *rhs = sv.rhs + sv.rhs_off[s];
   const int64_t po = sv.piv_off[s];
+  double *z = yz + po;
   int ty = sv.piv_type[po + t];
   if (ty == 0) {
-    rhs[t] = rhs[t] / sv.D0[po + t];
+    z[t] = z[t] / sv.D0[po + t];
   } else if (ty == 1) {
     double d11 = sv.D0[po + t], d21 = sv.D1[po + t], d22 = sv.D0[po + t + 1];
     double det = d11 * d22 - d21 * d21;
-    double y1 = rhs[t], y2 = rhs[t + 1];
-    rhs[t] = (d22 * y1 - d21 * y2) / det;
-    rhs[t + 1] = (d11 * y2 - d21 * y1) / det;
+    double y1 = z[t], y2 = z[t + 1];
+    z[t] = (d22 * y1 - d21 * y2) / det;
+    z[t + 1] = (d11 * y2 - d21 * y1) / det;
   }
 }
 
-// v_own -= L21^T x_struct (warp per own column)
+// v_own = z_own - L21^T x_struct (warp per own column)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t *__restrict__ fronts,
-                                                   const double *__restrict__ sol) {
+                                                   const double *__restrict__ sol, double *__restrict__ yz) {
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int nown = d.sn_nown[s];
@@ -542,55 +556,60 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
     acc = fma((double)F[(int64_t)i + (int64_t)t * f], sol[(int64_t)sr[q] * dpn + kd], acc);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) sv.rhs[sv.rhs_off[s] + t] -= acc;
+  if (lane == 0) yz[sv.piv_off[s] + t] -= acc;
 }
 
+// backward block step: x_b = L_bb^{-T} v_b (solved by every CTA), CTA 0
+// scatters x_b (un-pivoted) into the solution, and each CTA subtracts
+// L_bc^T x_b from v_c for its chunk of earlier columns c < k
 template <typename T>
-__global__ void __launch_bounds__(64) k_bwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb,
-                                                  double *__restrict__ sol) {
-  __shared__ double v[MAXNB];
-  const int s = fronts[blockIdx.x];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  const int t = threadIdx.x;
-  if (t < w) v[t] = rhs[k + t];
-  __syncthreads();
-  for (int c = w - 1; c >= 0; --c) {
-    double xc = v[c];
-    if (t < c) v[t] -= (double)F[(int64_t)(k + c) + (int64_t)(k + t) * f] * xc;
-    __syncthreads();
-  }
-  if (t < w) {
-    rhs[k + t] = v[t];
-    const int64_t po = sv.piv_off[s] + k;
-    sol[(int64_t)d.sn_first[s] * dpn + k + sv.piv_perm[po + t]] = v[t];
-  }
-}
-
-// columns left of the panel: v[c] -= sum_t L(k+t, c) x_t (warp per column)
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int nb) {
+__global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                    double *__restrict__ yz, double *__restrict__ sol) {
+  extern __shared__ unsigned char smraw[];
+  T *Ld = reinterpret_cast<T *>(smraw);
+  __shared__ double x[SB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
   if (k >= ns) return;
-  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (c >= k) return;
   const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
+  const int w = min(SB, ns - k);
+  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= k) return;
   const T *F = (const T *)sv.F + sv.front_off[s];
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  double acc = 0.0;
-  for (int t = lane; t < w; t += 32) acc = fma((double)F[(int64_t)(k + t) + (int64_t)c * f], rhs[k + t], acc);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) rhs[c] -= acc;
+  const int64_t po = sv.piv_off[s];
+  double *v = yz + po;
+  const int tid = threadIdx.x, lane = tid & 31;
+  load_diag_block<T>(F, f, k, w, Ld);
+  if (tid < w) x[tid] = v[k + tid];
+  __syncthreads();
+  const int nq = (w + 31) / 32;
+  for (int qi = nq - 1; qi >= 0; --qi) {
+    const int q = qi * 32;
+    const int wq = min(32, w - q);
+    if (tid < 32) {
+      double xl = lane < wq ? x[q + lane] : 0.0;
+      for (int c = wq - 1; c >= 0; --c) {
+        double xc = __shfl_sync(0xffffffffu, xl, c);
+        if (lane < c) xl -= (double)Ld[(q + c) * (SB + 1) + q + lane] * xc;
+      }
+      if (lane < wq) x[q + lane] = xl;
+    }
+    __syncthreads();
+    for (int t = tid; t < q; t += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < wq; ++c) acc = fma((double)Ld[(q + c) * (SB + 1) + t], x[q + c], acc);
+      x[t] -= acc;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && tid < w) sol[(int64_t)d.sn_first[s] * dpn + k + sv.piv_perm[po + k + tid]] = x[tid];
+  const int col = blockIdx.x * 256 + tid;
+  if (col < k) {
+    double acc = 0.0;
+    const T *Fc = F + (int64_t)col * f + k;
+    for (int t = 0; t < w; ++t) acc = fma((double)Fc[t], x[t], acc);
+    v[col] -= acc;
+  }
 }
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
@@ -698,39 +717,38 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   SV sv = view(st);
   const int nb = c.S.opts.panel;
   const int dpn = st.dpn;
+  const size_t smem = (size_t)SB * (SB + 1) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_fwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+    cudaFuncSetAttribute(k_fwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+    cudaFuncSetAttribute(k_bwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+    cudaFuncSetAttribute(k_bwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+    attr_set = true;
+  }
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, dpn);
     int64_t n = (li.i1 - li.i0) * dpn;
     k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, li.i0, n, b);
     c.count();
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
+    const int nf = (int)(li.f1 - li.f0);
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
-    if (max_ns > 0) {
-      dim3 gp((max_ns + nb - 1) / nb, (unsigned)(li.f1 - li.f0));
-      k_fwd_permute<<<gp, 64, 0, c.stream>>>(c.ds, sv, fronts, nb);
-      c.count();
-    }
-    for (int k = 0; k < max_ns; k += nb) {
+    if (max_ns == 0) continue;
+    dim3 gp((max_ns + nb - 1) / nb, nf);
+    k_fwd_permute<<<gp, 64, 0, c.stream>>>(c.ds, sv, fronts, nb);
+    c.count();
+    for (int k = 0; k < max_ns; k += SB) {
       int na = n_active(li, k);
       int max_rows = 0;
-      for (int q = 0; q < na; ++q) {
-        int w = std::min(nb, li.ns[q] - k);
-        max_rows = std::max(max_rows, li.f[q] - k - w);
-      }
-      k_fwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+      for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - k - std::min(SB, li.ns[q] - k));
+      dim3 g(std::max(1, (max_rows + 255) / 256), na);
+      k_fwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
       c.count();
-      if (max_rows > 0) {
-        dim3 g((max_rows + 255) / 256, na);
-        k_fwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
-        c.count();
-      }
     }
-    int nf = (int)(li.f1 - li.f0);
     dim3 gd((max_ns + 255) / 256, nf);
-    if (max_ns > 0) {
-      k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts);
-      c.count();
-    }
+    k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts, st.yz);
+    c.count();
   }
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
     LevelInfo li = level_info(c, L, dpn);
@@ -739,18 +757,14 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     if (max_ns == 0) continue;
     dim3 gi((max_ns + 7) / 8, nf);
-    k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x);
+    k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x, st.yz);
     c.count();
-    int last = ((max_ns - 1) / nb) * nb;
-    for (int k = last; k >= 0; k -= nb) {
+    int last = ((max_ns - 1) / SB) * SB;
+    for (int k = last; k >= 0; k -= SB) {
       int na = n_active(li, k);
-      k_bwd_diag<T><<<na, 64, 0, c.stream>>>(c.ds, sv, fronts, k, nb, x);
+      dim3 g(std::max(1, (k + 255) / 256), na);
+      k_bwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, st.yz, x);
       c.count();
-      if (k > 0) {
-        dim3 g((k + 7) / 8, na);
-        k_bwd_update<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
-        c.count();
-      }
     }
   }
 }
