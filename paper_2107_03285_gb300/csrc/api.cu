@@ -48,7 +48,6 @@ struct Upload {
 };
 
 void store_offsets(Ctx &c, Store &s, int dpn) {
-  const int nb = c.S.opts.panel;
   s.dpn = dpn;
   const int n_sn = (int)c.S.sn.size();
   s.h_front_off.assign(n_sn, 0); s.h_w_off.assign(n_sn, 0);
@@ -57,7 +56,7 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   for (int i = 0; i < n_sn; ++i) {
     int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
     s.h_front_off[i] = fo; fo += f * f;
-    s.h_w_off[i] = wo; wo += f * nb;
+    s.h_w_off[i] = wo; wo += f * FACTOR_BLOCK;
     s.h_rhs_off[i] = ro; ro += f;
     s.h_piv_off[i] = po; po += ns;
   }

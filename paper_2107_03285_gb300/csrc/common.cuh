@@ -13,6 +13,11 @@
 
 namespace sgn {
 
+// outer block of the factorization: Bunch-Kaufman panels (width = the
+// setup's panel) are grouped into blocks of this many columns; the trailing
+// Schur update runs once per block with an inner dimension of this size
+constexpr int FACTOR_BLOCK = 256;
+
 // device status word bits (sticky until read by a synchronising call)
 enum : int {
   DEV_INVERTED = 1,
@@ -45,7 +50,7 @@ struct Store {
   bool kkt = true;          // saddle-point system (else K alone)
   bool fp32 = false;        // element type of the fronts
   void *F = nullptr;        // fronts, column-major f x f each
-  void *W = nullptr;        // W = L21 D workspace, f x panel per front
+  void *W = nullptr;        // W = L21 D workspace, (f - K0) x FACTOR_BLOCK per front
   double *rhs = nullptr;    // per-front solve buffers (f each)
   double *yz = nullptr;     // per fully-summed DOF: y, then z = D^{-1} y, then v (solves)
   int32_t *piv_type = nullptr, *piv_perm = nullptr;  // per fully-summed DOF

@@ -294,10 +294,11 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
   }
 }
 
-// rows below the panel: W = F21 P^T L11^{-T}, L21 = W D^{-1}
+// rows below the panel: W = F21 P^T L11^{-T}, L21 = W D^{-1}.  W is kept for
+// the whole outer block starting at K0: W[(i - K0) + (col - K0) * (f - K0)]
 template <typename T>
 __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int nb) {
+                                                     int nb, int K0) {
   extern __shared__ double smem[];
   double *Ls = smem;                     // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
   double *xs = smem + MAXNB * MAXNB;     // [MAXNB][128]
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   }
   for (int t = 0; t < w; ++t) {
     double xt = xs[t * 128 + tid];
-    W[il + (int64_t)t * nrows] = T(xt);
+    W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = T(xt);
     double l;
     if (stype[t] == 0) {
       l = xt / sD0[t];
@@ -350,30 +351,15 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   }
 }
 
-// F22 -= W L21^T on the lower triangle; 64 x 64 tiles, 4 x 4 per thread
+// C -= A B^T on a 64 x 64 output tile, 4 x 4 per thread, K staged in chunks
+// of 32: A(r, t) = A[r + t * lda] (r < ma), B(c, t) = B[c + t * ldb] (c < nbc);
+// only entries with row + roff >= col (lower triangle) are written
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                 int nb) {
-  constexpr int KC = 32;  // K chunk staged in shared memory
+__device__ __forceinline__ void tile_gemm_sub(T *C, int64_t ldc, const T *A, int64_t lda, int ma, const T *B,
+                                              int64_t ldb, int nbc, int kk, int roff) {
+  constexpr int KC = 32;
   __shared__ T As[KC][64];
   __shared__ T Bs[KC][64];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const int r0 = k + w;
-  const int nrows = f - r0;
-  const int nt = (nrows + 63) / 64;
-  const int tile = blockIdx.x;
-  if (tile >= nt * (nt + 1) / 2) return;
-  int bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-  while (bi * (bi + 1) / 2 > tile) --bi;
-  const int bj = tile - bi * (bi + 1) / 2;
-  T *F = (T *)sv.F + sv.front_off[s];
-  const T *W = (const T *)sv.W + sv.w_off[s];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   T acc[4][4];
@@ -381,14 +367,13 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
   for (int m = 0; m < 4; ++m)
 #pragma unroll
     for (int n = 0; n < 4; ++n) acc[m][n] = T(0);
-  for (int t0 = 0; t0 < w; t0 += KC) {
-    const int kc = min(KC, w - t0);
+  for (int t0 = 0; t0 < kk; t0 += KC) {
+    const int kc = min(KC, kk - t0);
     __syncthreads();
     for (int idx = tid; idx < kc * 64; idx += 256) {
       int t = idx >> 6, ii = idx & 63;
-      int ra = bi * 64 + ii, rb = bj * 64 + ii;
-      As[t][ii] = ra < nrows ? W[ra + (int64_t)(t0 + t) * nrows] : T(0);
-      Bs[t][ii] = rb < nrows ? F[(int64_t)(r0 + rb) + (int64_t)(k + t0 + t) * f] : T(0);
+      As[t][ii] = ii < ma ? A[ii + (int64_t)(t0 + t) * lda] : T(0);
+      Bs[t][ii] = ii < nbc ? B[ii + (int64_t)(t0 + t) * ldb] : T(0);
     }
     __syncthreads();
     for (int t = 0; t < kc; ++t) {
@@ -405,14 +390,64 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
   }
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
-    int jl = bj * 64 + ty + 16 * n;
-    if (jl >= nrows) continue;
+    int jl = ty + 16 * n;
+    if (jl >= nbc) continue;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      int il = bi * 64 + tx + 16 * m;
-      if (il < nrows && il >= jl) F[(int64_t)(r0 + il) + (int64_t)(r0 + jl) * f] -= acc[m][n];
+      int il = tx + 16 * m;
+      if (il < ma && il + roff >= jl) C[il + (int64_t)jl * ldc] -= acc[m][n];
     }
   }
+}
+
+// trailing update after the outer block [K0, kend):
+// F[kend:, kend:] -= W[kend:, block] L[kend:, block]^T (lower triangle)
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int K0,
+                                                 int NB) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (K0 >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int kend = min(K0 + NB, ns);
+  const int kw = kend - K0;
+  const int nrows = f - kend;
+  const int nt = (nrows + 63) / 64;
+  const int tile = blockIdx.x;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  while (bi * (bi + 1) / 2 > tile) --bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  T *F = (T *)sv.F + sv.front_off[s];
+  const T *W = (const T *)sv.W + sv.w_off[s];
+  const int64_t ldw = f - K0;
+  const int r = bi * 64, cc = bj * 64;
+  tile_gemm_sub<T>(F + (int64_t)(kend + r) + (int64_t)(kend + cc) * f, f, W + (kend - K0 + r), ldw,
+                   min(64, nrows - r), F + (int64_t)(kend + cc) + (int64_t)K0 * f, f, min(64, nrows - cc), kw,
+                   r - cc);
+}
+
+// left-looking update of the panel [k, k + w) by the earlier panels of its
+// outer block: F[k:, k:k+w] -= W[k:, K0:k] L[k:k+w, K0:k]^T (lower part)
+template <typename T>
+__global__ void __launch_bounds__(256) k_panel_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                       int K0, int nb) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const int nrows = f - k;
+  const int r = blockIdx.x * 64;
+  if (r >= nrows) return;
+  T *F = (T *)sv.F + sv.front_off[s];
+  const T *W = (const T *)sv.W + sv.w_off[s];
+  const int64_t ldw = f - K0;
+  tile_gemm_sub<T>(F + (int64_t)(k + r) + (int64_t)k * f, f, W + (k - K0 + r), ldw, min(64, nrows - r),
+                   F + (int64_t)k + (int64_t)K0 * f, f, w, k - K0, r);
 }
 
 // ------------------------------------------------------------------ solves
@@ -564,7 +599,7 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
 // L_bc^T x_b from v_c for its chunk of earlier columns c < k
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                    double *__restrict__ yz, double *__restrict__ sol) {
+                                                    int nb, double *__restrict__ yz, double *__restrict__ sol) {
   extern __shared__ unsigned char smraw[];
   T *Ld = reinterpret_cast<T *>(smraw);
   __shared__ double x[SB];
@@ -602,7 +637,11 @@ __global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && tid < w) sol[(int64_t)d.sn_first[s] * dpn + k + sv.piv_perm[po + k + tid]] = x[tid];
+  if (blockIdx.x == 0 && tid < w) {
+    // piv_perm is local to the pivot panel (width nb) holding position k + tid
+    const int pos = k + tid, pstart = (pos / nb) * nb;
+    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = x[tid];
+  }
   const int col = blockIdx.x * 256 + tid;
   if (col < k) {
     double acc = 0.0;
@@ -681,31 +720,46 @@ void factor_impl(Ctx &c, Store &st) {
     c.count();
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
-    for (int k = 0; k < max_ns; k += nb) {
-      int na = n_active(li, k);
-      int max_rows = 0;
-      for (int q = 0; q < na; ++q) {
-        int w = std::min(nb, li.ns[q] - k);
-        max_rows = std::max(max_rows, li.f[q] - k - w);
+    for (int K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
+      const int kstop = std::min(K0 + FACTOR_BLOCK, max_ns);
+      for (int k = K0; k < kstop; k += nb) {
+        int na = n_active(li, k);
+        int max_rows = 0, max_f = 0;
+        for (int q = 0; q < na; ++q) {
+          int w = std::min(nb, li.ns[q] - k);
+          max_rows = std::max(max_rows, li.f[q] - k - w);
+          max_f = std::max(max_f, li.f[q] - k);
+        }
+        if (k > K0) {
+          dim3 gp((max_f + 63) / 64, na);
+          k_panel_update<T><<<gp, 256, 0, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
+          c.count();
+        }
+        k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
+        c.count();
+        if (max_rows > 0) {
+          dim3 gt((max_rows + 127) / 128, na);
+          k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb, K0);
+          c.count();
+        }
       }
-      k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
-      c.count();
+      int na = n_active(li, K0);
+      int max_rows = 0;
+      for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - std::min(K0 + FACTOR_BLOCK, li.ns[q]));
       if (max_rows > 0) {
-        dim3 gt((max_rows + 127) / 128, na);
-        k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb);
         int nt = (max_rows + 63) / 64;
         dim3 gu(nt * (nt + 1) / 2, na);
         cudaEvent_t *ev = c.prof_pair();
         if (ev) {
           cudaEventRecord(ev[0], c.stream);
           for (int q = 0; q < na; ++q) {
-            double w = std::min(nb, li.ns[q] - k), nr = li.f[q] - k - w;
-            c.prof_flops += nr * (nr + 1.0) * w;  // 2 flops x lower triangle x w
+            double kend = std::min(K0 + FACTOR_BLOCK, li.ns[q]), nr = li.f[q] - kend;
+            c.prof_flops += nr * (nr + 1.0) * (kend - K0);  // 2 flops x lower triangle x k
           }
         }
-        k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, k, nb);
+        k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
         if (ev) cudaEventRecord(ev[1], c.stream);
-        c.count(2);
+        c.count();
       }
     }
   }
@@ -763,7 +817,7 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     for (int k = last; k >= 0; k -= SB) {
       int na = n_active(li, k);
       dim3 g(std::max(1, (k + 255) / 256), na);
-      k_bwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, st.yz, x);
+      k_bwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
       c.count();
     }
   }
