@@ -247,6 +247,18 @@ def main():
         torch.distributed.barrier()
     value = ws * 1e3 / ms
     dp = out[1].clone()
+    # phase breakdown of one extra step (events between the C-ABI calls)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    s.assemble(xeq, p)
+    ev[1].record()
+    s.factor(prec, report=False)
+    ev[2].record()
+    s.solve(P.RHS_KKT, report=False, out=out)
+    ev[3].record()
+    torch.cuda.synchronize()
+    phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "factor_ms": ev[1].elapsed_time(ev[2]),
+              "solve_ms": ev[2].elapsed_time(ev[3])}
     dp_err = float(torch.linalg.norm(dp - dp64) / torch.linalg.norm(dp64)) if dp64 is not None else None
     _, _, _, srep = s.solve(P.RHS_KKT, report=True, out=out)
 
@@ -296,7 +308,7 @@ def main():
                    "refine_history": [float(v) for v in list(srep.history)[:srep.refine_steps + 1]],
                    "factor_flops": info.factor_flops,
                    "nnz_factor": info.nnz_factor, "fp64_path": fp64,
-                   "setup_s": info.setup_seconds, "bind_s": t_setup,
+                   "phases": phases, "setup_s": info.setup_seconds, "bind_s": t_setup,
                    "equilibrium": {"iters": nrep.iters, "residual": nrep.residual, "seconds": nrep.seconds}},
         "roofline": roofline,
         "cpu_baseline": cpu_info,

@@ -52,15 +52,25 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   const int n_sn = (int)c.S.sn.size();
   s.h_front_off.assign(n_sn, 0); s.h_w_off.assign(n_sn, 0);
   s.h_rhs_off.assign(n_sn, 0); s.h_piv_off.assign(n_sn, 0);
-  int64_t fo = 0, wo = 0, ro = 0, po = 0;
+  int64_t fo = 0, ro = 0, po = 0;
   for (int i = 0; i < n_sn; ++i) {
     int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
     s.h_front_off[i] = fo; fo += f * f;
-    s.h_w_off[i] = wo; wo += f * FACTOR_BLOCK;
     s.h_rhs_off[i] = ro; ro += f;
     s.h_piv_off[i] = po; po += ns;
   }
-  s.front_elems = fo; s.w_elems = wo; s.rhs_elems = ro; s.piv_elems = po;
+  // W (= L21 D of the current outer block) is only live while its level is
+  // factored, so all levels share one workspace sized for the largest level
+  int64_t wmax = 0;
+  for (const auto &lv : c.S.level_fronts) {
+    int64_t wo = 0;
+    for (int i : lv) {
+      s.h_w_off[i] = wo;
+      wo += (int64_t)c.S.sn[i].fnodes() * dpn * FACTOR_BLOCK;
+    }
+    wmax = std::max(wmax, wo);
+  }
+  s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po;
 }
 
 // lays out (base == nullptr: only measures) every device array
@@ -400,7 +410,7 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   solve_store(c, st, red_b, red_x);
   launch_recover(c, red_x, c.bp, c.zx, c.zp, c.zl);
   double bn = std::sqrt(device_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx));
-  double rn = 0.0;
+  double rn = 0.0, rn_prev = 0.0;
   int steps = 0;
   double hist[32];
   for (;;) {
@@ -409,6 +419,9 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     if (steps < 32) hist[steps] = bn > 0 ? rn / bn : rn;
     if (!(rn == rn)) { h->last_error = "non-finite residual"; return SGN_ENONFINITE; }
     if (rn <= tol * bn || steps >= max_refine) break;
+    // stagnation at round-off level: the FP64 residual cannot fall further
+    if (steps > 0 && rn > 0.5 * rn_prev && rn <= 1e-11 * bn) break;
+    rn_prev = rn;
     launch_reduce_rhs(c, c.rx, c.rp, c.rl, red_b, 2 * c.S.dim);
     solve_store(c, st, red_b, red_x);
     // d = M^{-1} r, recovered into (rx, rp, rl) scratch then added
