@@ -56,13 +56,15 @@ typedef enum {
   SGN_EPIVOT = 6,     /* a pivot had to be perturbed and refinement did not recover */
   SGN_EREFINE = 7,    /* iterative refinement did not reach its tolerance */
   SGN_ESTATE = 8,     /* call out of order (e.g. solve before factor) */
-  SGN_ENONFINITE = 9  /* a NaN or Inf reached a reduction */
+  SGN_ENONFINITE = 9, /* a NaN or Inf reached a reduction */
+  SGN_ETIMEOUT = 10   /* a bounded device-side wait expired (reported, never hangs) */
 } sgn_status;
 
 /* Precisions of the numeric factorization (sgn_factor). */
 typedef enum {
   SGN_FP64 = 0,       /* fronts, pivots and Schur updates in FP64 (DFMA) */
-  SGN_MIXED = 1       /* fronts in FP32 with FP32 Schur updates; FP64 pivot
+  SGN_MIXED = 1       /* fronts in FP32; Schur updates on the tcgen05 tensor cores
+                         as 3xTF32 products with FP32 accumulation; FP64 pivot
                          decisions, FP64 residuals and FP64 refinement */
 } sgn_precision;
 
@@ -126,6 +128,7 @@ typedef struct {
   int64_t n_2x2;                  /* 2x2 Bunch-Kaufman pivots */
   int64_t n_perturbed;            /* pivots replaced by the static-pivot threshold */
   double seconds;                 /* device time of the factorization */
+  int64_t tensor_core_updates;    /* trailing-update launches on the tcgen05 tensor cores */
 } sgn_factor_report;
 
 typedef struct {

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsgn.so")
 
 # status codes (sgn_status)
-OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINITE = range(10)
+OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINITE, ETIMEOUT = range(11)
 FP64, MIXED = 0, 1
 RHS_KKT, RHS_PAPER = 0, 1
 STORE_FP64, STORE_MIXED, STORE_KFACT = 1, 2, 4
@@ -53,7 +53,8 @@ class Info(C.Structure):
 
 class FactorReport(C.Structure):
     _fields_ = [("n_pos", C.c_int64), ("n_neg", C.c_int64), ("n_zero", C.c_int64),
-                ("n_2x2", C.c_int64), ("n_perturbed", C.c_int64), ("seconds", C.c_double)]
+                ("n_2x2", C.c_int64), ("n_perturbed", C.c_int64), ("seconds", C.c_double),
+                ("tensor_core_updates", C.c_int64)]
 
 
 class SolveOpts(C.Structure):

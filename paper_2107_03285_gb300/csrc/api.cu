@@ -4,12 +4,14 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
+#include "tc_update.cuh"
 
 using namespace sgn;
 
@@ -161,6 +163,10 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     s.piv_type = cv.take<int32_t>(s.piv_elems); s.piv_perm = cv.take<int32_t>(s.piv_elems);
     s.D0 = cv.take<double>(s.piv_elems); s.D1 = cv.take<double>(s.piv_elems);
     s.yz = cv.take<double>(s.piv_elems);
+    if (fp32) {
+      for (int q = 0; q < 4; ++q) s.wk[q] = cv.take<float>(s.w_elems);
+      s.maps = cv.take<char>(S.sn.size() * sizeof(tc::Maps));
+    }
     int64_t *p;
     st_up(p, s.h_front_off); s.front_off = p;
     st_up(p, s.h_w_off); s.w_off = p;
@@ -173,6 +179,39 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   return cv.off + 256;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA tensor maps of the four K-major operand arrays of every front: rows =
+// the front's rows, 256 K columns (1 KB rows), box 32 x 128 with 128B swizzle,
+// out-of-range rows read as zero
+bool encode_maps(Ctx &c, Store &st, std::vector<tc::Maps> &out) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  EncodeTiledFn enc = (EncodeTiledFn)fn;
+  out.assign(c.S.sn.size(), tc::Maps());
+  for (size_t i = 0; i < c.S.sn.size(); ++i) {
+    const cuuint64_t f = (cuuint64_t)c.S.sn[i].fnodes() * st.dpn;
+    cuuint64_t dims[2] = {(cuuint64_t)FACTOR_BLOCK, f};
+    cuuint64_t strides[1] = {(cuuint64_t)FACTOR_BLOCK * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)tc::TILE};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMap *m[4] = {&out[i].whi, &out[i].wlo, &out[i].lhi, &out[i].llo};
+    for (int k = 0; k < 4; ++k) {
+      void *addr = st.wk[k] + st.h_w_off[i];
+      CUresult r = enc(m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return false;
+    }
+  }
+  return true;
+}
+
 sgn_status check_status(sgn_ctx *h) {
   int st = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -180,6 +219,7 @@ sgn_status check_status(sgn_ctx *h) {
   if (st) {
     CUDA_TRY(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     if (st & DEV_INVERTED) { h->last_error = "inverted element (det F <= 0)"; return SGN_EINVERTED; }
+    if (st & DEV_TIMEOUT) { h->last_error = "a bounded device wait expired"; return SGN_ETIMEOUT; }
     h->last_error = "non-finite value in element evaluation";
     return SGN_ENONFINITE;
   }
@@ -211,6 +251,7 @@ const char *sgn_strerror(sgn_status s) {
     case SGN_EREFINE: return "iterative refinement did not reach its tolerance";
     case SGN_ESTATE: return "call out of order";
     case SGN_ENONFINITE: return "non-finite value";
+    case SGN_ETIMEOUT: return "a bounded device-side wait expired";
   }
   return "unknown status";
 }
@@ -287,6 +328,15 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   h->base = (char *)dev_buf;
   h->bytes = bytes;
   carve(*h, h->base, stores, &ups);
+  std::vector<tc::Maps> maps;
+  if (h->kkt32.enabled) {
+    h->kkt32.tc = false;
+    const char *off = getenv("SGN_DISABLE_TC");
+    if (!(off && off[0] == '1') && encode_maps(*h, h->kkt32, maps)) {
+      ups.push_back({h->kkt32.maps, maps.data(), maps.size() * sizeof(tc::Maps)});
+      h->kkt32.tc = true;
+    }
+  }
   for (auto &u : ups) CUDA_TRY(h, cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
   // uploads read host vectors owned by h->S or by the carve's thread-local
@@ -353,6 +403,7 @@ sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *rep) {
     CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
     CUDA_TRY(h, cudaEventRecord(e0, h->stream));
   }
+  const int64_t tc0 = h->tc_launches;
   factor_store(*h, st);
   h->active = &st;
   sgn_status s = launch_check(h);
@@ -370,6 +421,7 @@ sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *rep) {
     rep->n_pos = ctr[2] + h->S.n_elem;  // p pivots: C = alpha I > 0
     rep->n_neg = ctr[3]; rep->n_zero = ctr[4];
     rep->seconds = ms * 1e-3;
+    rep->tensor_core_updates = h->tc_launches - tc0;
     s = check_status(h);
     if (s != SGN_OK) return s;
   }

@@ -22,6 +22,7 @@ constexpr int FACTOR_BLOCK = 256;
 enum : int {
   DEV_INVERTED = 1,
   DEV_NONFINITE = 2,
+  DEV_TIMEOUT = 4,   // a bounded device-side wait expired
 };
 
 // device views of the static symbolic data
@@ -51,6 +52,12 @@ struct Store {
   bool fp32 = false;        // element type of the fronts
   void *F = nullptr;        // fronts, column-major f x f each
   void *W = nullptr;        // W = L21 D workspace, (f - K0) x FACTOR_BLOCK per front
+  // FP32 fronts only: K-major copies of W and L21 of the current outer block,
+  // split as hi (TF32-exact) + lo, rows = absolute front rows, for the
+  // tensor-core trailing update; and one set of TMA tensor maps per front
+  float *wk[4] = {nullptr, nullptr, nullptr, nullptr};  // Whi, Wlo, Lhi, Llo
+  void *maps = nullptr;
+  bool tc = false;          // tensor-core trailing update available
   double *rhs = nullptr;    // per-front solve buffers (f each)
   double *yz = nullptr;     // per fully-summed DOF: y, then z = D^{-1} y, then v (solves)
   int32_t *piv_type = nullptr, *piv_perm = nullptr;  // per fully-summed DOF
@@ -111,6 +118,7 @@ struct Ctx {
 
   // measurement support
   int64_t launches = 0;
+  int64_t tc_launches = 0;          // tensor-core trailing-update launches
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
   int64_t prof_used = 0;              // events used (2 per launch)

@@ -20,8 +20,10 @@
 // nonsingular; hence each panel's trailing block is nonsingular too.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "common.cuh"
+#include "tc_update.cuh"
 
 namespace sgn {
 
@@ -32,6 +34,7 @@ constexpr int MAXNB = 64;
 struct SV {  // store view passed to kernels
   void *F;
   void *W;
+  float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
   double *rhs;
   int32_t *piv_type, *piv_perm;
   double *D0, *D1;
@@ -42,7 +45,8 @@ struct SV {  // store view passed to kernels
 
 SV view(Store &s) {
   SV v;
-  v.F = s.F; v.W = s.W; v.rhs = s.rhs; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
+  v.F = s.F; v.W = s.W; v.rhs = s.rhs;
+  v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
   return v;
@@ -348,6 +352,20 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
       l = (xt * sD0[t - 1] - xs[(t - 1) * 128 + tid] * sD1[t - 1]) / det;
     }
     F[i + (int64_t)(k + t) * f] = T(l);
+    if (sv.wk0) {
+      const int64_t o = sv.w_off[s] + i * FACTOR_BLOCK + (k - K0 + t);
+      const float wf = (float)xt, lf = (float)T(l);
+      const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
+      sv.wk0[o] = wh; sv.wk1[o] = wf - wh; sv.wk2[o] = lh; sv.wk3[o] = lf - lh;
+    }
+  }
+  if (sv.wk0 && k + w == ns) {
+    // last panel of the front: zero the K columns up to the next 32 boundary
+    const int pad_end = ((k - K0 + w + 31) / 32) * 32 - (k - K0);
+    for (int t = w; t < pad_end; ++t) {
+      const int64_t o = sv.w_off[s] + i * FACTOR_BLOCK + (k - K0 + t);
+      sv.wk0[o] = 0.f; sv.wk1[o] = 0.f; sv.wk2[o] = 0.f; sv.wk3[o] = 0.f;
+    }
   }
 }
 
@@ -427,6 +445,32 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
   tile_gemm_sub<T>(F + (int64_t)(kend + r) + (int64_t)(kend + cc) * f, f, W + (kend - K0 + r), ldw,
                    min(64, nrows - r), F + (int64_t)(kend + cc) + (int64_t)K0 * f, f, min(64, nrows - cc), kw,
                    r - cc);
+}
+
+// tensor-core version of k_update for FP32 fronts: 128 x 128 tiles of the
+// lower triangle, 3xTF32 products accumulated in TMEM
+__global__ void __launch_bounds__(tc::THREADS, 1) k_update_tc(DevSym d, SV sv, const int32_t *__restrict__ fronts,
+                                                               int K0, int NB, const tc::Maps *__restrict__ maps,
+                                                               int *status) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (K0 >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int kend = min(K0 + NB, ns);
+  const int nrows = f - kend;
+  const int nt = (nrows + tc::TILE - 1) / tc::TILE;
+  const int tile = blockIdx.x;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  while (bi * (bi + 1) / 2 > tile) --bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  const int r = bi * tc::TILE, cc = bj * tc::TILE;
+  float *F = (float *)sv.F + sv.front_off[s];
+  tc::tile_update_tc(&maps[s], F + (int64_t)(kend + r) + (int64_t)(kend + cc) * f, f, min(tc::TILE, nrows - r),
+                     min(tc::TILE, nrows - cc), r - cc, kend + r, kend + cc, (kend - K0 + 31) / 32, status,
+                     DEV_TIMEOUT);
 }
 
 // left-looking update of the panel [k, k + w) by the earlier panels of its
@@ -708,6 +752,7 @@ void factor_impl(Ctx &c, Store &st) {
   if (!attr_set) {
     cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
     cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+    cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
     attr_set = true;
   }
   for (int L = 0; L < c.S.n_levels; ++L) {
@@ -757,7 +802,15 @@ void factor_impl(Ctx &c, Store &st) {
             c.prof_flops += nr * (nr + 1.0) * (kend - K0);  // 2 flops x lower triangle x k
           }
         }
-        k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
+        if (std::is_same<T, float>::value && st.tc) {
+          int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
+          dim3 gtc(nt128 * (nt128 + 1) / 2, na);
+          k_update_tc<<<gtc, tc::THREADS, tc::SMEM_BYTES, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK,
+                                                                       (const tc::Maps *)st.maps, c.status);
+          c.tc_launches++;
+        } else {
+          k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
+        }
         if (ev) cudaEventRecord(ev[1], c.stream);
         c.count();
       }

@@ -1,0 +1,242 @@
+// Front Schur update on the 5th-generation tensor cores (sm_103a):
+//     C[kend:, kend:] -= W L^T      (lower triangle, FP32 fronts)
+// where W = L21 D and L = L21 of one outer block (inner dimension <= 256).
+//
+// Each CTA owns one 128 x 128 output tile.  W and L are kept in K-major
+// global arrays split as x = hi + lo with hi = x with its low 13 mantissa bits
+// cleared (exactly representable in TF32) and lo = x - hi; the tile is
+// accumulated in TMEM (FP32) as Whi Lhi^T + Whi Llo^T + Wlo Lhi^T
+// ("3xTF32"), which keeps FP32-level accuracy on the TF32 tensor path.
+//
+//   warp 0 / lane 0 : TMA producer  (cp.async.bulk.tensor, 128B swizzle)
+//   warp 1 / lane 0 : MMA issuer    (tcgen05.mma.cta_group::1.kind::tf32)
+//   warps 0..3      : epilogue      (tcgen05.ld 32x32b, C -= D in global)
+// Every mbarrier wait is bounded; on expiry the CTA records DEV_TIMEOUT in
+// the status word, drains the copies it issued (bounded again), frees its
+// TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cstdint>
+
+namespace sgn {
+namespace tc {
+
+constexpr int TILE = 128;          // output tile (M = N)
+constexpr int KCH = 32;            // K per stage: 32 FP32 = one 128-byte swizzle row
+constexpr int STAGES = 2;
+constexpr int TILE_BYTES = TILE * KCH * 4;           // 16 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // Whi, Wlo, Lhi, Llo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr int THREADS = 128;
+constexpr long long WAIT_CYCLES = 1ll << 31;         // ~1 s at 2 GHz
+
+struct Maps {                      // one set of tensor maps per front
+  CUtensorMap whi, wlo, lhi, llo;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false (and DEV_TIMEOUT recorded) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, int flag) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicOr(status, flag);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128B swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B TF32, both K-major, M = N = 128
+__host__ __device__ constexpr uint32_t idesc_tf32_128x128() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TILE >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// the hi / lo split used for the 3xTF32 products
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// One 128 x 128 tile of C -= W L^T.
+//   C      : column-major, leading dimension ldc, tile origin already applied
+//   rows   : valid rows of the tile (<= 128), cols: valid columns
+//   roff   : global row offset minus global column offset of the tile origin
+//            (only entries with row + roff >= col are written: lower triangle)
+//   r0, c0 : row coordinates of the W and L tiles in their tensor maps
+//   kchunks: number of 32-wide K chunks (zero-padded beyond the true K)
+__device__ __forceinline__ void tile_update_tc(const Maps *maps, float *C, int64_t ldc, int rows, int cols, int roff,
+                                               int r0, int c0, int kchunks, int *status, int flag_timeout) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TILE)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->whi) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->wlo) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->lhi) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->llo) : "memory");
+    int issued = 0;
+    for (int kc = 0; kc < kchunks; ++kc) {
+      const int s = kc % STAGES;
+      if (kc >= STAGES) {
+        if (!mbar_wait(&empty_bar[s], ((kc / STAGES) - 1) & 1, status, flag_timeout)) { abort_flag = 1; break; }
+      }
+      if (*(volatile int *)&abort_flag) break;
+      unsigned char *st = sm + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      tma_load_2d(st + 0 * TILE_BYTES, &maps->whi, &full_bar[s], kc * KCH, r0);
+      tma_load_2d(st + 1 * TILE_BYTES, &maps->wlo, &full_bar[s], kc * KCH, r0);
+      tma_load_2d(st + 2 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, c0);
+      tma_load_2d(st + 3 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, c0);
+      ++issued;
+    }
+    // drain: every issued stage must have landed before the CTA may exit
+    for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
+      mbar_wait(&full_bar[kc % STAGES], (kc / STAGES) & 1, status, flag_timeout);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_tf32_128x128();
+    uint32_t acc = 0;
+    bool ok = true;
+    for (int kc = 0; kc < kchunks; ++kc) {
+      const int s = kc % STAGES;
+      if (!mbar_wait(&full_bar[s], (kc / STAGES) & 1, status, flag_timeout)) { ok = false; abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(sm + s * STAGE_BYTES);
+#pragma unroll
+      for (int k = 0; k < KCH / 8; ++k) {
+        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along the swizzled row
+        const uint64_t ahi = umma_desc_sw128(base + 0 * TILE_BYTES + off);
+        const uint64_t alo = umma_desc_sw128(base + 1 * TILE_BYTES + off);
+        const uint64_t bhi = umma_desc_sw128(base + 2 * TILE_BYTES + off);
+        const uint64_t blo = umma_desc_sw128(base + 3 * TILE_BYTES + off);
+        umma_tf32(tmem, ahi, bhi, idesc, acc);
+        acc = 1;
+        umma_tf32(tmem, ahi, blo, idesc, 1);
+        umma_tf32(tmem, alo, bhi, idesc, 1);
+      }
+      umma_commit(&empty_bar[s]);  // frees the stage once these MMAs complete
+    }
+    if (ok && kchunks > 0) umma_commit(&done_bar);
+    else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&done_bar)) : "memory");
+  }
+  __syncwarp();
+  // ---- epilogue: all four warps, warp w owns TMEM lanes 32w .. 32w + 31
+  const bool done_ok = mbar_wait(&done_bar, 0, status, flag_timeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done_ok && kchunks > 0 && !*(volatile int *)&abort_flag) {
+    const int r = warp * 32 + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < TILE; cb += 32) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (r < rows) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int cc = cb + j;
+          if (cc < cols && r + roff >= cc) C[r + (int64_t)cc * ldc] -= __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
+  }
+}
+
+}  // namespace tc
+}  // namespace sgn
