@@ -227,7 +227,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    s.profile(True)
+    s.profile(1)  # time the dominant kernel kind (trailing update) live
     launches0 = s.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -237,8 +237,8 @@ def main():
         e1.record()
         torch.cuda.synchronize()
     launches = s.launch_count() - launches0
-    prof = s.profile_read()
-    s.profile(False)
+    prof_launches, prof_seconds, prof_flops = s.profile_read()["update"]
+    s.profile(0)
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -247,7 +247,8 @@ def main():
         torch.distributed.barrier()
     value = ws * 1e3 / ms
     dp = out[1].clone()
-    # phase breakdown of one extra step (events between the C-ABI calls)
+    # phase and per-kernel-kind breakdown of one extra (profiled) step
+    s.profile(0xFF)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     s.assemble(xeq, p)
@@ -259,6 +260,9 @@ def main():
     torch.cuda.synchronize()
     phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "factor_ms": ev[1].elapsed_time(ev[2]),
               "solve_ms": ev[2].elapsed_time(ev[3])}
+    kinds = {k: {"launches": v[0], "ms": 1e3 * v[1], "tflops": (v[2] / v[1] / 1e12) if v[1] > 0 and v[2] > 0 else None}
+             for k, v in s.profile_read().items() if v[0] > 0}
+    s.profile(0)
     dp_err = float(torch.linalg.norm(dp - dp64) / torch.linalg.norm(dp64)) if dp64 is not None else None
     _, _, _, srep = s.solve(P.RHS_KKT, report=True, out=out)
 
@@ -283,14 +287,14 @@ def main():
         return
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
     fp32 = prec == P.MIXED
-    achieved = prof.flops / prof.seconds / 1e12 if prof.seconds > 0 else None
+    achieved = prof_flops / prof_seconds / 1e12 if prof_seconds > 0 else None
     peak = FP32_SIMT_TFLOPS if fp32 else FP64_TFLOPS
     roofline = {"kernel": "k_update (front Schur update, " + ("FP32 SIMT" if fp32 else "FP64 DFMA") + ")",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "peak_source": "measured FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)",
-                "launches_per_step": prof.launches / args.steps,
-                "share_of_step": prof.seconds / (ms * 1e-3 * args.steps)}
+                "launches_per_step": prof_launches / args.steps,
+                "share_of_step": prof_seconds / (ms * 1e-3 * args.steps)}
     cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
     cpu_info["value"] = cpu_rate
     cpu_info["unit"] = UNIT
@@ -308,7 +312,7 @@ def main():
                    "refine_history": [float(v) for v in list(srep.history)[:srep.refine_steps + 1]],
                    "factor_flops": info.factor_flops,
                    "nnz_factor": info.nnz_factor, "fp64_path": fp64,
-                   "phases": phases, "setup_s": info.setup_seconds, "bind_s": t_setup,
+                   "phases": phases, "kernel_kinds_profiled_step": kinds, "setup_s": info.setup_seconds, "bind_s": t_setup,
                    "equilibrium": {"iters": nrep.iters, "residual": nrep.residual, "seconds": nrep.seconds}},
         "roofline": roofline,
         "cpu_baseline": cpu_info,

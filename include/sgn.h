@@ -229,19 +229,30 @@ sgn_status sgn_gradient(sgn_t h, double *g_d);
 sgn_status sgn_factor_k(sgn_t h);
 
 /* ---- measurement support (no counterpart in the paper) ------------------
- * sgn_profile(h, 1) resets and enables CUDA-event timing of every launch of
- * the front Schur-update kernel (the dominant kernel of sgn_factor) on the
- * context's stream; sgn_profile(h, 0) disables it.  sgn_profile_read
- * synchronises and returns the launches, summed device seconds and summed
- * algorithmic flops (2 * rows * cols * k per lower-triangle update) since
- * the last reset. */
+ * sgn_profile(h, mask) resets the per-kernel timers and enables CUDA-event
+ * timing (on the context's stream) of every launch of the kernel kinds whose
+ * bit is set in mask (mask = 0 disables).  sgn_profile_read synchronises and
+ * fills out[k] for kind k < n: launches, summed device seconds, and summed
+ * algorithmic flops (trailing and panel updates: 2 * rows * cols * inner
+ * dimension of the lower-triangle update; 0 for the other kinds). */
+enum {
+  SGN_PROF_UPDATE = 0,          /* trailing Schur update of an outer block (dominant) */
+  SGN_PROF_PANEL_UPDATE = 1,    /* left-looking update of a pivot panel */
+  SGN_PROF_PIVOT = 2,           /* Bunch-Kaufman factorization of a panel's diagonal block */
+  SGN_PROF_TRSM = 3,            /* L21 / W of a panel */
+  SGN_PROF_FRONT_ASSEMBLY = 4,  /* front assembly (original entries + children) */
+  SGN_PROF_ELEMENTS = 5,        /* element evaluation and block gather */
+  SGN_PROF_SOLVE = 6,           /* forward / diagonal / backward substitution */
+  SGN_PROF_VECTOR = 7,          /* right-hand sides, p elimination, residuals, reductions */
+  SGN_PROF_KINDS = 8
+};
 typedef struct {
   int64_t launches;
   double seconds;
   double flops;
 } sgn_kernel_profile;
-sgn_status sgn_profile(sgn_t h, int32_t enable);
-sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *update_kernel);
+sgn_status sgn_profile(sgn_t h, int32_t mask);
+sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out, int32_t n);
 /* Number of CUDA kernels this context has launched since sgn_bind. */
 int64_t sgn_launch_count(sgn_t h);
 

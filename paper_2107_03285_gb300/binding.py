@@ -20,6 +20,7 @@ OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINI
 FP64, MIXED = 0, 1
 RHS_KKT, RHS_PAPER = 0, 1
 STORE_FP64, STORE_MIXED, STORE_KFACT = 1, 2, 4
+PROF_KINDS = ["update", "panel_update", "pivot", "trsm", "front_assembly", "elements", "solve", "vector"]
 
 EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
@@ -103,7 +104,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_factor_k": (C.c_int, [VP]),
         "sgn_export_kkt": (C.c_int, [VP, P(C.c_int64), P(C.c_int64), P(C.c_int64), dp]),
         "sgn_profile": (C.c_int, [VP, C.c_int32]),
-        "sgn_profile_read": (C.c_int, [VP, P(KernelProfile)]),
+        "sgn_profile_read": (C.c_int, [VP, P(KernelProfile), C.c_int32]),
         "sgn_launch_count": (C.c_int64, [VP]),
     }
     for name, (res, args) in sig.items():

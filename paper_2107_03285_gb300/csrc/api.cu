@@ -385,9 +385,15 @@ void sgn_destroy(sgn_t h) {
 sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d) {
   if (!h || !x_d || !p_d) return SGN_EINVAL;
   if (!h->bound || !h->have_objective) return SGN_ESTATE;
-  launch_elem_state(*h, x_d, p_d);
-  launch_slot_gather(*h, true);
-  launch_objective_terms(*h, x_d, p_d);
+  {
+    ProfScope ps(*h, SGN_PROF_ELEMENTS);
+    launch_elem_state(*h, x_d, p_d);
+    launch_slot_gather(*h, true);
+  }
+  {
+    ProfScope ps(*h, SGN_PROF_VECTOR);
+    launch_objective_terms(*h, x_d, p_d);
+  }
   h->assembled = true;
   h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
   return launch_check(h);
@@ -578,26 +584,29 @@ sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows, int64_t *cols, d
   return SGN_OK;
 }
 
-sgn_status sgn_profile(sgn_t h, int32_t enable) {
+sgn_status sgn_profile(sgn_t h, int32_t mask) {
   if (!h) return SGN_EINVAL;
-  h->prof = enable != 0;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->prof_mask = mask;
   h->prof_used = 0;
-  h->prof_flops = 0.0;
+  h->prof_kind.clear();
+  h->prof_fl.clear();
   return SGN_OK;
 }
 
-sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out) {
-  if (!h || !out) return SGN_EINVAL;
+sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out, int32_t n) {
+  if (!h || !out || n < 0) return SGN_EINVAL;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  double s = 0.0;
-  for (int64_t i = 0; i + 1 < h->prof_used; i += 2) {
+  for (int k = 0; k < n; ++k) out[k] = sgn_kernel_profile{0, 0.0, 0.0};
+  for (int64_t i = 0; i < h->prof_used; ++i) {
+    int k = h->prof_kind[i];
+    if (k >= n) continue;
     float ms = 0.f;
-    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->prof_ev[i], h->prof_ev[i + 1]));
-    s += ms * 1e-3;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    out[k].launches += 1;
+    out[k].seconds += ms * 1e-3;
+    out[k].flops += h->prof_fl[i];
   }
-  out->launches = h->prof_used / 2;
-  out->seconds = s;
-  out->flops = h->prof_flops;
   return SGN_OK;
 }
 

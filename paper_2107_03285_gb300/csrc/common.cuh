@@ -119,14 +119,27 @@ struct Ctx {
   // measurement support
   int64_t launches = 0;
   int64_t tc_launches = 0;          // tensor-core trailing-update launches
-  bool prof = false;
-  std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
-  int64_t prof_used = 0;              // events used (2 per launch)
-  double prof_flops = 0.0;
+  int prof_mask = 0;
+  std::vector<cudaEvent_t> prof_ev; // pool; pairs (start, stop) in use order
+  std::vector<int> prof_kind;       // kind of each used pair
+  std::vector<double> prof_fl;      // flops of each used pair
+  int64_t prof_used = 0;            // pairs used
   std::string prof_err;
   void count(int n = 1) { launches += n; }
-  // returns the event pair to bracket one profiled launch (nullptr if off)
-  cudaEvent_t *prof_pair();
+  // event pair bracketing one launch of `kind` (nullptr if not profiled)
+  cudaEvent_t *prof_pair(int kind, double flops = 0.0);
+};
+
+// brackets the launches issued in its scope with a profiled event pair
+struct ProfScope {
+  Ctx &c;
+  cudaEvent_t *ev;
+  ProfScope(Ctx &ctx, int kind, double flops = 0.0) : c(ctx), ev(ctx.prof_pair(kind, flops)) {
+    if (ev) cudaEventRecord(ev[0], c.stream);
+  }
+  ~ProfScope() {
+    if (ev) cudaEventRecord(ev[1], c.stream);
+  }
 };
 
 // ---- launchers (assemble.cu)

@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
 // of 32: A(r, t) = A[r + t * lda] (r < ma), B(c, t) = B[c + t * ldb] (c < nbc);
 // only entries with row + roff >= col (lower triangle) are written
 template <typename T>
-__device__ __forceinline__ void tile_gemm_sub(T *C, int64_t ldc, const T *A, int64_t lda, int ma, const T *B,
+__device__ __forceinline__ void tile_gemm_sub(T *__restrict__ C, int64_t ldc, const T *__restrict__ A, int64_t lda,
+                                              int ma, const T *__restrict__ B,
                                               int64_t ldb, int nbc, int kk, int roff) {
   constexpr int KC = 32;
   __shared__ T As[KC][64];
@@ -406,14 +407,24 @@ __device__ __forceinline__ void tile_gemm_sub(T *C, int64_t ldc, const T *A, int
         for (int n = 0; n < 4; ++n) acc[m][n] = fma(av[m], bv[n], acc[m][n]);
     }
   }
+  // all 16 loads first, then the stores (distinct addresses)
+  T cur[4][4];
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
-    int jl = ty + 16 * n;
-    if (jl >= nbc) continue;
+    const int jl = ty + 16 * n;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      int il = tx + 16 * m;
-      if (il < ma && il + roff >= jl) C[il + (int64_t)jl * ldc] -= acc[m][n];
+      const int il = tx + 16 * m;
+      cur[m][n] = (jl < nbc && il < ma && il + roff >= jl) ? C[il + (int64_t)jl * ldc] : T(0);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int jl = ty + 16 * n;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int il = tx + 16 * m;
+      if (jl < nbc && il < ma && il + roff >= jl) C[il + (int64_t)jl * ldc] = cur[m][n] - acc[m][n];
     }
   }
 }
@@ -758,11 +769,14 @@ void factor_impl(Ctx &c, Store &st) {
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, st.dpn);
     int64_t nitems = li.i1 - li.i0;
-    if (D == 2)
-      k_front_assemble<T, 2><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-    else
-      k_front_assemble<T, 3><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-    c.count();
+    {
+      ProfScope ps(c, SGN_PROF_FRONT_ASSEMBLY);
+      if (D == 2)
+        k_front_assemble<T, 2><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      else
+        k_front_assemble<T, 3><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      c.count();
+    }
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     for (int K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
@@ -776,13 +790,23 @@ void factor_impl(Ctx &c, Store &st) {
           max_f = std::max(max_f, li.f[q] - k);
         }
         if (k > K0) {
+          double fl = 0.0;
+          for (int q = 0; q < na; ++q) {
+            double w = std::min(nb, li.ns[q] - k), nr = li.f[q] - k;
+            fl += 2.0 * (nr * w - w * (w - 1) / 2.0) * (k - K0);
+          }
+          ProfScope ps(c, SGN_PROF_PANEL_UPDATE, fl);
           dim3 gp((max_f + 63) / 64, na);
           k_panel_update<T><<<gp, 256, 0, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
           c.count();
         }
-        k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
-        c.count();
+        {
+          ProfScope ps(c, SGN_PROF_PIVOT);
+          k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
+          c.count();
+        }
         if (max_rows > 0) {
+          ProfScope ps(c, SGN_PROF_TRSM);
           dim3 gt((max_rows + 127) / 128, na);
           k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb, K0);
           c.count();
@@ -794,14 +818,12 @@ void factor_impl(Ctx &c, Store &st) {
       if (max_rows > 0) {
         int nt = (max_rows + 63) / 64;
         dim3 gu(nt * (nt + 1) / 2, na);
-        cudaEvent_t *ev = c.prof_pair();
-        if (ev) {
-          cudaEventRecord(ev[0], c.stream);
-          for (int q = 0; q < na; ++q) {
-            double kend = std::min(K0 + FACTOR_BLOCK, li.ns[q]), nr = li.f[q] - kend;
-            c.prof_flops += nr * (nr + 1.0) * (kend - K0);  // 2 flops x lower triangle x k
-          }
+        double fl = 0.0;
+        for (int q = 0; q < na; ++q) {
+          double kend = std::min(K0 + FACTOR_BLOCK, li.ns[q]), nr = li.f[q] - kend;
+          fl += nr * (nr + 1.0) * (kend - K0);  // 2 flops x lower triangle x k
         }
+        ProfScope ps(c, SGN_PROF_UPDATE, fl);
         if (std::is_same<T, float>::value && st.tc) {
           int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
           dim3 gtc(nt128 * (nt128 + 1) / 2, na);
@@ -811,7 +833,6 @@ void factor_impl(Ctx &c, Store &st) {
         } else {
           k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
         }
-        if (ev) cudaEventRecord(ev[1], c.stream);
         c.count();
       }
     }
@@ -821,6 +842,7 @@ void factor_impl(Ctx &c, Store &st) {
 
 template <typename T>
 void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
+  ProfScope ps(c, SGN_PROF_SOLVE);
   SV sv = view(st);
   const int nb = c.S.opts.panel;
   const int dpn = st.dpn;
@@ -878,17 +900,19 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
 
 }  // namespace
 
-cudaEvent_t *Ctx::prof_pair() {
-  if (!prof) return nullptr;
-  if (prof_used + 2 > (int64_t)prof_ev.size()) {
-    for (int i = 0; i < 256; ++i) {
+cudaEvent_t *Ctx::prof_pair(int kind, double flops) {
+  if (!((prof_mask >> kind) & 1)) return nullptr;
+  if (2 * (prof_used + 1) > (int64_t)prof_ev.size()) {
+    for (int i = 0; i < 512; ++i) {
       cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) { prof = false; prof_err = "event pool"; return nullptr; }
+      if (cudaEventCreate(&e) != cudaSuccess) { prof_mask = 0; prof_err = "event pool"; return nullptr; }
       prof_ev.push_back(e);
     }
   }
-  cudaEvent_t *p = prof_ev.data() + prof_used;
-  prof_used += 2;
+  cudaEvent_t *p = prof_ev.data() + 2 * prof_used;
+  prof_kind.push_back(kind);
+  prof_fl.push_back(flops);
+  ++prof_used;
   return p;
 }
 

@@ -218,15 +218,25 @@ __device__ __forceinline__ void tile_update_tc(const Maps *maps, float *C, int64
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done_ok && kchunks > 0 && !*(volatile int *)&abort_flag) {
     const int r = warp * 32 + lane;
+    float *__restrict__ Cr = C + r;
 #pragma unroll 1
     for (int cb = 0; cb < TILE; cb += 32) {
       uint32_t v[32];
+      __syncwarp();
       tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
       if (r < rows) {
+        // all loads first, then all stores: the 32 columns are distinct
+        // addresses, so nothing serialises a load behind a store
+        float cv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int cc = cb + j;
-          if (cc < cols && r + roff >= cc) C[r + (int64_t)cc * ldc] -= __uint_as_float(v[j]);
+          cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(Cr + (int64_t)cc * ldc) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int cc = cb + j;
+          if (cc < cols && r + roff >= cc) __stcg(Cr + (int64_t)cc * ldc, cv[j] - __uint_as_float(v[j]));
         }
       }
     }

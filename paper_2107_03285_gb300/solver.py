@@ -155,13 +155,17 @@ class SGN:
                                          B._dptr(vals, C.c_double)), "sgn_export_kkt")
         return rows, cols, vals
 
-    def profile(self, enable=True):
-        B._check(self.lib.sgn_profile(self.h, 1 if enable else 0), "sgn_profile")
+    def profile(self, mask=1):
+        """Enable CUDA-event timing of the kernel kinds in `mask` (bit k =
+        binding.PROF_KINDS[k]); 0 disables.  Resets the timers."""
+        B._check(self.lib.sgn_profile(self.h, int(mask)), "sgn_profile")
 
     def profile_read(self):
-        prof = B.KernelProfile()
-        B._check(self.lib.sgn_profile_read(self.h, C.byref(prof)), "sgn_profile_read")
-        return prof
+        """{kind: (launches, seconds, flops)} since the last profile()."""
+        n = len(B.PROF_KINDS)
+        arr = (B.KernelProfile * n)()
+        B._check(self.lib.sgn_profile_read(self.h, arr, n), "sgn_profile_read")
+        return {B.PROF_KINDS[k]: (arr[k].launches, arr[k].seconds, arr[k].flops) for k in range(n)}
 
     def launch_count(self):
         return int(self.lib.sgn_launch_count(self.h))
