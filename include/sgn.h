@@ -98,7 +98,7 @@ typedef struct {
 /* Symbolic-phase options; zero-initialise for defaults. */
 typedef struct {
   int32_t leaf_nodes;        /* nested dissection stops at <= leaf_nodes nodes (0: 16) */
-  int32_t panel;             /* pivot panel width, even, 8..64 (0: 32) */
+  int32_t panel;             /* pivot panel width: 8, 16, 32 or 64 (0: 32) */
 } sgn_setup_opts;
 
 /* Least-squares objective (host arrays, copied by sgn_set_objective). */

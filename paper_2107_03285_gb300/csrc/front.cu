@@ -281,19 +281,44 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
     sv.D0[po + tid] = sD0[tid];
     sv.D1[po + tid] = sD1[tid];
   }
-  // apply the panel permutation to the factored rows left of the panel
-  // (the panel buffer a[][] is free again and serves as staging)
-  for (int c0 = 0; c0 < k; c0 += MAXNB) {
-    int cw = min(MAXNB, k - c0);
+  // the rows of this panel in the columns left of it are permuted later, once
+  // per outer block, by k_row_swap
+}
+
+// applies the pivot permutations of the panels of the outer block [K0, kend)
+// to the already factored columns left of each panel, so that L ends up in
+// the final (pivoted) row order.  Deferring this to the end of the block is
+// valid: inside the block, a panel only ever reads the rows of its own and
+// later panels, never rows of an earlier panel in earlier columns.
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_swap(DevSym d, SV sv, const int32_t *__restrict__ fronts, int K0, int NB,
+                                                   int nb) {
+  __shared__ T buf[MAXNB][65];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (K0 >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int kend = min(K0 + NB, ns);
+  const int c0 = blockIdx.x * 64;
+  if (c0 >= kend) return;
+  T *F = (T *)sv.F + sv.front_off[s];
+  const int32_t *perm = sv.piv_perm + sv.piv_off[s];
+  const int tid = threadIdx.x;
+  for (int k = K0; k < kend; k += nb) {
+    // panel [k, k + w) needs columns [c0, min(c0 + 64, k))
+    if (k <= c0) continue;
+    const int w = min(nb, ns - k);
+    const int cw = min(64, k - c0);
     __syncthreads();
     for (int idx = tid; idx < w * cw; idx += blockDim.x) {
       int cc = idx / w, t = idx - cc * w;
-      a[cc][t] = (double)F[(int64_t)(k + sperm[t]) + (int64_t)(c0 + cc) * f];
+      buf[t][cc] = F[(int64_t)(k + perm[k + t]) + (int64_t)(c0 + cc) * f];
     }
     __syncthreads();
     for (int idx = tid; idx < w * cw; idx += blockDim.x) {
       int cc = idx / w, t = idx - cc * w;
-      F[(int64_t)(k + t) + (int64_t)(c0 + cc) * f] = T(a[cc][t]);
+      F[(int64_t)(k + t) + (int64_t)(c0 + cc) * f] = buf[t][cc];
     }
   }
 }
@@ -303,10 +328,11 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
 template <typename T>
 __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                      int nb, int K0) {
-  extern __shared__ double smem[];
-  double *Ls = smem;                     // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
-  double *xs = smem + MAXNB * MAXNB;     // [MAXNB][128]
-  __shared__ double sD0[MAXNB], sD1[MAXNB];
+  // arithmetic in the store's precision (FP32 fronts keep the FP32 pipe busy)
+  extern __shared__ unsigned char trsm_raw[];
+  T *Ls = reinterpret_cast<T *>(trsm_raw);  // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
+  T *xs = Ls + MAXNB * MAXNB;                // [MAXNB][128]
+  __shared__ T sD0[MAXNB], sD1[MAXNB];
   __shared__ int sperm[MAXNB], stype[MAXNB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
@@ -322,39 +348,39 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   const int tid = threadIdx.x;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
     int t = idx / w, c = idx - t * w;
-    Ls[t * MAXNB + c] = (c < t) ? (double)F[(int64_t)(k + t) + (int64_t)(k + c) * f] : 0.0;
+    Ls[t * MAXNB + c] = (c < t) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
-    sD0[tid] = sv.D0[po + tid]; sD1[tid] = sv.D1[po + tid];
+    sD0[tid] = T(sv.D0[po + tid]); sD1[tid] = T(sv.D1[po + tid]);
     sperm[tid] = sv.piv_perm[po + tid]; stype[tid] = sv.piv_type[po + tid];
   }
   __syncthreads();
   const int il = blockIdx.x * 128 + tid;
   if (il >= nrows) return;
   const int64_t i = r0 + il;
-  for (int t = 0; t < w; ++t) xs[t * 128 + tid] = (double)F[i + (int64_t)(k + sperm[t]) * f];
+  for (int t = 0; t < w; ++t) xs[t * 128 + tid] = F[i + (int64_t)(k + sperm[t]) * f];
   for (int c = 0; c < w; ++c) {
-    double xc = xs[c * 128 + tid];
+    const T xc = xs[c * 128 + tid];
     for (int t = c + 1; t < w; ++t) xs[t * 128 + tid] -= Ls[t * MAXNB + c] * xc;
   }
   for (int t = 0; t < w; ++t) {
-    double xt = xs[t * 128 + tid];
-    W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = T(xt);
-    double l;
+    const T xt = xs[t * 128 + tid];
+    W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = xt;
+    T l;
     if (stype[t] == 0) {
       l = xt / sD0[t];
     } else if (stype[t] == 1) {
-      double det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
+      T det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
       l = (xt * sD0[t + 1] - xs[(t + 1) * 128 + tid] * sD1[t]) / det;
     } else {
-      double det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
+      T det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
       l = (xt * sD0[t - 1] - xs[(t - 1) * 128 + tid] * sD1[t - 1]) / det;
     }
-    F[i + (int64_t)(k + t) * f] = T(l);
+    F[i + (int64_t)(k + t) * f] = l;
     if (sv.wk0) {
       const int64_t o = sv.w_off[s] + i * FACTOR_BLOCK + (k - K0 + t);
-      const float wf = (float)xt, lf = (float)T(l);
+      const float wf = (float)xt, lf = (float)l;
       const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
       sv.wk0[o] = wh; sv.wk1[o] = wf - wh; sv.wk2[o] = lh; sv.wk3[o] = lf - lh;
     }
@@ -600,8 +626,17 @@ __global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_
   const int il = blockIdx.x * 256 + tid;
   if (il < nrows) {
     const int64_t i = r0 + il;
+    const T *Fi = F + i + (int64_t)k * f;
     double acc = 0.0;
-    for (int t = 0; t < w; ++t) acc = fma((double)F[i + (int64_t)(k + t) * f], y[t], acc);
+    int t = 0;
+    for (; t + 16 <= w; t += 16) {  // 16 independent loads in flight per thread
+      T v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = Fi[(int64_t)(t + u) * f];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc = fma((double)v[u], y[t + u], acc);
+    }
+    for (; t < w; ++t) acc = fma((double)Fi[(int64_t)t * f], y[t], acc);
     rhs[i] -= acc;
   }
 }
@@ -641,9 +676,23 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
   const T *F = (const T *)sv.F + sv.front_off[s];
   const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
   double acc = 0.0;
-  for (int i = ns + lane; i < f; i += 32) {
+  const T *Ft = F + (int64_t)t * f;
+  int i = ns + lane;
+  for (; i + 96 < f; i += 128) {  // four independent rows in flight per lane
+    T a[4];
+    int r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ii = i + 32 * u;
+      a[u] = Ft[ii];
+      r[u] = sr[ii / dpn - nown] * dpn + ii % dpn;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fma((double)a[u], sol[r[u]], acc);
+  }
+  for (; i < f; i += 32) {
     int q = i / dpn - nown, kd = i % dpn;
-    acc = fma((double)F[(int64_t)i + (int64_t)t * f], sol[(int64_t)sr[q] * dpn + kd], acc);
+    acc = fma((double)Ft[i], sol[(int64_t)sr[q] * dpn + kd], acc);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) yz[sv.piv_off[s] + t] -= acc;
@@ -701,7 +750,15 @@ __global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_
   if (col < k) {
     double acc = 0.0;
     const T *Fc = F + (int64_t)col * f + k;
-    for (int t = 0; t < w; ++t) acc = fma((double)Fc[t], x[t], acc);
+    int t = 0;
+    for (; t + 16 <= w; t += 16) {
+      T vv[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) vv[u] = Fc[t + u];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc = fma((double)vv[u], x[t + u], acc);
+    }
+    for (; t < w; ++t) acc = fma((double)Fc[t], x[t], acc);
     v[col] -= acc;
   }
 }
@@ -758,11 +815,13 @@ void factor_impl(Ctx &c, Store &st) {
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
   unsigned long long *ctr = (unsigned long long *)c.counters;
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
-  const size_t trsm_smem = (MAXNB * MAXNB + MAXNB * 128) * sizeof(double);
+  const size_t trsm_smem = (MAXNB * MAXNB + MAXNB * 128) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
-    cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+    cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((MAXNB * MAXNB + MAXNB * 128) * sizeof(double)));
+    cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((MAXNB * MAXNB + MAXNB * 128) * sizeof(float)));
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
     attr_set = true;
   }
@@ -833,6 +892,12 @@ void factor_impl(Ctx &c, Store &st) {
         } else {
           k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
         }
+        c.count();
+      }
+      {
+        ProfScope ps(c, SGN_PROF_PIVOT);
+        dim3 gs((kstop + 63) / 64, na);
+        k_row_swap<T><<<gs, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK, nb);
         c.count();
       }
     }
