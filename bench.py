@@ -231,11 +231,13 @@ def main():
     launches0 = s.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("sgn_timed")
         e0.record()
         for _ in range(args.steps):
             step(prec)
         e1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = s.launch_count() - launches0
     prof_launches, prof_seconds, prof_flops = s.profile_read()["update"]
     s.profile(0)

@@ -111,12 +111,31 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
       const int32_t *relc = d.relpos + d.sn_struct_off[c];
       const int nq = nstc - q;
       const int64_t rows = (int64_t)nq * dpn;
-      for (int64_t idx = threadIdx.x; idx < rows * dpn; idx += blockDim.x) {
-        int k = (int)(idx / rows);
-        int64_t rem = idx - (int64_t)k * rows;
-        int qq = q + (int)(rem / dpn), kp = (int)(rem % dpn);
-        int64_t ic = nsc + (int64_t)qq * dpn + kp, jc = nsc + (int64_t)q * dpn + k;
-        if (ic >= jc) F[(int64_t)relc[qq] * dpn + kp + (int64_t)(col0 + k) * f] += Fc[ic + jc * fc];
+      const int64_t n = rows * dpn;
+      for (int64_t base = threadIdx.x; base < n; base += 4 * (int64_t)blockDim.x) {
+        T v[4], o[4];
+        int64_t dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t idx = base + (int64_t)u * blockDim.x;
+          dst[u] = -1;
+          v[u] = T(0);
+          if (idx < n) {
+            const int k = (int)(idx / rows);
+            const int64_t rem = idx - (int64_t)k * rows;
+            const int qq = q + (int)(rem / dpn), kp = (int)(rem % dpn);
+            const int64_t ic = nsc + (int64_t)qq * dpn + kp, jc = nsc + (int64_t)q * dpn + k;
+            if (ic >= jc) {
+              dst[u] = (int64_t)relc[qq] * dpn + kp + (int64_t)(col0 + k) * f;
+              v[u] = Fc[ic + jc * fc];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = dst[u] >= 0 ? F[dst[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) F[dst[u]] = o[u] + v[u];
       }
     }
     __syncthreads();
@@ -141,9 +160,19 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
   T *F = (T *)sv.F + sv.front_off[s];
   const int tid = threadIdx.x;
   const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    int j = idx / w, i = idx - j * w;
-    a[j][i] = (i >= j) ? (double)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : 0.0;
+  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int j = idx / w, i = idx - j * w;
+      v[u] = (idx < w * w && i >= j) ? (double)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < w * w) a[idx / w][idx % w] = v[u];
+    }
   }
   if (tid < w) { sperm[tid] = tid; stype[tid] = 0; sD1[tid] = 0.0; }
   __syncthreads();
@@ -311,9 +340,19 @@ __global__ void __launch_bounds__(256) k_row_swap(DevSym d, SV sv, const int32_t
     const int w = min(nb, ns - k);
     const int cw = min(64, k - c0);
     __syncthreads();
-    for (int idx = tid; idx < w * cw; idx += blockDim.x) {
-      int cc = idx / w, t = idx - cc * w;
-      buf[t][cc] = F[(int64_t)(k + perm[k + t]) + (int64_t)(c0 + cc) * f];
+    for (int base = tid; base < w * cw; base += 8 * blockDim.x) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int cc = idx / w, t = idx - cc * w;
+        v[u] = idx < w * cw ? F[(int64_t)(k + perm[k + t]) + (int64_t)(c0 + cc) * f] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < w * cw) buf[idx % w][idx / w] = v[u];
+      }
     }
     __syncthreads();
     for (int idx = tid; idx < w * cw; idx += blockDim.x) {
@@ -346,9 +385,20 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   T *F = (T *)sv.F + sv.front_off[s];
   T *W = (T *)sv.W + sv.w_off[s];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    int t = idx / w, c = idx - t * w;
-    Ls[t * MAXNB + c] = (c < t) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
+  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int c = idx / w, t = idx - c * w;
+      v[u] = (idx < w * w && c < t) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int c = idx / w, t = idx - c * w;
+      if (idx < w * w) Ls[t * MAXNB + c] = v[u];
+    }
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
@@ -359,7 +409,14 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   const int il = blockIdx.x * 128 + tid;
   if (il >= nrows) return;
   const int64_t i = r0 + il;
-  for (int t = 0; t < w; ++t) xs[t * 128 + tid] = F[i + (int64_t)(k + sperm[t]) * f];
+  for (int t0 = 0; t0 < w; t0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? F[i + (int64_t)(k + sperm[t0 + u]) * f] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (t0 + u < w) xs[(t0 + u) * 128 + tid] = v[u];
+  }
   for (int c = 0; c < w; ++c) {
     const T xc = xs[c * 128 + tid];
     for (int t = c + 1; t < w; ++t) xs[t * 128 + tid] -= Ls[t * MAXNB + c] * xc;
@@ -415,10 +472,22 @@ __device__ __forceinline__ void tile_gemm_sub(T *__restrict__ C, int64_t ldc, co
   for (int t0 = 0; t0 < kk; t0 += KC) {
     const int kc = min(KC, kk - t0);
     __syncthreads();
-    for (int idx = tid; idx < kc * 64; idx += 256) {
-      int t = idx >> 6, ii = idx & 63;
-      As[t][ii] = ii < ma ? A[ii + (int64_t)(t0 + t) * lda] : T(0);
-      Bs[t][ii] = ii < nbc ? B[ii + (int64_t)(t0 + t) * ldb] : T(0);
+    {
+      T va[8], vb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = tid + u * 256;
+        const int t = idx >> 6, ii = idx & 63;
+        const bool ok = t < kc;
+        va[u] = (ok && ii < ma) ? A[ii + (int64_t)(t0 + t) * lda] : T(0);
+        vb[u] = (ok && ii < nbc) ? B[ii + (int64_t)(t0 + t) * ldb] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = tid + u * 256;
+        As[idx >> 6][idx & 63] = va[u];
+        Bs[idx >> 6][idx & 63] = vb[u];
+      }
     }
     __syncthreads();
     for (int t = 0; t < kc; ++t) {
@@ -575,9 +644,22 @@ constexpr int SB = 128;  // solve block width (independent of the pivot panel wi
 // (k, k) into shared memory, Ld[t * (SB + 1) + c] = L(k + t, k + c), c < t
 template <typename T>
 __device__ __forceinline__ void load_diag_block(const T *__restrict__ F, int f, int k, int w, T *Ld) {
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-    int c = idx / w, t = idx - c * w;
-    if (t > c) Ld[t * (SB + 1) + c] = F[(int64_t)(k + t) + (int64_t)(k + c) * f];
+  // 8 independent loads in flight per thread
+  const int n = w * w, step = blockDim.x;
+  for (int base = threadIdx.x; base < n; base += 8 * step) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * step;
+      const int c = idx / w, t = idx - c * w;
+      v[u] = (idx < n && t > c) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * step;
+      const int c = idx / w, t = idx - c * w;
+      if (idx < n && t > c) Ld[t * (SB + 1) + c] = v[u];
+    }
   }
 }
 
