@@ -15,7 +15,6 @@
 
 using namespace sgn;
 
-struct sgn_ctx : public Ctx {};
 
 namespace {
 
@@ -324,6 +323,7 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   if (bytes < need) return SGN_ENOMEM;
   h->stream = (cudaStream_t)stream;
   CUDA_TRY(h, cudaGetDevice(&h->device));
+  CUDA_TRY(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   std::vector<Upload> ups;
   h->base = (char *)dev_buf;
   h->bytes = bytes;

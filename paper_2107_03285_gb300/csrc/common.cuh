@@ -74,6 +74,7 @@ struct Ctx {
   int stores = 0;
   cudaStream_t stream = nullptr;
   int device = -1;
+  int num_sms = 152;
   bool bound = false;
 
   // carving
@@ -145,6 +146,8 @@ struct ProfScope {
 // ---- launchers (assemble.cu)
 void launch_elem_state(Ctx &c, const double *x, const double *p);
 void launch_slot_gather(Ctx &c, bool with_G);
+void launch_elem_state_into(Ctx &c, const double *x, const double *p, double *st);
+void launch_slot_gather_from(Ctx &c, const double *st);
 void launch_objective_terms(Ctx &c, const double *x, const double *p);
 void launch_reduce_rhs(Ctx &c, const double *bx, const double *bp, const double *bl, double *red, int dpn_kkt);
 void launch_recover(Ctx &c, const double *red, const double *bp, double *zx, double *zp, double *zl);
@@ -170,3 +173,6 @@ void solve_store(Ctx &c, Store &s, const double *b_red, double *x_red);
 void pivot_counts(Ctx &c, Store &s);  // fills c.counters (device)
 
 }  // namespace sgn
+
+// the opaque handle of the C ABI is the context itself
+struct sgn_ctx : public sgn::Ctx {};

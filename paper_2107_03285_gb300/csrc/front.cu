@@ -146,7 +146,10 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
 template <typename T>
 __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                   int nb, double eps_rel, unsigned long long *counters) {
-  __shared__ double a[MAXNB][MAXNB + 1];  // a[j][i] = A(i, j), column j
+  // eliminations in the store's precision (CT = T); every pivot decision
+  // compares magnitudes in FP64
+  using CT = T;
+  __shared__ CT a[MAXNB][MAXNB + 1];  // a[j][i] = A(i, j), column j
   __shared__ double sD0[MAXNB], sD1[MAXNB];
   __shared__ int sperm[MAXNB], stype[MAXNB];
   __shared__ int s_kp, s_kstep;
@@ -161,12 +164,12 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
   const int tid = threadIdx.x;
   const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
   for (int base = tid; base < w * w; base += 8 * blockDim.x) {
-    double v[8];
+    CT v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
       const int j = idx / w, i = idx - j * w;
-      v[u] = (idx < w * w && i >= j) ? (double)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : 0.0;
+      v[u] = (idx < w * w && i >= j) ? (CT)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : CT(0);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
     double m = 0.0;
     for (int idx = tid; idx < w * w; idx += 32) {
       int j = idx / w, i = idx - j * w;
-      if (i >= j) m = fmax(m, fabs(a[j][i]));
+      if (i >= j) m = fmax(m, fabs((double)a[j][i]));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (tid == 0) s_bmax = m;
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
       double cm = -1.0;
       int ci = w;
       for (int i = j + 1 + tid; i < w; i += 32) {
-        double v = fabs(a[j][i]);
+        double v = fabs((double)a[j][i]);
         if (v > cm) { cm = v; ci = i; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
       }
       double colmax = fmax(cm, 0.0);
       int imax = ci;
-      double absakk = fabs(a[j][j]);
+      double absakk = fabs((double)a[j][j]);
       int kstep = 1, kp = j;
       if (!(fmax(absakk, colmax) > thresh)) {
         kstep = 1; kp = j;  // (near-)zero column: static pivot below
@@ -214,13 +217,13 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
         double rm = 0.0;
         for (int t = j + tid; t < w; t += 32) {
           if (t == imax) continue;
-          double v = t < imax ? fabs(a[t][imax]) : fabs(a[imax][t]);
+          double v = t < imax ? fabs((double)a[t][imax]) : fabs((double)a[imax][t]);
           rm = fmax(rm, v);
         }
         for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
         double rowmax = rm;
         if (absakk >= alpha * colmax * (colmax / rowmax)) { kstep = 1; kp = j; }
-        else if (fabs(a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
+        else if (fabs((double)a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
         else { kstep = 2; kp = imax; }
       }
       if (tid == 0) { s_kp = kp; s_kstep = kstep; }
@@ -234,33 +237,33 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
       int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
       for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += blockDim.x) {
         if (idx == 0) {
-          double t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
+          CT t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
           int tp = sperm[kk]; sperm[kk] = sperm[kp]; sperm[kp] = tp;
         } else if (idx <= n1) {
           int i = kp + idx;
-          double t0 = a[kk][i]; a[kk][i] = a[kp][i]; a[kp][i] = t0;
+          CT t0 = a[kk][i]; a[kk][i] = a[kp][i]; a[kp][i] = t0;
         } else if (idx <= n1 + n2) {
           int i = kk + (idx - n1);
-          double t0 = a[kk][i]; a[kk][i] = a[i][kp]; a[i][kp] = t0;
+          CT t0 = a[kk][i]; a[kk][i] = a[i][kp]; a[i][kp] = t0;
         } else {
           int cc = idx - n1 - n2 - 1;
-          double t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
+          CT t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
         }
       }
       __syncthreads();
     }
     if (kstep == 1) {
       if (tid == 0) {
-        double dj = a[j][j];
+        double dj = (double)a[j][j];
         if (!(fabs(dj) > thresh)) {
           dj = (dj >= 0.0) ? thresh : -thresh;
-          a[j][j] = dj;
+          a[j][j] = (CT)dj;
           atomicAdd(counters + 0, 1ull);
         }
-        sD0[j] = dj; stype[j] = 0;
+        sD0[j] = (double)a[j][j]; stype[j] = 0;
       }
       __syncthreads();
-      const double rd = 1.0 / a[j][j];
+      const CT rd = CT(1) / a[j][j];
       const int m = w - j - 1;
       for (int idx = tid; idx < m * m; idx += blockDim.x) {
         int cc = j + 1 + idx / m, i = j + 1 + idx % m;
@@ -270,28 +273,28 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
       for (int i = j + 1 + tid; i < w; i += blockDim.x) a[j][i] *= rd;
       __syncthreads();
     } else {
-      const double d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
-      const double det = d11 * d22 - d21 * d21;
-      const double i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
+      const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
+      const CT det = d11 * d22 - d21 * d21;
+      const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
       const int m = w - j - 2;
       for (int idx = tid; idx < m * m; idx += blockDim.x) {
         int cc = j + 2 + idx / m, i = j + 2 + idx % m;
         if (i >= cc) {
-          double l1 = a[j][i] * i11 + a[j + 1][i] * i21;
-          double l2 = a[j][i] * i21 + a[j + 1][i] * i22;
+          CT l1 = a[j][i] * i11 + a[j + 1][i] * i21;
+          CT l2 = a[j][i] * i21 + a[j + 1][i] * i22;
           a[cc][i] -= l1 * a[j][cc] + l2 * a[j + 1][cc];
         }
       }
       __syncthreads();
       for (int i = j + 2 + tid; i < w; i += blockDim.x) {
-        double w1 = a[j][i], w2 = a[j + 1][i];
+        CT w1 = a[j][i], w2 = a[j + 1][i];
         a[j][i] = w1 * i11 + w2 * i21;
         a[j + 1][i] = w1 * i21 + w2 * i22;
       }
       if (tid == 0) {
-        sD0[j] = d11; sD1[j] = d21; sD0[j + 1] = d22;
+        sD0[j] = (double)d11; sD1[j] = (double)d21; sD0[j + 1] = (double)d22;
         stype[j] = 1; stype[j + 1] = 2;
-        a[j][j + 1] = 0.0;
+        a[j][j + 1] = CT(0);
         atomicAdd(counters + 1, 1ull);
       }
       __syncthreads();
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
   // write back L11 (unit lower; diagonal holds D0) and pivot data
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
     int jj = idx / w, i = idx - jj * w;
-    if (i >= jj) F[(int64_t)(k + i) + (int64_t)(k + jj) * f] = T(i == jj ? sD0[jj] : a[jj][i]);
+    if (i >= jj) F[(int64_t)(k + i) + (int64_t)(k + jj) * f] = (i == jj) ? T(sD0[jj]) : T(a[jj][i]);
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
@@ -368,9 +371,11 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                      int nb, int K0) {
   // arithmetic in the store's precision (FP32 fronts keep the FP32 pipe busy)
+  constexpr int XS = 129;                    // padded row stride of the staging tiles
   extern __shared__ unsigned char trsm_raw[];
   T *Ls = reinterpret_cast<T *>(trsm_raw);  // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
-  T *xs = Ls + MAXNB * MAXNB;                // [MAXNB][128]
+  T *xs = Ls + MAXNB * MAXNB;                // [MAXNB][XS]: W values, xs[t*XS + row]
+  T *ls = xs + MAXNB * XS;                   // [MAXNB][XS]: L values (FP32 fronts only)
   __shared__ T sD0[MAXNB], sD1[MAXNB];
   __shared__ int sperm[MAXNB], stype[MAXNB];
   const int s = fronts[blockIdx.y];
@@ -407,47 +412,56 @@ __global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32
   }
   __syncthreads();
   const int il = blockIdx.x * 128 + tid;
-  if (il >= nrows) return;
-  const int64_t i = r0 + il;
-  for (int t0 = 0; t0 < w; t0 += 8) {
-    T v[8];
+  if (il < nrows) {
+    const int64_t i = r0 + il;
+    for (int t0 = 0; t0 < w; t0 += 8) {
+      T v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? F[i + (int64_t)(k + sperm[t0 + u]) * f] : T(0);
+      for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? F[i + (int64_t)(k + sperm[t0 + u]) * f] : T(0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (t0 + u < w) xs[(t0 + u) * 128 + tid] = v[u];
-  }
-  for (int c = 0; c < w; ++c) {
-    const T xc = xs[c * 128 + tid];
-    for (int t = c + 1; t < w; ++t) xs[t * 128 + tid] -= Ls[t * MAXNB + c] * xc;
-  }
-  for (int t = 0; t < w; ++t) {
-    const T xt = xs[t * 128 + tid];
-    W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = xt;
-    T l;
-    if (stype[t] == 0) {
-      l = xt / sD0[t];
-    } else if (stype[t] == 1) {
-      T det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
-      l = (xt * sD0[t + 1] - xs[(t + 1) * 128 + tid] * sD1[t]) / det;
-    } else {
-      T det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
-      l = (xt * sD0[t - 1] - xs[(t - 1) * 128 + tid] * sD1[t - 1]) / det;
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < w) xs[(t0 + u) * XS + tid] = v[u];
     }
-    F[i + (int64_t)(k + t) * f] = l;
-    if (sv.wk0) {
-      const int64_t o = sv.w_off[s] + i * FACTOR_BLOCK + (k - K0 + t);
-      const float wf = (float)xt, lf = (float)l;
-      const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
-      sv.wk0[o] = wh; sv.wk1[o] = wf - wh; sv.wk2[o] = lh; sv.wk3[o] = lf - lh;
+    for (int c = 0; c < w; ++c) {
+      const T xc = xs[c * XS + tid];
+      for (int t = c + 1; t < w; ++t) xs[t * XS + tid] -= Ls[t * MAXNB + c] * xc;
+    }
+    for (int t = 0; t < w; ++t) {
+      const T xt = xs[t * XS + tid];
+      W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = xt;
+      T l;
+      if (stype[t] == 0) {
+        l = xt / sD0[t];
+      } else if (stype[t] == 1) {
+        T det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
+        l = (xt * sD0[t + 1] - xs[(t + 1) * XS + tid] * sD1[t]) / det;
+      } else {
+        T det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
+        l = (xt * sD0[t - 1] - xs[(t - 1) * XS + tid] * sD1[t - 1]) / det;
+      }
+      F[i + (int64_t)(k + t) * f] = l;
+      if (sv.wk0) ls[t * XS + tid] = l;
     }
   }
-  if (sv.wk0 && k + w == ns) {
-    // last panel of the front: zero the K columns up to the next 32 boundary
-    const int pad_end = ((k - K0 + w + 31) / 32) * 32 - (k - K0);
-    for (int t = w; t < pad_end; ++t) {
-      const int64_t o = sv.w_off[s] + i * FACTOR_BLOCK + (k - K0 + t);
-      sv.wk0[o] = 0.f; sv.wk1[o] = 0.f; sv.wk2[o] = 0.f; sv.wk3[o] = 0.f;
+  if (sv.wk0) {
+    // K-major hi/lo copies for the tensor-core update: each warp writes whole
+    // 128-byte row segments (lane = column); the last panel of a front also
+    // zeroes its columns up to the next multiple of 32
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
+    for (int rr = 0; rr < 32; ++rr) {
+      const int rloc = warp * 32 + rr;
+      const int ilr = blockIdx.x * 128 + rloc;
+      if (ilr >= nrows) break;
+      const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
+      for (int t = lane; t < wpad; t += 32) {
+        const float wf = t < w ? (float)xs[t * XS + rloc] : 0.f;
+        const float lf = t < w ? (float)ls[t * XS + rloc] : 0.f;
+        const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
+        sv.wk0[base + t] = wh; sv.wk1[base + t] = wf - wh;
+        sv.wk2[base + t] = lh; sv.wk3[base + t] = lf - lh;
+      }
     }
   }
 }
@@ -579,6 +593,30 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_update_tc(DevSym d, SV sv, c
                      DEV_TIMEOUT);
 }
 
+// persistent tensor-core trailing update: CTA x of front y walks tiles
+// x, x + gridDim.x, ... of that front's lower triangle
+__global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
+                                                                 int K0, int NB, const tc::Maps *__restrict__ maps,
+                                                                 int *status) {
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (K0 >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int kend = min(K0 + NB, ns);
+  const int nrows = f - kend;
+  const int nt = (nrows + tc::TILE - 1) / tc::TILE;
+  tc::TileJob job;
+  job.ntiles = nt * (nt + 1) / 2;
+  if ((int)blockIdx.x >= job.ntiles) return;
+  job.C0 = (float *)sv.F + sv.front_off[s] + (int64_t)kend + (int64_t)kend * f;
+  job.ldc = f;
+  job.nrows = nrows;
+  job.kend = kend;
+  job.kchunks = (kend - K0 + 31) / 32;
+  tc::tile_loop_tc(&maps[s], job, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
+}
+
 // left-looking update of the panel [k, k + w) by the earlier panels of its
 // outer block: F[k:, k:k+w] -= W[k:, K0:k] L[k:k+w, K0:k]^T (lower part)
 template <typename T>
@@ -640,38 +678,73 @@ __global__ void __launch_bounds__(64) k_fwd_permute(DevSym d, SV sv, const int32
 
 constexpr int SB = 128;  // solve block width (independent of the pivot panel width)
 
-// loads the strict lower triangle of the w x w diagonal block starting at
-// (k, k) into shared memory, Ld[t * (SB + 1) + c] = L(k + t, k + c), c < t
+// Arithmetic of the substitutions is done in the factor's precision (AT = T):
+// with FP32 fronts every solve is the correction solve of mixed-precision
+// iterative refinement, whose residual and update are formed in FP64 outside.
+
+// forward, diagonal block: y_b = L_bb^{-1} r_b for every active front (one
+// CTA each); y_b goes to yz, r stays untouched for the GEMV kernel
 template <typename T>
-__device__ __forceinline__ void load_diag_block(const T *__restrict__ F, int f, int k, int w, T *Ld) {
-  // 8 independent loads in flight per thread
-  const int n = w * w, step = blockDim.x;
-  for (int base = threadIdx.x; base < n; base += 8 * step) {
+__global__ void __launch_bounds__(256) k_fwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                   double *__restrict__ yz) {
+  using AT = T;
+  extern __shared__ unsigned char diag_raw[];
+  AT(*Ld)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(diag_raw);
+  __shared__ AT y[SB];
+  const int s = fronts[blockIdx.x];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(SB, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  const double *rhs = sv.rhs + sv.rhs_off[s];
+  const int tid = threadIdx.x, lane = tid & 31;
+  // strict lower triangle of the block, 8 loads in flight per thread
+  const int n = w * w;
+  for (int base = tid; base < n; base += 8 * blockDim.x) {
     T v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * step;
+      const int idx = base + u * blockDim.x;
       const int c = idx / w, t = idx - c * w;
       v[u] = (idx < n && t > c) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * step;
-      const int c = idx / w, t = idx - c * w;
-      if (idx < n && t > c) Ld[t * (SB + 1) + c] = v[u];
+      const int idx = base + u * blockDim.x;
+      if (idx < n) Ld[idx % w][idx / w] = v[u];
     }
   }
+  if (tid < w) y[tid] = (AT)rhs[k + tid];
+  __syncthreads();
+  for (int q = 0; q < w; q += 32) {
+    const int wq = min(32, w - q);
+    if (tid < 32) {
+      AT yl = lane < wq ? y[q + lane] : AT(0);
+      for (int c = 0; c < wq; ++c) {
+        AT yc = __shfl_sync(0xffffffffu, yl, c);
+        if (lane > c && lane < wq) yl -= Ld[q + lane][q + c] * yc;
+      }
+      if (lane < wq) y[q + lane] = yl;
+    }
+    __syncthreads();
+    for (int t = q + wq + tid; t < w; t += blockDim.x) {
+      AT acc = AT(0);
+      for (int c = 0; c < wq; ++c) acc += Ld[t][q + c] * y[q + c];
+      y[t] -= acc;
+    }
+    __syncthreads();
+  }
+  if (tid < w) yz[sv.piv_off[s] + k + tid] = (double)y[tid];
 }
 
-// forward block step: y_b = L_bb^{-1} r_b (every CTA solves the small block
-// itself, so no second launch is needed), then r_i -= L_ib y_b for the rows
-// of this CTA's chunk.  CTA 0 records y_b.
+// forward, rows below the block: r_i -= L_ib y_b; each thread owns 2 rows
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                    double *__restrict__ yz) {
-  extern __shared__ unsigned char smraw[];
-  T *Ld = reinterpret_cast<T *>(smraw);
-  __shared__ double y[SB];
+__global__ void __launch_bounds__(256) k_fwd_gemv(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                   const double *__restrict__ yz) {
+  using AT = T;
+  __shared__ AT y[SB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
@@ -679,48 +752,35 @@ __global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_
   const int f = front_order(d, s, dpn);
   const int w = min(SB, ns - k);
   const int r0 = k + w, nrows = f - r0;
-  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= nrows) return;
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  const int tid = threadIdx.x, lane = tid & 31;
-  load_diag_block<T>(F, f, k, w, Ld);
-  if (tid < w) y[tid] = rhs[k + tid];
+  const int row0 = blockIdx.x * 512;
+  if (row0 >= nrows) return;
+  if (threadIdx.x < w) y[threadIdx.x] = (AT)yz[sv.piv_off[s] + k + threadIdx.x];
   __syncthreads();
-  for (int q = 0; q < w; q += 32) {
-    const int wq = min(32, w - q);
-    if (tid < 32) {
-      double yl = lane < wq ? y[q + lane] : 0.0;
-      for (int c = 0; c < wq; ++c) {
-        double yc = __shfl_sync(0xffffffffu, yl, c);
-        if (lane > c && lane < wq) yl -= (double)Ld[(q + lane) * (SB + 1) + q + c] * yc;
-      }
-      if (lane < wq) y[q + lane] = yl;
-    }
-    __syncthreads();
-    for (int t = q + wq + tid; t < w; t += blockDim.x) {
-      double acc = 0.0;
-      for (int c = 0; c < wq; ++c) acc = fma((double)Ld[t * (SB + 1) + q + c], y[q + c], acc);
-      y[t] -= acc;
-    }
-    __syncthreads();
-  }
-  if (blockIdx.x == 0 && tid < w) yz[sv.piv_off[s] + k + tid] = y[tid];
-  const int il = blockIdx.x * 256 + tid;
-  if (il < nrows) {
-    const int64_t i = r0 + il;
-    const T *Fi = F + i + (int64_t)k * f;
-    double acc = 0.0;
-    int t = 0;
-    for (; t + 16 <= w; t += 16) {  // 16 independent loads in flight per thread
-      T v[16];
+  const T *F = (const T *)sv.F + sv.front_off[s] + (int64_t)k * f;
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  const int i0 = r0 + row0 + threadIdx.x, i1 = i0 + 256;
+  const bool ok0 = i0 < f, ok1 = i1 < f;
+  AT a0 = AT(0), a1 = AT(0);
+  int t = 0;
+  for (; t + 8 <= w; t += 8) {
+    T v0[8], v1[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = Fi[(int64_t)(t + u) * f];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) acc = fma((double)v[u], y[t + u], acc);
+    for (int u = 0; u < 8; ++u) {
+      v0[u] = ok0 ? F[(int64_t)(t + u) * f + i0] : T(0);
+      v1[u] = ok1 ? F[(int64_t)(t + u) * f + i1] : T(0);
     }
-    for (; t < w; ++t) acc = fma((double)Fi[(int64_t)t * f], y[t], acc);
-    rhs[i] -= acc;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a0 += (AT)v0[u] * y[t + u];
+      a1 += (AT)v1[u] * y[t + u];
+    }
   }
+  for (; t < w; ++t) {
+    if (ok0) a0 += (AT)F[(int64_t)t * f + i0] * y[t];
+    if (ok1) a1 += (AT)F[(int64_t)t * f + i1] * y[t];
+  }
+  if (ok0) rhs[i0] -= (double)a0;
+  if (ok1) rhs[i1] -= (double)a1;
 }
 
 __global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts, double *__restrict__ yz) {
@@ -743,106 +803,147 @@ __global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts
   }
 }
 
-// v_own = z_own - L21^T x_struct (warp per own column)
+// v_own = z_own - L21^T x_struct: a CTA owns 32 own columns; its 8 warps
+// split the struct rows, each lane reads 4 consecutive rows of 4 columns
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                    const double *__restrict__ sol, double *__restrict__ yz) {
+  using AT = T;
+  __shared__ AT part[8][32];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int nown = d.sn_nown[s];
   const int ns = nown * dpn;
-  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (t >= ns) return;
+  const int t0 = blockIdx.x * 32;
+  if (t0 >= ns) return;
   const int f = front_order(d, s, dpn);
   const T *F = (const T *)sv.F + sv.front_off[s];
   const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
-  double acc = 0.0;
-  const T *Ft = F + (int64_t)t * f;
-  int i = ns + lane;
-  for (; i + 96 < f; i += 128) {  // four independent rows in flight per lane
-    T a[4];
-    int r[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncol = min(32, ns - t0);
+  // each warp handles columns t0 + [0, 32) over rows ns + warp + 8 j
+  AT acc = AT(0);
+  const int col = t0 + lane;
+  if (lane < ncol) {
+    const T *Fc = F + (int64_t)col * f;
+    int i = ns + warp;
+    for (; i + 24 < f; i += 32) {
+      T v[4];
+      double xv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int ii = i + 32 * u;
-      a[u] = Ft[ii];
-      r[u] = sr[ii / dpn - nown] * dpn + ii % dpn;
+      for (int u = 0; u < 4; ++u) {
+        const int ii = i + 8 * u;
+        v[u] = Fc[ii];
+        xv[u] = sol[(int64_t)sr[ii / dpn - nown] * dpn + ii % dpn];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += (AT)v[u] * (AT)xv[u];
     }
+    for (; i < f; i += 8) acc += (AT)Fc[i] * (AT)sol[(int64_t)sr[i / dpn - nown] * dpn + i % dpn];
+  }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && lane < ncol) {
+    AT tot = AT(0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc = fma((double)a[u], sol[r[u]], acc);
+    for (int u = 0; u < 8; ++u) tot += part[u][lane];
+    yz[sv.piv_off[s] + col] -= (double)tot;
   }
-  for (; i < f; i += 32) {
-    int q = i / dpn - nown, kd = i % dpn;
-    acc = fma((double)Ft[i], sol[(int64_t)sr[q] * dpn + kd], acc);
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) yz[sv.piv_off[s] + t] -= acc;
 }
 
-// backward block step: x_b = L_bb^{-T} v_b (solved by every CTA), CTA 0
-// scatters x_b (un-pivoted) into the solution, and each CTA subtracts
-// L_bc^T x_b from v_c for its chunk of earlier columns c < k
+// backward, diagonal block: x_b = L_bb^{-T} v_b (one CTA per front); x_b is
+// written un-pivoted into the solution and, pivoted, into yz for the GEMV
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                    int nb, double *__restrict__ yz, double *__restrict__ sol) {
-  extern __shared__ unsigned char smraw[];
-  T *Ld = reinterpret_cast<T *>(smraw);
-  __shared__ double x[SB];
-  const int s = fronts[blockIdx.y];
+__global__ void __launch_bounds__(256) k_bwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb,
+                                                   double *__restrict__ yz, double *__restrict__ sol) {
+  using AT = T;
+  extern __shared__ unsigned char diag_raw[];
+  AT(*Ld)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(diag_raw);
+  __shared__ AT x[SB];
+  const int s = fronts[blockIdx.x];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
   if (k >= ns) return;
   const int f = front_order(d, s, dpn);
   const int w = min(SB, ns - k);
-  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= k) return;
   const T *F = (const T *)sv.F + sv.front_off[s];
   const int64_t po = sv.piv_off[s];
-  double *v = yz + po;
   const int tid = threadIdx.x, lane = tid & 31;
-  load_diag_block<T>(F, f, k, w, Ld);
-  if (tid < w) x[tid] = v[k + tid];
+  const int n = w * w;
+  for (int base = tid; base < n; base += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int c = idx / w, t = idx - c * w;
+      v[u] = (idx < n && t > c) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < n) Ld[idx % w][idx / w] = v[u];
+    }
+  }
+  if (tid < w) x[tid] = (AT)yz[po + k + tid];
   __syncthreads();
   const int nq = (w + 31) / 32;
   for (int qi = nq - 1; qi >= 0; --qi) {
     const int q = qi * 32;
     const int wq = min(32, w - q);
     if (tid < 32) {
-      double xl = lane < wq ? x[q + lane] : 0.0;
+      AT xl = lane < wq ? x[q + lane] : AT(0);
       for (int c = wq - 1; c >= 0; --c) {
-        double xc = __shfl_sync(0xffffffffu, xl, c);
-        if (lane < c) xl -= (double)Ld[(q + c) * (SB + 1) + q + lane] * xc;
+        AT xc = __shfl_sync(0xffffffffu, xl, c);
+        if (lane < c) xl -= Ld[q + c][q + lane] * xc;
       }
       if (lane < wq) x[q + lane] = xl;
     }
     __syncthreads();
     for (int t = tid; t < q; t += blockDim.x) {
-      double acc = 0.0;
-      for (int c = 0; c < wq; ++c) acc = fma((double)Ld[(q + c) * (SB + 1) + t], x[q + c], acc);
+      AT acc = AT(0);
+      for (int c = 0; c < wq; ++c) acc += Ld[q + c][t] * x[q + c];
       x[t] -= acc;
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && tid < w) {
+  if (tid < w) {
+    yz[po + k + tid] = (double)x[tid];
     // piv_perm is local to the pivot panel (width nb) holding position k + tid
     const int pos = k + tid, pstart = (pos / nb) * nb;
-    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = x[tid];
+    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)x[tid];
   }
-  const int col = blockIdx.x * 256 + tid;
-  if (col < k) {
-    double acc = 0.0;
-    const T *Fc = F + (int64_t)col * f + k;
-    int t = 0;
-    for (; t + 16 <= w; t += 16) {
-      T vv[16];
+}
+
+// backward, columns left of the block: v_c -= sum_t L(k + t, c) x_t
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_gemv(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                   double *__restrict__ yz) {
+  using AT = T;
+  __shared__ AT x[SB];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int col = blockIdx.x * 256 + threadIdx.x;
+  if (blockIdx.x * 256 >= k) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(SB, ns - k);
+  const int64_t po = sv.piv_off[s];
+  if (threadIdx.x < w) x[threadIdx.x] = (AT)yz[po + k + threadIdx.x];
+  __syncthreads();
+  if (col >= k) return;
+  const T *Fc = (const T *)sv.F + sv.front_off[s] + (int64_t)col * f + k;
+  AT acc = AT(0);
+  int t = 0;
+  for (; t + 16 <= w; t += 16) {
+    T v[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) vv[u] = Fc[t + u];
+    for (int u = 0; u < 16; ++u) v[u] = Fc[t + u];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) acc = fma((double)vv[u], x[t + u], acc);
-    }
-    for (; t < w; ++t) acc = fma((double)Fc[t], x[t], acc);
-    v[col] -= acc;
+    for (int u = 0; u < 16; ++u) acc += (AT)v[u] * x[t + u];
   }
+  for (; t < w; ++t) acc += (AT)Fc[t] * x[t];
+  yz[po + col] -= (double)acc;
 }
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
@@ -897,14 +998,15 @@ void factor_impl(Ctx &c, Store &st) {
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
   unsigned long long *ctr = (unsigned long long *)c.counters;
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
-  const size_t trsm_smem = (MAXNB * MAXNB + MAXNB * 128) * sizeof(T);
+  const size_t trsm_smem = (MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((MAXNB * MAXNB + MAXNB * 128) * sizeof(double)));
+                         (int)((MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(double)));
     cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((MAXNB * MAXNB + MAXNB * 128) * sizeof(float)));
+                         (int)((MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(float)));
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
     attr_set = true;
   }
   for (int L = 0; L < c.S.n_levels; ++L) {
@@ -966,10 +1068,14 @@ void factor_impl(Ctx &c, Store &st) {
         }
         ProfScope ps(c, SGN_PROF_UPDATE, fl);
         if (std::is_same<T, float>::value && st.tc) {
+          // one CTA per SM (192 KB shared memory); spread the SMs over the
+          // active fronts and let every CTA loop over its front's tiles
           int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
-          dim3 gtc(nt128 * (nt128 + 1) / 2, na);
-          k_update_tc<<<gtc, tc::THREADS, tc::SMEM_BYTES, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK,
-                                                                       (const tc::Maps *)st.maps, c.status);
+          int tiles = nt128 * (nt128 + 1) / 2;
+          int g = std::max(1, std::min(tiles, (c.num_sms + na - 1) / na));
+          dim3 gtc(g, na);
+          k_update_tcp<<<gtc, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK,
+                                                                          (const tc::Maps *)st.maps, c.status);
           c.tc_launches++;
         } else {
           k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
@@ -993,13 +1099,11 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   SV sv = view(st);
   const int nb = c.S.opts.panel;
   const int dpn = st.dpn;
-  const size_t smem = (size_t)SB * (SB + 1) * sizeof(T);
+  const size_t diag_smem = (size_t)SB * (SB + 1) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_fwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-    cudaFuncSetAttribute(k_fwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-    cudaFuncSetAttribute(k_bwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-    cudaFuncSetAttribute(k_bwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+    cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
+    cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
     attr_set = true;
   }
   for (int L = 0; L < c.S.n_levels; ++L) {
@@ -1018,9 +1122,13 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
       int na = n_active(li, k);
       int max_rows = 0;
       for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - k - std::min(SB, li.ns[q] - k));
-      dim3 g(std::max(1, (max_rows + 255) / 256), na);
-      k_fwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
+      k_fwd_diag<T><<<na, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
       c.count();
+      if (max_rows > 0) {
+        dim3 g((max_rows + 511) / 512, na);
+        k_fwd_gemv<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, st.yz);
+        c.count();
+      }
     }
     dim3 gd((max_ns + 255) / 256, nf);
     k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts, st.yz);
@@ -1032,15 +1140,19 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     int nf = (int)(li.f1 - li.f0);
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     if (max_ns == 0) continue;
-    dim3 gi((max_ns + 7) / 8, nf);
+    dim3 gi((max_ns + 31) / 32, nf);
     k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x, st.yz);
     c.count();
     int last = ((max_ns - 1) / SB) * SB;
     for (int k = last; k >= 0; k -= SB) {
       int na = n_active(li, k);
-      dim3 g(std::max(1, (k + 255) / 256), na);
-      k_bwd_block<T><<<g, 256, smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
+      k_bwd_diag<T><<<na, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
       c.count();
+      if (k > 0) {
+        dim3 g((k + 255) / 256, na);
+        k_bwd_gemv<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, st.yz);
+        c.count();
+      }
     }
   }
 }

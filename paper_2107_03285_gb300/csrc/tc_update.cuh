@@ -214,9 +214,11 @@ __device__ __forceinline__ void tile_update_tc(const Maps *maps, float *C, int64
   }
   __syncwarp();
   // ---- epilogue: all four warps, warp w owns TMEM lanes 32w .. 32w + 31
-  const bool done_ok = mbar_wait(&done_bar, 0, status, flag_timeout);
+  bool done_ok = mbar_wait(&done_bar, 0, status, flag_timeout);
+  // tcgen05.ld is warp-collective: the whole warp takes the same branch
+  done_ok = __all_sync(0xffffffffu, done_ok && !*(volatile int *)&abort_flag);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (done_ok && kchunks > 0 && !*(volatile int *)&abort_flag) {
+  if (done_ok && kchunks > 0) {
     const int r = warp * 32 + lane;
     float *__restrict__ Cr = C + r;
 #pragma unroll 1
@@ -245,6 +247,182 @@ __device__ __forceinline__ void tile_update_tc(const Maps *maps, float *C, int64
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
+  }
+}
+
+}  // namespace tc
+}  // namespace sgn
+
+namespace sgn {
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised version: each CTA walks a list of tiles of one
+// front; two TMEM accumulators (2 x 128 columns) let the epilogue of tile i
+// run while the producer and MMA warps already work on tile i + 1.
+//   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
+//   warps 2..5    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31)
+constexpr int PSTAGES = 3;
+constexpr int PTHREADS = 192;
+constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;
+
+struct TileJob {                 // one front's part of a trailing update
+  float *C0;                     // F + kend + kend * f (origin of the trailing block)
+  int64_t ldc;                   // f
+  int nrows;                     // f - kend
+  int kend;                      // first trailing row (TMA row coordinate of tile row 0)
+  int kchunks;                   // 32-wide K chunks
+  int ntiles;                    // lower-triangle 128-tiles
+};
+
+__device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
+  bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  while (bi * (bi + 1) / 2 > tile) --bi;
+  bj = tile - bi * (bi + 1) / 2;
+}
+
+__device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job, int first, int stride,
+                                             int *status, int flag_timeout) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  __shared__ uint64_t full_bar[PSTAGES], empty_bar[PSTAGES], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int my_tiles = first < job.ntiles ? (job.ntiles - first + stride - 1) / stride : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PSTAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * TILE)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kch = job.kchunks;
+
+  if (warp == 0) {
+    if (lane == 0 && my_tiles > 0 && kch > 0) {
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->whi) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->wlo) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->lhi) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->llo) : "memory");
+      int g = 0;  // global chunk counter over all of this CTA's tiles
+      bool stop = false;
+      for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+        int bi, bj;
+        tile_coords(first + lt * stride, bi, bj);
+        const int rw = job.kend + bi * TILE, rl = job.kend + bj * TILE;
+        for (int kc = 0; kc < kch; ++kc, ++g) {
+          const int s = g % PSTAGES;
+          if (g >= PSTAGES && !mbar_wait(&empty_bar[s], ((g / PSTAGES) - 1) & 1, status, flag_timeout)) {
+            abort_flag = 1; stop = true; break;
+          }
+          if (*(volatile int *)&abort_flag) { stop = true; break; }
+          unsigned char *st = sm + s * STAGE_BYTES;
+          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+          tma_load_2d(st + 0 * TILE_BYTES, &maps->whi, &full_bar[s], kc * KCH, rw);
+          tma_load_2d(st + 1 * TILE_BYTES, &maps->wlo, &full_bar[s], kc * KCH, rw);
+          tma_load_2d(st + 2 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, rl);
+          tma_load_2d(st + 3 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl);
+        }
+      }
+      // drain the copies still in flight (bounded)
+      for (int q = (g > PSTAGES ? g - PSTAGES : 0); q < g; ++q)
+        mbar_wait(&full_bar[q % PSTAGES], (q / PSTAGES) & 1, status, flag_timeout);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && my_tiles > 0 && kch > 0) {
+      const uint32_t idesc = idesc_tf32_128x128();
+      int g = 0;
+      bool stop = false;
+      for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+        const int b = lt & 1;
+        if (lt >= 2 && !mbar_wait(&acc_empty[b], ((lt >> 1) - 1) & 1, status, flag_timeout)) {
+          abort_flag = 1; break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_tmem = tmem + (uint32_t)(b * TILE);
+        for (int kc = 0; kc < kch; ++kc, ++g) {
+          const int s = g % PSTAGES;
+          if (!mbar_wait(&full_bar[s], (g / PSTAGES) & 1, status, flag_timeout)) { abort_flag = 1; stop = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t base = smem_u32(sm + s * STAGE_BYTES);
+#pragma unroll
+          for (int k = 0; k < KCH / 8; ++k) {
+            const uint32_t off = k * 32;
+            const uint64_t ahi = umma_desc_sw128(base + 0 * TILE_BYTES + off);
+            const uint64_t alo = umma_desc_sw128(base + 1 * TILE_BYTES + off);
+            const uint64_t bhi = umma_desc_sw128(base + 2 * TILE_BYTES + off);
+            const uint64_t blo = umma_desc_sw128(base + 3 * TILE_BYTES + off);
+            umma_tf32(acc_tmem, ahi, bhi, idesc, (kc | k) != 0);
+            umma_tf32(acc_tmem, ahi, blo, idesc, 1);
+            umma_tf32(acc_tmem, alo, bhi, idesc, 1);
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        if (stop) break;
+        umma_commit(&acc_full[b]);
+      }
+      if (*(volatile int *)&abort_flag) {
+        // release the epilogue of both buffers so nobody waits for a full second
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_full[0])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_full[1])) : "memory");
+      }
+    }
+  } else {
+    // epilogue warps 2..5
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    for (int lt = 0; lt < my_tiles && kch > 0; ++lt) {
+      const int b = lt & 1;
+      bool ok = mbar_wait(&acc_full[b], (lt >> 1) & 1, status, flag_timeout);
+      // tcgen05.ld is warp-collective: the whole warp takes the same branch
+      ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) break;
+      int bi, bj;
+      tile_coords(first + lt * stride, bi, bj);
+      const int rows = min(TILE, job.nrows - bi * TILE), cols = min(TILE, job.nrows - bj * TILE);
+      const int roff = (bi - bj) * TILE;
+      float *__restrict__ Cr = job.C0 + (int64_t)(bi * TILE + r) + (int64_t)(bj * TILE) * job.ldc;
+#pragma unroll 1
+      for (int cb = 0; cb < TILE; cb += 32) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + cb), v);
+        if (r < rows) {
+          float cv[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int cc = cb + j;
+            cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(Cr + (int64_t)cc * job.ldc) : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int cc = cb + j;
+            if (cc < cols && r + roff >= cc) __stcg(Cr + (int64_t)cc * job.ldc, cv[j] - __uint_as_float(v[j]));
+          }
+        }
+      }
+      // this warp's TMEM reads of buffer b are complete (tcgen05.wait::ld)
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE) : "memory");
   }
 }
 
