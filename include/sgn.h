@@ -211,6 +211,25 @@ sgn_status sgn_step_host(sgn_t h, sgn_precision prec, const double *x_h, const d
  * rows_h / cols_h / vals_h must hold *nnz entries.  Synchronises. */
 sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows_h, int64_t *cols_h, double *vals_h);
 
+/* sgn_assemble_static: same result as sgn_assemble (x_d, p_d in; the
+ * assembled blocks, right-hand-side terms and dc/dp of the handle out), but
+ * the per-element state it passes from the element kernel to the slot
+ * gather lives in a fixed 16 MB device array inside the library instead of
+ * the caller's bound buffer.  The paper has no counterpart: this exists for
+ * callers that cannot allocate, or do not want to size, that part of the
+ * workspace (e.g. a frozen allocator in a long-running service); the array
+ * is allocated with the library image and every GPU that loads libsgn.so
+ * holds it until the process exits.  Allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  Limit: (3 + (dim+1) dim) *
+ * n_elem doubles <= 2^21, i.e. 139,810 tetrahedra or 233,016 triangles;
+ * larger meshes get SGN_EINVAL.  The first call on a device looks up the
+ * array's device address with that device current, so make that first call
+ * before any stream capture.  All calls share the array (it keeps the last
+ * call's contents; every entry is rewritten before it is read, so nothing
+ * needs clearing): calls whose work overlaps on the GPU, from any handle or
+ * stream, race on it. */
+sgn_status sgn_assemble_static(sgn_t h, const double *x_d, const double *p_d);
+
 /* ---- forward simulation and gradient -------------------------------------
  * sgn_equilibrium: Newton's method on Pi(x; p) with a backtracking line
  * search that keeps Pi monotone and rejects inverted elements (Sec. 5,

@@ -458,6 +458,20 @@ void launch_elem_state(Ctx &c, const double *x, const double *p) {
                  c.E0, c.nu, c.st, c.cpv, c.status);
 }
 
+// same two kernels with the element state in caller-chosen scratch memory
+void launch_elem_state_into(Ctx &c, const double *x, const double *p, double *st) {
+  const DevSym &d = c.ds;
+  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, p,
+                 c.E0, c.nu, st, c.cpv, c.status);
+}
+
+void launch_slot_gather_from(Ctx &c, const double *st) {
+  const DevSym &d = c.ds;
+  int n_up = (int)c.S.up_slot.size();
+  SGN_DISPATCH_D(c, k_slot_gather, nblk(n_up), TPB, 0, n_up, d.n_elem, d.up_slot, d.up_slot_t, d.up_ptr,
+                 d.up_contrib, d.elem_B, st, c.cpv, 1.0 / c.alpha, c.Kv, c.Gv);
+}
+
 void launch_slot_gather(Ctx &c, bool with_G) {
   const DevSym &d = c.ds;
   int n_up = (int)c.S.up_slot.size();
