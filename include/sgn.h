@@ -145,7 +145,9 @@ typedef struct {
 
 typedef struct {
   int32_t max_iter;               /* default 0 -> 50 */
-  double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10) */
+  double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10); a residual a Newton
+                                     step no longer halves also counts once below 1e-7 ||f_ext||
+                                     (the round-off floor of c grows with the mesh) */
 } sgn_newton_opts;
 
 typedef struct {
@@ -202,6 +204,17 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
  * device->host copy of the step.  Synchronises. */
 sgn_status sgn_step_host(sgn_t h, sgn_precision prec, const double *x_h, const double *p_h,
                          double *dx_h, double *dp_h, double *dl_h, sgn_solve_report *report);
+
+/* sgn_step_graph: one SGN step -- sgn_assemble at (x_d, p_d), sgn_factor
+ * (prec), the solve of Eq. sparseSystemGN with the Newton-KKT right-hand
+ * side and exactly refine_steps FP64 refinement steps -- issued as a single
+ * CUDA-graph launch on the handle's stream (the graph is captured on the
+ * first call and replayed while the arguments stay the same).  Outputs as
+ * in sgn_solve; dx_d / dl_d may be NULL.  If residual_h is non-NULL the call
+ * synchronises and stores ||b - M z|| / ||b|| (FP64) there.  EINVAL for
+ * refine_steps outside 0..64. */
+sgn_status sgn_step_graph(sgn_t h, sgn_precision prec, int32_t refine_steps, const double *x_d, const double *p_d,
+                          double *dx_d, double *dp_d, double *dl_d, double *residual_h);
 
 /* sgn_export_kkt: copies the assembled saddle-point matrix of Eq.
  * sparseSystemGN (the last sgn_assemble) to host COO arrays, both triangles.

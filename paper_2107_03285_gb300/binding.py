@@ -25,7 +25,7 @@ PROF_KINDS = ["update", "panel_update", "pivot", "trsm", "front_assembly", "elem
 EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
-            "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static"]
+            "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph"]
 
 
 class Mesh(C.Structure):
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_strerror": (C.c_char_p, [C.c_int]),
         "sgn_assemble": (C.c_int, [VP, VP, VP]),
         "sgn_assemble_static": (C.c_int, [VP, VP, VP]),
+        "sgn_step_graph": (C.c_int, [VP, C.c_int, C.c_int32, VP, VP, VP, VP, VP, dp]),
         "sgn_factor": (C.c_int, [VP, C.c_int, P(FactorReport)]),
         "sgn_solve": (C.c_int, [VP, C.c_int, VP, VP, VP, VP, P(SolveOpts), P(SolveReport)]),
         "sgn_step_host": (C.c_int, [VP, C.c_int, dp, dp, dp, dp, dp, P(SolveReport)]),

@@ -143,6 +143,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.red = cv.take<double>(2 * nx * 2);  // reduced rhs and solution
   c.n_partial = 1024;
   c.partial = cv.take<double>(c.n_partial);
+  c.partial2 = cv.take<double>(2 * c.n_partial);
   c.status = cv.take<int>(4);
   c.counters = cv.take<int64_t>(8);
   const size_t nn = (size_t)S.n_nodes * d;
@@ -158,6 +159,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     size_t es = fp32 ? 4 : 8;
     s.F = cv.take<char>((size_t)s.front_elems * es);
     s.W = cv.take<char>((size_t)s.w_elems * es);
+    s.Ldg = cv.take<char>((size_t)s.piv_elems * c.S.opts.panel * es);
     s.rhs = cv.take<double>(s.rhs_elems);
     s.piv_type = cv.take<int32_t>(s.piv_elems); s.piv_perm = cv.take<int32_t>(s.piv_elems);
     s.D0 = cv.take<double>(s.piv_elems); s.D1 = cv.take<double>(s.piv_elems);
@@ -343,6 +345,14 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   // staging; wait for them before those can change
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->stores = stores;
+  set_kernel_attributes();
+  if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  {
+    const char *g = getenv("SGN_DISABLE_GRAPHS");
+    h->use_graphs = !(g && g[0] == '1');
+  }
+  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf);
+  if (h->step_graph) { cudaGraphExecDestroy(h->step_graph); h->step_graph = nullptr; }
   h->bound = true;
   h->assembled = false;
   h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
@@ -378,6 +388,10 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
 
 void sgn_destroy(sgn_t h) {
   if (!h) return;
+  if (h->bound) cudaStreamSynchronize(h->stream);
+  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf);
+  if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   delete h;
 }
@@ -587,17 +601,21 @@ sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows, int64_t *cols, d
 sgn_status sgn_profile(sgn_t h, int32_t mask) {
   if (!h) return SGN_EINVAL;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->harvest_graph_events();
   h->prof_mask = mask;
   h->prof_used = 0;
   h->prof_kind.clear();
   h->prof_fl.clear();
+  for (int k = 0; k < 8; ++k) { h->gacc_sec[k] = 0.0; h->gacc_fl[k] = 0.0; h->gacc_n[k] = 0; }
   return SGN_OK;
 }
 
 sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out, int32_t n) {
   if (!h || !out || n < 0) return SGN_EINVAL;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  for (int k = 0; k < n; ++k) out[k] = sgn_kernel_profile{0, 0.0, 0.0};
+  h->harvest_graph_events();
+  for (int k = 0; k < n; ++k)
+    out[k] = sgn_kernel_profile{k < 8 ? h->gacc_n[k] : 0, k < 8 ? h->gacc_sec[k] : 0.0, k < 8 ? h->gacc_fl[k] : 0.0};
   for (int64_t i = 0; i < h->prof_used; ++i) {
     int k = h->prof_kind[i];
     if (k >= n) continue;
@@ -611,6 +629,79 @@ sgn_status sgn_profile_read(sgn_t h, sgn_kernel_profile *out, int32_t n) {
 }
 
 int64_t sgn_launch_count(sgn_t h) { return h ? h->launches : -1; }
+
+sgn_status sgn_step_graph(sgn_t h, sgn_precision prec, int32_t refine_steps, const double *x_d, const double *p_d,
+                          double *dx_d, double *dp_d, double *dl_d, double *residual_h) {
+  if (!h || !x_d || !p_d || !dp_d || refine_steps < 0 || refine_steps > 64) return SGN_EINVAL;
+  if (!h->bound || !h->have_objective) return SGN_ESTATE;
+  Store &st = prec == SGN_MIXED ? h->kkt32 : h->kkt64;
+  if (!st.enabled) return SGN_ESTATE;
+  if (!h->cap_stream) return SGN_ECUDA;
+  Ctx &c = *h;
+  const int64_t nx = (int64_t)c.S.n_free * c.S.dim, ne = c.S.n_elem;
+  const void *key[6] = {x_d, p_d, dx_d, dp_d, dl_d, &st};
+  bool same = h->step_graph && h->step_prec == (int)prec && h->step_refine == refine_steps;
+  for (int i = 0; i < 6 && same; ++i) same = h->step_key[i] == key[i];
+  if (!same) {
+    if (h->step_graph) { cudaGraphExecDestroy(h->step_graph); h->step_graph = nullptr; }
+    double *red_b = c.red, *red_x = c.red + 2 * nx;
+    auto body = [&]() {
+      launch_elem_state(c, x_d, p_d);
+      launch_slot_gather(c, true);
+      launch_objective_terms(c, x_d, p_d);
+      factor_direct(c, st);
+      cudaMemsetAsync(c.bx, 0, nx * sizeof(double), c.stream);
+      launch_axpy(c, c.bx, c.fx, -1.0, nx);
+      cudaMemsetAsync(c.bp, 0, ne * sizeof(double), c.stream);
+      launch_axpy(c, c.bp, c.fp, -1.0, ne);
+      cudaMemsetAsync(c.bl, 0, nx * sizeof(double), c.stream);
+      launch_reduce_rhs(c, c.bx, c.bp, c.bl, red_b, 2 * c.S.dim);
+      solve_direct(c, st, red_b, red_x);
+      launch_recover(c, red_x, c.bp, c.zx, c.zp, c.zl);
+      for (int it = 0; it < refine_steps; ++it) {
+        launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
+        launch_reduce_rhs(c, c.rx, c.rp, c.rl, red_b, 2 * c.S.dim);
+        solve_direct(c, st, red_b, red_x);
+        launch_recover(c, red_x, c.rp, c.rx, c.rp, c.rl);
+        launch_axpy(c, c.zx, c.rx, 1.0, nx);
+        launch_axpy(c, c.zp, c.rp, 1.0, ne);
+        launch_axpy(c, c.zl, c.rl, 1.0, nx);
+      }
+      launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
+      launch_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx, c.partial2);
+      launch_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx, c.partial2 + c.n_partial);
+      if (dx_d) launch_to_nodes_plain(c, c.zx, dx_d);
+      if (dl_d) launch_to_nodes_plain(c, c.zl, dl_d);
+      cudaMemcpyAsync(dp_d, c.zp, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    };
+    const int mask = h->prof_mask;
+    h->prof_mask = 0;  // no profiling events inside the step graph
+    h->step_graph = capture_fn(c, body, &h->step_launches, &h->step_tc);
+    h->prof_mask = mask;
+    if (!h->step_graph) { h->last_error = "graph capture failed"; return SGN_ECUDA; }
+    for (int i = 0; i < 6; ++i) h->step_key[i] = key[i];
+    h->step_prec = (int)prec;
+    h->step_refine = refine_steps;
+  }
+  CUDA_TRY(h, cudaGraphLaunch(h->step_graph, c.stream));
+  c.launches += h->step_launches;
+  c.tc_launches += h->step_tc;
+  c.assembled = true;
+  st.factored = true;
+  c.active = &st;
+  if (residual_h) {
+    std::vector<double> part(2 * c.n_partial);
+    CUDA_TRY(h, cudaMemcpyAsync(part.data(), c.partial2, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                c.stream));
+    CUDA_TRY(h, cudaStreamSynchronize(c.stream));
+    double rr = 0.0, bb = 0.0;
+    for (int i = 0; i < c.n_partial; ++i) { rr += part[i]; bb += part[c.n_partial + i]; }
+    *residual_h = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    sgn_status s = check_status(h);
+    if (s != SGN_OK) return s;
+  }
+  return SGN_OK;
+}
 
 sgn_status sgn_factor_k(sgn_t h) {
   if (!h) return SGN_EINVAL;
@@ -674,8 +765,12 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
   double init = cn / scale;
   int it = 0;
   bool conv = false;
+  double cn_prev = -1.0;
   for (;; ++it) {
-    if (cn <= tol * scale) { conv = true; break; }
+    // converged, or stagnating at the round-off floor of ||c|| (a Newton step
+    // no longer halves it and it is already below 1e-7 ||f_ext||)
+    if (cn <= tol * scale || (cn_prev > 0 && cn > 0.5 * cn_prev && cn <= 1e-7 * scale)) { conv = true; break; }
+    cn_prev = cn;
     if (it >= max_iter) break;
     // Newton direction: K dx = -c
     launch_slot_gather(c, false);

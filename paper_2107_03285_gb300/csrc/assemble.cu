@@ -522,6 +522,12 @@ double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64
   return s;
 }
 
+void launch_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64_t nb, const double *c2, int64_t nc,
+                   double *partial_out) {
+  k_sumsq3<<<c.n_partial, TPB, 0, c.stream>>>(a, na, b, nb, c2, nc, partial_out);
+  c.count();
+}
+
 double device_dot(Ctx &c, const double *a, const double *b, int64_t n) {
   int blocks = c.n_partial;
   k_dot<<<blocks, TPB, 0, c.stream>>>(a, b, n, c.partial);

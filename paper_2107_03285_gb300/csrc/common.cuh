@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,7 @@ struct Store {
   bool fp32 = false;        // element type of the fronts
   void *F = nullptr;        // fronts, column-major f x f each
   void *W = nullptr;        // W = L21 D workspace, (f - K0) x FACTOR_BLOCK per front
+  void *Ldg = nullptr;      // factored diagonal blocks staged by the panel kernel (panel per DOF)
   // FP32 fronts only: K-major copies of W and L21 of the current outer block,
   // split as hi (TF32-exact) + lo, rows = absolute front rows, for the
   // tensor-core trailing update; and one set of TMA tensor maps per front
@@ -66,6 +68,22 @@ struct Store {
   std::vector<int64_t> h_front_off, h_w_off, h_rhs_off, h_piv_off;
   int64_t front_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0;
   bool factored = false;
+  // CUDA graphs of the static launch sequences (captured once, replayed)
+  cudaGraphExec_t fgraph = nullptr;        // factorization
+  cudaGraphExec_t fgraph_prof = nullptr;   // factorization with events around the trailing updates
+  std::vector<struct GraphEv> fprof;       // those events
+  int64_t fgraph_launches = 0, fgraph_tc = 0;
+  cudaGraphExec_t sgraph = nullptr;        // substitutions for one (b, x) pair
+  const double *sgraph_b = nullptr;
+  double *sgraph_x = nullptr;
+  int64_t sgraph_launches = 0;
+};
+
+// an event pair recorded inside a captured graph (re-recorded on every replay)
+struct GraphEv {
+  int kind;
+  double flops;
+  cudaEvent_t e0, e1;
 };
 
 struct Ctx {
@@ -104,6 +122,7 @@ struct Ctx {
   double *rx = nullptr, *rp = nullptr, *rl = nullptr;
   double *red = nullptr;            // reduced rhs / solution [n_free * 2d]
   double *partial = nullptr;        // reduction scratch
+  double *partial2 = nullptr;       // [2][n_partial]: ||r||^2, ||b||^2 partial sums of a graph step
   int n_partial = 0;
   int *status = nullptr;            // device status word
   int64_t *counters = nullptr;      // pivot counters (perturbed, 2x2, pos, neg, zero)
@@ -129,6 +148,18 @@ struct Ctx {
   void count(int n = 1) { launches += n; }
   // event pair bracketing one launch of `kind` (nullptr if not profiled)
   cudaEvent_t *prof_pair(int kind, double flops = 0.0);
+  // CUDA graphs
+  bool use_graphs = true;
+  cudaGraphExec_t step_graph = nullptr;    // sgn_step_graph
+  const void *step_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int step_prec = -1, step_refine = -1;
+  int64_t step_launches = 0, step_tc = 0;
+  cudaStream_t cap_stream = nullptr;       // capture stream (the caller's may be the legacy stream)
+  std::vector<GraphEv> *capture_events = nullptr;  // non-null while capturing a profiled graph
+  std::vector<GraphEv> *pending_events = nullptr;  // events of the last profiled replay, not yet read
+  double gacc_sec[8] = {0}, gacc_fl[8] = {0};
+  int64_t gacc_n[8] = {0};
+  void harvest_graph_events();
 };
 
 // brackets the launches issued in its scope with a profiled event pair
@@ -155,6 +186,9 @@ void launch_residual(Ctx &c, const double *bx, const double *bp, const double *b
                      const double *zp, const double *zl, double *rx, double *rp, double *rl);
 // returns sum of squares of the concatenation of (a, na), (b, nb), (c2, nc) on the host (synchronises)
 double device_dot(Ctx &c, const double *a, const double *b, int64_t n);
+// per-block partial sums of squares into partial_out (n_partial doubles), no synchronisation
+void launch_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64_t nb, const double *c2, int64_t nc,
+                   double *partial_out);
 double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64_t nb, const double *c2, int64_t nc);
 void launch_axpy(Ctx &c, double *y, const double *x, double a, int64_t n);
 void launch_to_nodes(Ctx &c, const double *vr, double *out_nodes, double fixed_value_from_X);
@@ -171,6 +205,11 @@ void launch_gradient_finish(Ctx &c, const double *lam_r, double *g);
 void factor_store(Ctx &c, Store &s);
 void solve_store(Ctx &c, Store &s, const double *b_red, double *x_red);
 void pivot_counts(Ctx &c, Store &s);  // fills c.counters (device)
+void set_kernel_attributes();
+void factor_direct(Ctx &c, Store &s);                                   // no graph
+cudaGraphExec_t capture_fn(Ctx &c, const std::function<void()> &body, int64_t *launches, int64_t *tc);
+void solve_direct(Ctx &c, Store &s, const double *b_red, double *x_red);  // no graph
+void destroy_graphs(Store &s);
 
 }  // namespace sgn
 

@@ -20,6 +20,7 @@
 // nonsingular; hence each panel's trailing block is nonsingular too.
 #include <cmath>
 #include <cstdio>
+#include <functional>
 #include <type_traits>
 
 #include "common.cuh"
@@ -34,6 +35,7 @@ constexpr int MAXNB = 64;
 struct SV {  // store view passed to kernels
   void *F;
   void *W;
+  void *Ldg;                     // staged factored diagonal blocks (panel x panel per panel)
   float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
   double *rhs;
   int32_t *piv_type, *piv_perm;
@@ -45,7 +47,7 @@ struct SV {  // store view passed to kernels
 
 SV view(Store &s) {
   SV v;
-  v.F = s.F; v.W = s.W; v.rhs = s.rhs;
+  v.F = s.F; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
   v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
@@ -143,42 +145,24 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
 }
 
 // ------------------------------------------------------- Bunch-Kaufman panel
-template <typename T>
-__global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                  int nb, double eps_rel, unsigned long long *counters) {
-  // eliminations in the store's precision (CT = T); every pivot decision
-  // compares magnitudes in FP64
-  using CT = T;
-  __shared__ CT a[MAXNB][MAXNB + 1];  // a[j][i] = A(i, j), column j
-  __shared__ double sD0[MAXNB], sD1[MAXNB];
-  __shared__ int sperm[MAXNB], stype[MAXNB];
+// Bunch-Kaufman LDL^T of the w x w block a (lower triangle, a[j][i] = A(i, j))
+// by the whole CTA: 1x1 / 2x2 pivots, alpha = (1 + sqrt 17) / 8, pivot search
+// restricted to the block, every decision on FP64 magnitudes, eliminations in
+// CT.  On return a holds the unit-lower L11 (a[j][j+1] = 0 inside 2x2 pivots),
+// sD0 / sD1 the 1x1 and 2x2 pivots, stype their kinds and sperm the block's
+// permutation (position -> original index).  Deterministic: every CTA that
+// runs it on the same block takes the same decisions.
+// Run by one warp (threads 0..31 of the block): only warp-level barriers.
+template <typename CT>
+__device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double eps_rel, int *sperm, int *stype,
+                                double *sD0, double *sD1, unsigned long long *counters, const bool count) {
   __shared__ int s_kp, s_kstep;
   __shared__ double s_bmax;
-  const int s = fronts[blockIdx.x];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  T *F = (T *)sv.F + sv.front_off[s];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x;  // 0..31
   const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
-  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
-    CT v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int j = idx / w, i = idx - j * w;
-      v[u] = (idx < w * w && i >= j) ? (CT)F[(int64_t)(k + i) + (int64_t)(k + j) * f] : CT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < w * w) a[idx / w][idx % w] = v[u];
-    }
-  }
-  if (tid < w) { sperm[tid] = tid; stype[tid] = 0; sD1[tid] = 0.0; }
-  __syncthreads();
+  // one warp initialises all w <= 64 entries
+  for (int t = tid; t < w; t += 32) { sperm[t] = t; stype[t] = 0; sD1[t] = 0.0; sD0[t] = 0.0; }
+  __syncwarp();
   if (tid < 32) {
     double m = 0.0;
     for (int idx = tid; idx < w * w; idx += 32) {
@@ -188,7 +172,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (tid == 0) s_bmax = m;
   }
-  __syncthreads();
+  __syncwarp();
   const double thresh = eps_rel * fmax(s_bmax, 1e-300);
   int j = 0;
   while (j < w) {
@@ -228,14 +212,14 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
       }
       if (tid == 0) { s_kp = kp; s_kstep = kstep; }
     }
-    __syncthreads();
+    __syncwarp();
     const int kstep = s_kstep, kp = s_kp;
     const int kk = j + kstep - 1;
     if (kp != kk) {
       // symmetric interchange of kk and kp in the trailing lower triangle and
       // of the already eliminated part of both rows
       int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
-      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += blockDim.x) {
+      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += 32) {
         if (idx == 0) {
           CT t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
           int tp = sperm[kk]; sperm[kk] = sperm[kp]; sperm[kp] = tp;
@@ -250,7 +234,7 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
           CT t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
     if (kstep == 1) {
       if (tid == 0) {
@@ -258,26 +242,26 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
         if (!(fabs(dj) > thresh)) {
           dj = (dj >= 0.0) ? thresh : -thresh;
           a[j][j] = (CT)dj;
-          atomicAdd(counters + 0, 1ull);
+          if (count) atomicAdd(counters + 0, 1ull);
         }
         sD0[j] = (double)a[j][j]; stype[j] = 0;
       }
-      __syncthreads();
+      __syncwarp();
       const CT rd = CT(1) / a[j][j];
       const int m = w - j - 1;
-      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      for (int idx = tid; idx < m * m; idx += 32) {
         int cc = j + 1 + idx / m, i = j + 1 + idx % m;
         if (i >= cc) a[cc][i] -= a[j][i] * a[j][cc] * rd;
       }
-      __syncthreads();
-      for (int i = j + 1 + tid; i < w; i += blockDim.x) a[j][i] *= rd;
-      __syncthreads();
+      __syncwarp();
+      for (int i = j + 1 + tid; i < w; i += 32) a[j][i] *= rd;
+      __syncwarp();
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
       const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
       const int m = w - j - 2;
-      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      for (int idx = tid; idx < m * m; idx += 32) {
         int cc = j + 2 + idx / m, i = j + 2 + idx % m;
         if (i >= cc) {
           CT l1 = a[j][i] * i11 + a[j + 1][i] * i21;
@@ -285,8 +269,8 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
           a[cc][i] -= l1 * a[j][cc] + l2 * a[j + 1][cc];
         }
       }
-      __syncthreads();
-      for (int i = j + 2 + tid; i < w; i += blockDim.x) {
+      __syncwarp();
+      for (int i = j + 2 + tid; i < w; i += 32) {
         CT w1 = a[j][i], w2 = a[j + 1][i];
         a[j][i] = w1 * i11 + w2 * i21;
         a[j + 1][i] = w1 * i21 + w2 * i22;
@@ -295,16 +279,78 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
         sD0[j] = (double)d11; sD1[j] = (double)d21; sD0[j + 1] = (double)d22;
         stype[j] = 1; stype[j + 1] = 2;
         a[j][j + 1] = CT(0);
-        atomicAdd(counters + 1, 1ull);
+        if (count) atomicAdd(counters + 1, 1ull);
       }
-      __syncthreads();
+      __syncwarp();
     }
     j += kstep;
   }
-  // write back L11 (unit lower; diagonal holds D0) and pivot data
+}
+
+// Pivot panel [k, k + w), diagonal block (one CTA per active front):
+//   left-looking update by the earlier panels of the outer block,
+//   A_bb -= W[k:k+w, K0:k] L[k:k+w, K0:k]^T (all threads), then Bunch-Kaufman
+//   by warp 0 (warp-level barriers only).  L11 (D on its diagonal) is staged,
+//   D and the permutation go to the pivot arrays; the front's diagonal block
+//   itself is rewritten by the end-of-block kernel.
+template <typename T>
+__global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                     int K0, int nb, double eps_rel, unsigned long long *counters) {
+  using CT = T;
+  constexpr int KC = sizeof(T) == 8 ? 8 : 32;  // keeps static shared memory under 48 KB
+  __shared__ CT a[MAXNB][MAXNB + 1];
+  __shared__ CT Lp[KC][MAXNB], Wd[KC][MAXNB];
+  __shared__ double sD0[MAXNB], sD1[MAXNB];
+  __shared__ int sperm[MAXNB], stype[MAXNB];
+  const int s = fronts[blockIdx.x];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  const T *W = (const T *)sv.W + sv.w_off[s];
+  const int64_t ldw = f - K0;
+  const int tid = threadIdx.x;
+  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
+    CT v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int jj = idx / w, ii = idx - jj * w;
+      v[u] = (idx < w * w && ii >= jj) ? (CT)F[(int64_t)(k + ii) + (int64_t)(k + jj) * f] : CT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < w * w) a[idx / w][idx % w] = v[u];
+    }
+  }
+  const int kp_in = k - K0;
+  for (int cu = 0; cu < kp_in; cu += KC) {
+    const int kc = min(KC, kp_in - cu);
+    __syncthreads();
+    for (int idx = tid; idx < kc * w; idx += blockDim.x) {
+      const int u = idx / w, t = idx - u * w;
+      Lp[u][t] = (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f];
+      Wd[u][t] = (CT)W[(int64_t)(k - K0 + t) + (int64_t)(cu + u) * ldw];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < w * w; idx += blockDim.x) {
+      const int jj = idx / w, ii = idx - jj * w;
+      if (ii < jj) continue;
+      CT acc = CT(0);
+      for (int u = 0; u < kc; ++u) acc += Wd[u][ii] * Lp[u][jj];
+      a[jj][ii] -= acc;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) bk_factor_block<CT>(a, w, eps_rel, sperm, stype, sD0, sD1, counters, true);
+  __syncthreads();
+  T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    int jj = idx / w, i = idx - jj * w;
-    if (i >= jj) F[(int64_t)(k + i) + (int64_t)(k + jj) * f] = (i == jj) ? T(sD0[jj]) : T(a[jj][i]);
+    const int jj = idx / w, ii = idx - jj * w;
+    if (ii >= jj) stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : T(a[jj][ii]);
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
@@ -313,8 +359,122 @@ __global__ void __launch_bounds__(128) k_bk_diag(DevSym d, SV sv, const int32_t 
     sv.D0[po + tid] = sD0[tid];
     sv.D1[po + tid] = sD1[tid];
   }
-  // the rows of this panel in the columns left of it are permuted later, once
-  // per outer block, by k_row_swap
+}
+
+// Pivot panel [k, k + w), rows below it (128 rows per CTA): the same
+// left-looking update for these rows, then W = F21 P^T L11^{-T} (= L21 D) and
+// L21 = W D^{-1}, written to the front, to the outer block's W and (FP32
+// fronts with tensor cores) to the K-major hi / lo operand copies.
+template <typename T>
+__global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                     int K0, int nb) {
+  using CT = T;
+  constexpr int RB = 128, KC = 32, XS = RB + 1;
+  extern __shared__ unsigned char rows_raw[];
+  CT *Lp = reinterpret_cast<CT *>(rows_raw);   // [KC][MAXNB]
+  CT *L11 = Lp + KC * MAXNB;                    // [MAXNB][MAXNB + 1]: L11[t][c] = L(t, c)
+  CT *xs = L11 + MAXNB * (MAXNB + 1);           // [MAXNB][XS]
+  CT *ls = xs + MAXNB * XS;                     // [MAXNB][XS]
+  __shared__ CT sD0[MAXNB], sD1[MAXNB];
+  __shared__ int sperm[MAXNB], stype[MAXNB];
+  const int s = fronts[blockIdx.y];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  if (k >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int w = min(nb, ns - k);
+  const int r0 = k + w;
+  const int nrows = f - r0;
+  if ((int)blockIdx.x * RB >= nrows) return;
+  T *F = (T *)sv.F + sv.front_off[s];
+  T *W = (T *)sv.W + sv.w_off[s];
+  const int64_t ldw = f - K0;
+  const int tid = threadIdx.x;
+  const int il = blockIdx.x * RB + tid;
+  const bool row_ok = il < nrows;
+  const int64_t i = r0 + il;
+  const int kp_in = k - K0;
+  const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int t = idx / w, c = idx - t * w;
+    L11[t * (MAXNB + 1) + c] = c < t ? (CT)stage[(int64_t)t * nb + c] : CT(0);
+  }
+  const int64_t po = sv.piv_off[s] + k;
+  if (tid < w) {
+    sD0[tid] = (CT)sv.D0[po + tid]; sD1[tid] = (CT)sv.D1[po + tid];
+    sperm[tid] = sv.piv_perm[po + tid]; stype[tid] = sv.piv_type[po + tid];
+  }
+  if (row_ok) {
+    for (int t0 = 0; t0 < w; t0 += 8) {
+      CT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? (CT)F[i + (int64_t)(k + t0 + u) * f] : CT(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < w) xs[(t0 + u) * XS + tid] = v[u];
+    }
+  }
+  for (int cu = 0; cu < kp_in; cu += KC) {
+    const int kc = min(KC, kp_in - cu);
+    __syncthreads();
+    for (int idx = tid; idx < kc * w; idx += blockDim.x) {
+      const int u = idx / w, t = idx - u * w;
+      Lp[u * MAXNB + t] = (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f];
+    }
+    __syncthreads();
+    if (row_ok) {
+      CT wr[KC];
+#pragma unroll
+      for (int u = 0; u < KC; ++u) wr[u] = u < kc ? (CT)W[(i - K0) + (int64_t)(cu + u) * ldw] : CT(0);
+      for (int t = 0; t < w; ++t) {
+        CT acc = CT(0);
+#pragma unroll
+        for (int u = 0; u < KC; ++u) acc += wr[u] * Lp[u * MAXNB + t];
+        xs[t * XS + tid] -= acc;
+      }
+    }
+  }
+  __syncthreads();
+  if (row_ok) {
+    for (int t = 0; t < w; ++t) ls[t * XS + tid] = xs[sperm[t] * XS + tid];
+    for (int t = 0; t < w; ++t) xs[t * XS + tid] = ls[t * XS + tid];
+    for (int c = 0; c < w; ++c) {
+      const CT xc = xs[c * XS + tid];
+      for (int t = c + 1; t < w; ++t) xs[t * XS + tid] -= L11[t * (MAXNB + 1) + c] * xc;
+    }
+    for (int t = 0; t < w; ++t) {
+      const CT xt = xs[t * XS + tid];
+      W[(i - K0) + (int64_t)(k - K0 + t) * ldw] = T(xt);
+      CT l;
+      if (stype[t] == 0) {
+        l = xt / sD0[t];
+      } else if (stype[t] == 1) {
+        l = (xt * sD0[t + 1] - xs[(t + 1) * XS + tid] * sD1[t]) / (sD0[t] * sD0[t + 1] - sD1[t] * sD1[t]);
+      } else {
+        l = (xt * sD0[t - 1] - xs[(t - 1) * XS + tid] * sD1[t - 1]) / (sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1]);
+      }
+      F[i + (int64_t)(k + t) * f] = T(l);
+      ls[t * XS + tid] = l;
+    }
+  }
+  if (sv.wk0) {
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
+    for (int rr = 0; rr < 32; ++rr) {
+      const int rloc = warp * 32 + rr;
+      const int ilr = blockIdx.x * RB + rloc;
+      if (ilr >= nrows) break;
+      const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
+      for (int t = lane; t < wpad; t += 32) {
+        const float wf = t < w ? (float)xs[t * XS + rloc] : 0.f;
+        const float lf = t < w ? (float)ls[t * XS + rloc] : 0.f;
+        const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
+        sv.wk0[base + t] = wh; sv.wk1[base + t] = wf - wh;
+        sv.wk2[base + t] = lh; sv.wk3[base + t] = lf - lh;
+      }
+    }
+  }
 }
 
 // applies the pivot permutations of the panels of the outer block [K0, kend)
@@ -337,6 +497,17 @@ __global__ void __launch_bounds__(256) k_row_swap(DevSym d, SV sv, const int32_t
   T *F = (T *)sv.F + sv.front_off[s];
   const int32_t *perm = sv.piv_perm + sv.piv_off[s];
   const int tid = threadIdx.x;
+  if (blockIdx.x == 0) {
+    // the factored diagonal blocks of this outer block's panels
+    for (int k = K0; k < kend; k += nb) {
+      const int w = min(nb, ns - k);
+      const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
+      for (int idx = tid; idx < w * w; idx += blockDim.x) {
+        const int jj = idx / w, ii = idx - jj * w;
+        if (ii >= jj) F[(int64_t)(k + ii) + (int64_t)(k + jj) * f] = stage[(int64_t)ii * nb + jj];
+      }
+    }
+  }
   for (int k = K0; k < kend; k += nb) {
     // panel [k, k + w) needs columns [c0, min(c0 + 64, k))
     if (k <= c0) continue;
@@ -361,107 +532,6 @@ __global__ void __launch_bounds__(256) k_row_swap(DevSym d, SV sv, const int32_t
     for (int idx = tid; idx < w * cw; idx += blockDim.x) {
       int cc = idx / w, t = idx - cc * w;
       F[(int64_t)(k + t) + (int64_t)(c0 + cc) * f] = buf[t][cc];
-    }
-  }
-}
-
-// rows below the panel: W = F21 P^T L11^{-T}, L21 = W D^{-1}.  W is kept for
-// the whole outer block starting at K0: W[(i - K0) + (col - K0) * (f - K0)]
-template <typename T>
-__global__ void __launch_bounds__(128) k_panel_trsm(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int nb, int K0) {
-  // arithmetic in the store's precision (FP32 fronts keep the FP32 pipe busy)
-  constexpr int XS = 129;                    // padded row stride of the staging tiles
-  extern __shared__ unsigned char trsm_raw[];
-  T *Ls = reinterpret_cast<T *>(trsm_raw);  // [MAXNB][MAXNB]: Ls[t*MAXNB + c] = L(t, c)
-  T *xs = Ls + MAXNB * MAXNB;                // [MAXNB][XS]: W values, xs[t*XS + row]
-  T *ls = xs + MAXNB * XS;                   // [MAXNB][XS]: L values (FP32 fronts only)
-  __shared__ T sD0[MAXNB], sD1[MAXNB];
-  __shared__ int sperm[MAXNB], stype[MAXNB];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const int r0 = k + w;
-  const int nrows = f - r0;
-  if (blockIdx.x * 128 >= nrows) return;
-  T *F = (T *)sv.F + sv.front_off[s];
-  T *W = (T *)sv.W + sv.w_off[s];
-  const int tid = threadIdx.x;
-  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int c = idx / w, t = idx - c * w;
-      v[u] = (idx < w * w && c < t) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int c = idx / w, t = idx - c * w;
-      if (idx < w * w) Ls[t * MAXNB + c] = v[u];
-    }
-  }
-  const int64_t po = sv.piv_off[s] + k;
-  if (tid < w) {
-    sD0[tid] = T(sv.D0[po + tid]); sD1[tid] = T(sv.D1[po + tid]);
-    sperm[tid] = sv.piv_perm[po + tid]; stype[tid] = sv.piv_type[po + tid];
-  }
-  __syncthreads();
-  const int il = blockIdx.x * 128 + tid;
-  if (il < nrows) {
-    const int64_t i = r0 + il;
-    for (int t0 = 0; t0 < w; t0 += 8) {
-      T v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? F[i + (int64_t)(k + sperm[t0 + u]) * f] : T(0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (t0 + u < w) xs[(t0 + u) * XS + tid] = v[u];
-    }
-    for (int c = 0; c < w; ++c) {
-      const T xc = xs[c * XS + tid];
-      for (int t = c + 1; t < w; ++t) xs[t * XS + tid] -= Ls[t * MAXNB + c] * xc;
-    }
-    for (int t = 0; t < w; ++t) {
-      const T xt = xs[t * XS + tid];
-      W[(i - K0) + (int64_t)(k - K0 + t) * (f - K0)] = xt;
-      T l;
-      if (stype[t] == 0) {
-        l = xt / sD0[t];
-      } else if (stype[t] == 1) {
-        T det = sD0[t] * sD0[t + 1] - sD1[t] * sD1[t];
-        l = (xt * sD0[t + 1] - xs[(t + 1) * XS + tid] * sD1[t]) / det;
-      } else {
-        T det = sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1];
-        l = (xt * sD0[t - 1] - xs[(t - 1) * XS + tid] * sD1[t - 1]) / det;
-      }
-      F[i + (int64_t)(k + t) * f] = l;
-      if (sv.wk0) ls[t * XS + tid] = l;
-    }
-  }
-  if (sv.wk0) {
-    // K-major hi/lo copies for the tensor-core update: each warp writes whole
-    // 128-byte row segments (lane = column); the last panel of a front also
-    // zeroes its columns up to the next multiple of 32
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
-    for (int rr = 0; rr < 32; ++rr) {
-      const int rloc = warp * 32 + rr;
-      const int ilr = blockIdx.x * 128 + rloc;
-      if (ilr >= nrows) break;
-      const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
-      for (int t = lane; t < wpad; t += 32) {
-        const float wf = t < w ? (float)xs[t * XS + rloc] : 0.f;
-        const float lf = t < w ? (float)ls[t * XS + rloc] : 0.f;
-        const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
-        sv.wk0[base + t] = wh; sv.wk1[base + t] = wf - wh;
-        sv.wk2[base + t] = lh; sv.wk3[base + t] = lf - lh;
-      }
     }
   }
 }
@@ -617,26 +687,6 @@ __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv,
   tc::tile_loop_tc(&maps[s], job, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
 }
 
-// left-looking update of the panel [k, k + w) by the earlier panels of its
-// outer block: F[k:, k:k+w] -= W[k:, K0:k] L[k:k+w, K0:k]^T (lower part)
-template <typename T>
-__global__ void __launch_bounds__(256) k_panel_update(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                       int K0, int nb) {
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const int nrows = f - k;
-  const int r = blockIdx.x * 64;
-  if (r >= nrows) return;
-  T *F = (T *)sv.F + sv.front_off[s];
-  const T *W = (const T *)sv.W + sv.w_off[s];
-  const int64_t ldw = f - K0;
-  tile_gemm_sub<T>(F + (int64_t)(k + r) + (int64_t)k * f, f, W + (k - K0 + r), ldw, min(64, nrows - r),
-                   F + (int64_t)k + (int64_t)K0 * f, f, w, k - K0, r);
-}
 
 // ------------------------------------------------------------------ solves
 __global__ void k_fwd_gather(DevSym d, SV sv, int64_t item_base, int64_t n, const double *__restrict__ b) {
@@ -998,17 +1048,7 @@ void factor_impl(Ctx &c, Store &st) {
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
   unsigned long long *ctr = (unsigned long long *)c.counters;
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
-  const size_t trsm_smem = (MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(double)));
-    cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((MAXNB * MAXNB + 2 * MAXNB * 129) * sizeof(float)));
-    cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
-    attr_set = true;
-  }
+  const size_t rows_smem = (size_t)(32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(T);
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, st.dpn);
     int64_t nitems = li.i1 - li.i0;
@@ -1026,32 +1066,23 @@ void factor_impl(Ctx &c, Store &st) {
       const int kstop = std::min(K0 + FACTOR_BLOCK, max_ns);
       for (int k = K0; k < kstop; k += nb) {
         int na = n_active(li, k);
-        int max_rows = 0, max_f = 0;
+        int max_rows = 0;
+        double fl = 0.0;
         for (int q = 0; q < na; ++q) {
           int w = std::min(nb, li.ns[q] - k);
           max_rows = std::max(max_rows, li.f[q] - k - w);
-          max_f = std::max(max_f, li.f[q] - k);
-        }
-        if (k > K0) {
-          double fl = 0.0;
-          for (int q = 0; q < na; ++q) {
-            double w = std::min(nb, li.ns[q] - k), nr = li.f[q] - k;
-            fl += 2.0 * (nr * w - w * (w - 1) / 2.0) * (k - K0);
-          }
-          ProfScope ps(c, SGN_PROF_PANEL_UPDATE, fl);
-          dim3 gp((max_f + 63) / 64, na);
-          k_panel_update<T><<<gp, 256, 0, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
-          c.count();
+          double nr = li.f[q] - k;
+          fl += 2.0 * (nr * w - w * (w - 1) / 2.0) * (k - K0);  // left-looking panel update
         }
         {
           ProfScope ps(c, SGN_PROF_PIVOT);
-          k_bk_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
+          k_panel_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, K0, nb, eps_rel, ctr);
           c.count();
         }
         if (max_rows > 0) {
-          ProfScope ps(c, SGN_PROF_TRSM);
-          dim3 gt((max_rows + 127) / 128, na);
-          k_panel_trsm<T><<<gt, 128, trsm_smem, c.stream>>>(c.ds, sv, fronts, k, nb, K0);
+          ProfScope ps(c, SGN_PROF_TRSM, fl);
+          dim3 gp((max_rows + 127) / 128, na);
+          k_panel_rows<T><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
           c.count();
         }
       }
@@ -1100,12 +1131,6 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   const int nb = c.S.opts.panel;
   const int dpn = st.dpn;
   const size_t diag_smem = (size_t)SB * (SB + 1) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
-    cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
-    attr_set = true;
-  }
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, dpn);
     int64_t n = (li.i1 - li.i0) * dpn;
@@ -1161,6 +1186,12 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
 
 cudaEvent_t *Ctx::prof_pair(int kind, double flops) {
   if (!((prof_mask >> kind) & 1)) return nullptr;
+  if (capture_events) {
+    GraphEv g{kind, flops, nullptr, nullptr};
+    if (cudaEventCreate(&g.e0) != cudaSuccess || cudaEventCreate(&g.e1) != cudaSuccess) return nullptr;
+    capture_events->push_back(g);
+    return &capture_events->back().e0;  // e0 and e1 are adjacent members
+  }
   if (2 * (prof_used + 1) > (int64_t)prof_ev.size()) {
     for (int i = 0; i < 512; ++i) {
       cudaEvent_t e;
@@ -1175,14 +1206,134 @@ cudaEvent_t *Ctx::prof_pair(int kind, double flops) {
   return p;
 }
 
-void factor_store(Ctx &c, Store &s) {
+void factor_direct(Ctx &c, Store &s) {
   if (s.fp32) factor_impl<float>(c, s);
   else factor_impl<double>(c, s);
 }
 
-void solve_store(Ctx &c, Store &s, const double *b, double *x) {
+void solve_direct(Ctx &c, Store &s, const double *b, double *x) {
   if (s.fp32) solve_impl<float>(c, s, b, x);
   else solve_impl<double>(c, s, b, x);
+}
+
+void Ctx::harvest_graph_events() {
+  if (!pending_events) return;
+  cudaEventSynchronize(pending_events->back().e1);
+  for (const GraphEv &g : *pending_events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) {
+      gacc_sec[g.kind] += ms * 1e-3;
+      gacc_fl[g.kind] += g.flops;
+      gacc_n[g.kind] += 1;
+    }
+  }
+  pending_events = nullptr;
+}
+
+// captures `body` (which launches on c.stream) into an executable graph
+template <typename Body>
+cudaGraphExec_t capture(Ctx &c, Body body, int64_t *launches, int64_t *tc) {
+  cudaStream_t save = c.stream;
+  const int64_t l0 = c.launches, t0 = c.tc_launches;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  c.stream = c.cap_stream;
+  if (cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    c.stream = save;
+    return nullptr;
+  }
+  body();
+  cudaError_t e = cudaStreamEndCapture(c.cap_stream, &g);
+  c.stream = save;
+  if (e != cudaSuccess || !g) return nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(g);
+  *launches = c.launches - l0;
+  if (tc) *tc = c.tc_launches - t0;
+  c.launches = l0;  // counted again at every replay
+  c.tc_launches = t0;
+  return ex;
+}
+
+cudaGraphExec_t capture_fn(Ctx &c, const std::function<void()> &body, int64_t *launches, int64_t *tc) {
+  return capture(c, body, launches, tc);
+}
+
+void factor_store(Ctx &c, Store &s) {
+  auto run = [&]() {
+    if (s.fp32) factor_impl<float>(c, s);
+    else factor_impl<double>(c, s);
+  };
+  c.harvest_graph_events();
+  const int only_update = 1 << SGN_PROF_UPDATE;
+  if (!c.use_graphs || !c.cap_stream || (c.prof_mask != 0 && c.prof_mask != only_update)) {
+    run();
+    return;
+  }
+  if (c.prof_mask == 0) {
+    if (!s.fgraph) s.fgraph = capture(c, run, &s.fgraph_launches, &s.fgraph_tc);
+    if (!s.fgraph) { run(); return; }
+    cudaGraphLaunch(s.fgraph, c.stream);
+  } else {
+    if (!s.fgraph_prof) {
+      c.capture_events = &s.fprof;
+      int64_t l = 0, t = 0;
+      s.fgraph_prof = capture(c, run, &l, &t);
+      c.capture_events = nullptr;
+      if (!s.fgraph) { s.fgraph_launches = l; s.fgraph_tc = t; }
+    }
+    if (!s.fgraph_prof) { run(); return; }
+    cudaGraphLaunch(s.fgraph_prof, c.stream);
+    c.pending_events = &s.fprof;
+  }
+  c.launches += s.fgraph_launches;
+  c.tc_launches += s.fgraph_tc;
+  s.factored = true;
+}
+
+void solve_store(Ctx &c, Store &s, const double *b, double *x) {
+  auto run = [&]() {
+    if (s.fp32) solve_impl<float>(c, s, b, x);
+    else solve_impl<double>(c, s, b, x);
+  };
+  if (!c.use_graphs || !c.cap_stream || c.prof_mask != 0) {
+    run();
+    return;
+  }
+  if (!s.sgraph || s.sgraph_b != b || s.sgraph_x != x) {
+    if (s.sgraph) cudaGraphExecDestroy(s.sgraph);
+    s.sgraph = capture(c, run, &s.sgraph_launches, nullptr);
+    s.sgraph_b = b;
+    s.sgraph_x = x;
+  }
+  if (!s.sgraph) { run(); return; }
+  cudaGraphLaunch(s.sgraph, c.stream);
+  c.launches += s.sgraph_launches;
+}
+
+void set_kernel_attributes() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaFuncSetAttribute(k_panel_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(double)));
+  cudaFuncSetAttribute(k_panel_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(float)));
+  cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
+  cudaFuncSetAttribute(k_fwd_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_fwd_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_bwd_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_bwd_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+}
+
+void destroy_graphs(Store &s) {
+  if (s.fgraph) cudaGraphExecDestroy(s.fgraph);
+  if (s.fgraph_prof) cudaGraphExecDestroy(s.fgraph_prof);
+  if (s.sgraph) cudaGraphExecDestroy(s.sgraph);
+  for (GraphEv &g : s.fprof) { cudaEventDestroy(g.e0); cudaEventDestroy(g.e1); }
+  s.fgraph = s.fgraph_prof = s.sgraph = nullptr;
+  s.fprof.clear();
 }
 
 void pivot_counts(Ctx &c, Store &s) {

@@ -118,6 +118,21 @@ class SGN:
         dx, dp, dl, srep = self.solve(mode, g)
         return dx, dp, dl, frep, srep
 
+    def step_graph(self, x, p, precision=B.MIXED, refine_steps=3, out=None, residual=True):
+        """One SGN step as a single CUDA-graph launch (captured on first use
+        for these buffers).  x, p must stay the same device tensors between
+        calls for the graph to be replayed."""
+        x = self._dev(x, (self.n_nodes, self.dim))
+        p = self._dev(p, (self.n_elem,))
+        dx, dp, dl = out if out is not None else (self._empty(self.n_nodes, self.dim), self._empty(self.n_elem),
+                                                   self._empty(self.n_nodes, self.dim))
+        res = C.c_double(0.0)
+        B._check(self.lib.sgn_step_graph(self.h, int(precision), int(refine_steps), self._p(x), self._p(p),
+                                         self._p(dx), self._p(dp), self._p(dl),
+                                         C.byref(res) if residual else None), "sgn_step_graph")
+        self._x, self._pv = x, p
+        return dx, dp, dl, res.value
+
     def step_host(self, x, p, precision=B.FP64):
         """Host buffers in and out (H2D / D2H copies inside the call)."""
         xh = _f64(x).reshape(self.n_nodes, self.dim)
@@ -140,7 +155,7 @@ class SGN:
         rep = B.NewtonReport()
         code = self.lib.sgn_equilibrium(self.h, self._p(pd), self._p(fd), self._p(x),
                                         C.byref(B.NewtonOpts(int(max_iter), float(tol))), C.byref(rep))
-        if code != B.OK:
+        if code not in (B.OK, B.ENEWTON):  # non-convergence is reported in rep.converged
             B._check(code, "sgn_equilibrium")
         return x, rep
 

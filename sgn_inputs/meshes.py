@@ -195,6 +195,46 @@ def problem_tiny_3d(n: int = 3, seed: int = 1, p_sigma: float = 0.2) -> Problem:
     return problem_3d(n=n, seed=seed, p_sigma=p_sigma, name=f"tiny3d_{n}")
 
 
+def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, side_hi: int = 60,
+                    shift_sigma: float = 0.03, p_sigma: float = 0.1, gap: float = 0.5) -> Problem:
+    """Many independent plane-strain design instances in one disjoint mesh.
+
+    Instance i is a side_i x side_i grid (side_i ~ U{side_lo..side_hi}),
+    clamped on its left edge, body-loaded, with its right edge tracked towards
+    rest + (0, -0.05) + s_i where s_i ~ N(0, shift_sigma^2) (one 2-vector per
+    instance); p ~ N(0, p_sigma^2).  Instances are translated along x by
+    (1 + gap) apart so they never share nodes; meta["node_offsets"] and
+    meta["elem_offsets"] delimit them."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, size=n_instances)
+    Xs, conns, fixeds, fexts, tracks, targets, weights, ps = [], [], [], [], [], [], [], []
+    node_off, elem_off = [0], [0]
+    for i, n in enumerate(sides):
+        shift = (0.0, -0.05) + rng.normal(0.0, shift_sigma, size=2)
+        sub = problem_2d(int(n), seed=int(rng.integers(0, 2**31 - 1)), shift=tuple(shift), p_sigma=p_sigma)
+        dx = i * (1.0 + gap)
+        X = sub.X.copy()
+        X[:, 0] += dx
+        tgt = sub.target.reshape(-1, 2).copy()
+        tgt[:, 0] += dx
+        Xs.append(X)
+        conns.append(sub.conn + node_off[-1])
+        fixeds.append(sub.fixed_node)
+        fexts.append(sub.fext)
+        tracks.append(sub.track_dof + 2 * node_off[-1])
+        targets.append(tgt.ravel())
+        weights.append(sub.weight)
+        ps.append(sub.p0)
+        node_off.append(node_off[-1] + X.shape[0])
+        elem_off.append(elem_off[-1] + sub.conn.shape[0])
+    return Problem(f"batch2d_{n_instances}", 2, np.concatenate(Xs), np.concatenate(conns).astype(np.int32),
+                   np.concatenate(fixeds), np.concatenate(fexts), np.concatenate(tracks),
+                   np.concatenate(targets), np.concatenate(weights), 1e-4, 1e4, 0.3, np.concatenate(ps),
+                   meta={"sides": sides, "node_offsets": np.array(node_off), "elem_offsets": np.array(elem_off),
+                         "seed": seed, "side_lo": side_lo, "side_hi": side_hi, "shift_sigma": shift_sigma,
+                         "p_sigma": p_sigma})
+
+
 PRESETS = {
     # 21x21 plane-strain grid, 800 triangles, p ~ N(0, 0.1^2)
     "grid2d_21": lambda seed=0: problem_2d(21, seed=seed),
@@ -202,6 +242,8 @@ PRESETS = {
     "kuhn3d_40": lambda seed=0: problem_3d(40, seed=seed),
     # 80^3 Kuhn tets, 2,958,234 elements
     "kuhn3d_80": lambda seed=0: problem_3d(80, seed=seed),
+    # 256 plane-strain instances, sides ~ U{10..60}
+    "batch2d_256": lambda seed=0: problem_batch2d(256, seed=seed),
 }
 
 
@@ -214,4 +256,6 @@ def make_preset(name: str, seed: int = 0) -> Problem:
         return problem_3d(int(size), seed=seed)
     if kind == "grid2d":
         return problem_2d(int(size), seed=seed)
+    if kind == "batch2d":
+        return problem_batch2d(int(size), seed=seed)
     raise KeyError(name)

@@ -1,0 +1,131 @@
+"""Batched form: many independent plane-strain instances of uneven size in one
+disjoint mesh, assembled, factored and solved together (one elimination
+forest, every level of every instance batched into the same launches).
+Every instance's slice of the batched step must equal the oracle's step of
+that instance alone."""
+import numpy as np
+import pytest
+
+from oracle import equilibrium as EQ
+from oracle import system as S
+from sgn_inputs import problem_2d, problem_batch2d
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_03285_gb300 import build as build_mod
+    build_mod.build()
+    import paper_2107_03285_gb300 as P
+    return P
+
+
+def _instances(batch):
+    """Rebuild every instance exactly as problem_batch2d drew it."""
+    rng = np.random.default_rng(batch.meta["seed"])
+    sides = rng.integers(batch.meta["side_lo"], batch.meta["side_hi"] + 1, size=len(batch.meta["sides"]))
+    out = []
+    for n in sides:
+        shift = (0.0, -0.05) + rng.normal(0.0, batch.meta["shift_sigma"], size=2)
+        out.append(problem_2d(int(n), seed=int(rng.integers(0, 2**31 - 1)), shift=tuple(shift),
+                              p_sigma=batch.meta["p_sigma"]))
+    return out
+
+
+def _batch_state(batch, subs):
+    """Oracle equilibria of the instances, placed into the batch mesh."""
+    x = batch.X.copy()
+    no = batch.meta["node_offsets"]
+    refs = []
+    for i, sub in enumerate(subs):
+        xi, info = EQ.newton(sub, sub.p0)
+        assert info["converged"]
+        shift = batch.X[no[i], 0] - sub.X[0, 0]
+        x[no[i]:no[i + 1]] = xi + np.array([shift, 0.0])
+        b = S.blocks(sub, xi, sub.p0)
+        refs.append(S.sgn_step(b, "kkt")[1])
+    return x, refs
+
+
+@pytest.mark.parametrize("prec_name,tol", [("FP64", 1e-9), ("MIXED", 1e-8)])
+def test_batched_instances_match_single_instance_oracle(P, prec_name, tol):
+    batch = problem_batch2d(12, seed=7, side_lo=5, side_hi=24)
+    subs = _instances(batch)
+    assert [s.n_nodes for s in subs] == list(np.diff(batch.meta["node_offsets"]))
+    x, refs = _batch_state(batch, subs)
+    s = P.SGN.from_problem(batch, stores=P.STORE_FP64 | P.STORE_MIXED)
+    prec = getattr(P, prec_name)
+    _, dp, _, frep, srep = s.step(x, batch.p0, prec)
+    dp = dp.cpu().numpy()
+    eo = batch.meta["elem_offsets"]
+    for i, ref in enumerate(refs):
+        got = dp[eo[i]:eo[i + 1]]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, i
+    # the batch is one saddle-point system: its inertia is the sum of the instances'
+    n_x = batch.n_free * 2
+    assert (frep.n_pos, frep.n_neg, frep.n_zero) == (n_x + batch.n_elem, n_x, 0)
+    s.close()
+
+
+def test_batch_of_256_runs_and_samples_match_oracle(P):
+    """The full batched workload (256 instances, sides U{10..60}): the mixed
+    step agrees with the FP64 GPU step everywhere, and sampled instances agree
+    with the oracle."""
+    batch = problem_batch2d(256, seed=0)
+    subs = _instances(batch)
+    no, eo = batch.meta["node_offsets"], batch.meta["elem_offsets"]
+    x = batch.X.copy()
+    sample = [0, 77, 255]
+    refs = {}
+    for i in sample:
+        sub = subs[i]
+        xi, info = EQ.newton(sub, sub.p0)
+        assert info["converged"]
+        refs[i] = (xi, S.sgn_step(S.blocks(sub, xi, sub.p0), "kkt")[1])
+    s = P.SGN.from_problem(batch, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT)
+    xg, rep = s.equilibrium(batch.p0, batch.fext)
+    assert rep.converged, (rep.iters, rep.residual)
+    xg = xg.cpu().numpy()
+    for i in sample:
+        # GPU equilibrium of the batch == oracle equilibrium of the instance
+        xi, _ = refs[i]
+        shift = batch.X[no[i], 0] - subs[i].X[0, 0]
+        np.testing.assert_allclose(xg[no[i]:no[i + 1]] - [shift, 0.0], xi, rtol=0, atol=1e-8)
+    _, dp64, _, _, _ = s.step(xg, batch.p0, P.FP64)
+    dp64 = dp64.cpu().numpy()
+    _, dpm, _, _, srep = s.step(xg, batch.p0, P.MIXED)
+    dpm = dpm.cpu().numpy()
+    assert np.linalg.norm(dpm - dp64) / np.linalg.norm(dp64) < 1e-8
+    for i in sample:
+        ref = refs[i][1]
+        got = dp64[eo[i]:eo[i + 1]]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8, i
+    s.close()
+
+
+def test_graph_step_equals_stepwise_calls(P):
+    """sgn_step_graph (assemble + factor + solve + fixed refinement as one
+    CUDA-graph launch) gives the stepwise result, call after call."""
+    batch = problem_batch2d(12, seed=7, side_lo=5, side_hi=24)
+    subs = _instances(batch)
+    x, refs = _batch_state(batch, subs)
+    s = P.SGN.from_problem(batch, stores=P.STORE_MIXED)
+    xd = torch.as_tensor(x, device="cuda")
+    pd = torch.as_tensor(batch.p0, device="cuda")
+    _, dp_ref, _, _, _ = s.step(xd, pd, P.MIXED)
+    dp_ref = dp_ref.clone()
+    out = (torch.empty_like(xd), torch.empty_like(pd), torch.empty_like(xd))
+    for _ in range(3):
+        _, dp, _, res = s.step_graph(xd, pd, P.MIXED, refine_steps=4, out=out)
+        assert res < 1e-11
+        assert float(torch.linalg.norm(dp - dp_ref) / torch.linalg.norm(dp_ref)) < 1e-10
+    eo = batch.meta["elem_offsets"]
+    dpn = out[1].cpu().numpy()
+    for i, ref in enumerate(refs):
+        assert np.linalg.norm(dpn[eo[i]:eo[i + 1]] - ref) / np.linalg.norm(ref) < 1e-8
+    s.close()

@@ -17,7 +17,8 @@ def _equilibrium(prob, p, x0=None, tol=2e-12):
     # 2e-12 is about the round-off floor of ||c|| / ||f_ext|| on the tiny
     # meshes (the floor grows with the mesh: ~6e-11 on the 21x21 grid)
     x, info = EQ.newton(prob, p, x0=x0, tol=tol, max_iter=60)
-    assert info["residual"] <= tol, info
+    # converged, possibly by stagnating just above tol at the round-off floor
+    assert info["converged"] and info["residual"] <= 5 * tol, info
     return x
 
 
