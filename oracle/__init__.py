@@ -21,10 +21,16 @@ What is here, each written from the definition it cites:
 * ``equilibrium``  -- forward simulation: Newton's method with a
                       backtracking line search that keeps the potential
                       monotone (Sec. 5, "Computing Equilibrium States").
+* ``learned``      -- the learned warm start of that Newton solve: RBF design
+                      map, snapshot basis (SVD of the centred snapshots), the
+                      GELU MLP with its backpropagated gradients, AdamW.
 
 Parity pins: every function above is checked in ``tests/test_oracle_*.py``
 against something other than itself (complex-step derivatives, the
 linear-elastic closed form at F = I, finite differences of the equilibrium
 map, brute-force Gauss-Newton from finite-difference Jacobians, Theorem 1,
-Theorem 2, the saddle-point inertia).  No function here is "parity unpinned".
+Theorem 2, the saddle-point inertia; for ``learned``: the GELU closed form and
+its finite differences, finite-difference MLP gradients, AdamW's first step in
+closed form, orthonormality and exact reconstruction of low-rank snapshots, the
+RBF map at a centre).  No function here is "parity unpinned".
 """

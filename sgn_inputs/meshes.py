@@ -235,6 +235,33 @@ def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, si
                          "p_sigma": p_sigma})
 
 
+def problem_rbf3d(n: int = 40, n_rbf: int = 64, width: float = 0.15, seed: int = 0,
+                  theta_sigma: float = 0.3, load_scale: float | None = None) -> Problem:
+    """The 3D cube of problem_3d whose per-tet log-modulus field is given by
+    n_rbf Gaussian radial basis functions: p_e = sum_k theta_k
+    exp(-|X_e - c_k|^2 / (2 width^2)) at the tet centroid X_e, with centres
+    c_k ~ U[0,1]^3 (seeded).  meta holds the centres, the width and theta_sigma
+    (coefficient vectors theta ~ N(0, theta_sigma^2), see draw_thetas).
+    load_scale defaults to (41 / (n + 1))^2: every resolution carries the
+    total top-face load of the 40-cell cube (about 15% peak displacement,
+    four Newton iterations from the rest shape)."""
+    if load_scale is None:
+        load_scale = (41.0 / (n + 1)) ** 2
+    prob = problem_3d(n, seed=seed, load_scale=load_scale)
+    rng = np.random.default_rng(seed + 7919)
+    centers = rng.uniform(0.0, 1.0, size=(n_rbf, 3))
+    prob.name = f"rbf3d_{n}"
+    prob.meta.update({"rbf_centers": centers, "rbf_width": width, "theta_sigma": theta_sigma,
+                      "n_rbf": n_rbf})
+    return prob
+
+
+def draw_thetas(prob: Problem, count: int, seed: int) -> np.ndarray:
+    """count coefficient vectors theta ~ N(0, theta_sigma^2) for an RBF problem."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, prob.meta["theta_sigma"], size=(count, prob.meta["n_rbf"]))
+
+
 PRESETS = {
     # 21x21 plane-strain grid, 800 triangles, p ~ N(0, 0.1^2)
     "grid2d_21": lambda seed=0: problem_2d(21, seed=seed),
@@ -242,6 +269,8 @@ PRESETS = {
     "kuhn3d_40": lambda seed=0: problem_3d(40, seed=seed),
     # 80^3 Kuhn tets, 2,958,234 elements
     "kuhn3d_80": lambda seed=0: problem_3d(80, seed=seed),
+    # 40^3 cube with 64 RBF design coefficients (learned warm start)
+    "rbf3d_40": lambda seed=0: problem_rbf3d(40, seed=seed),
     # 256 plane-strain instances, sides ~ U{10..60}
     "batch2d_256": lambda seed=0: problem_batch2d(256, seed=seed),
 }
@@ -258,4 +287,6 @@ def make_preset(name: str, seed: int = 0) -> Problem:
         return problem_2d(int(size), seed=seed)
     if kind == "batch2d":
         return problem_batch2d(int(size), seed=seed)
+    if kind == "rbf3d":
+        return problem_rbf3d(int(size), seed=seed)
     raise KeyError(name)
