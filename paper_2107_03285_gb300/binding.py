@@ -19,13 +19,19 @@ LIB_PATH = os.path.join(HERE, "libsgn.so")
 OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINITE, ETIMEOUT = range(11)
 FP64, MIXED = 0, 1
 RHS_KKT, RHS_PAPER = 0, 1
-STORE_FP64, STORE_MIXED, STORE_KFACT = 1, 2, 4
+STORE_FP64, STORE_MIXED, STORE_KFACT, STORE_KFACT_MIXED = 1, 2, 4, 8
 PROF_KINDS = ["update", "panel_update", "pivot", "trsm", "front_assembly", "elements", "solve", "vector"]
 
 EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
-            "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph"]
+            "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
+            "sgn_last_error",
+            # learned warm start (include/sgn_learn.h)
+            "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
+            "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
+            "sgn_equilibrium_warm", "sgn_learn_param_count", "sgn_learn_params", "sgn_learn_grads",
+            "sgn_learn_apply", "sgn_learn_basis_get"]
 
 
 class Mesh(C.Structure):
@@ -72,12 +78,18 @@ class KernelProfile(C.Structure):
 
 
 class NewtonOpts(C.Structure):
-    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double)]
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("precision", C.c_int32)]
 
 
 class NewtonReport(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
-                ("initial_residual", C.c_double), ("seconds", C.c_double)]
+                ("initial_residual", C.c_double), ("seconds", C.c_double), ("solves", C.c_int32),
+                ("history", C.c_double * 32), ("step_length", C.c_double * 32)]
+
+
+class LearnOpts(C.Structure):
+    _fields_ = [("n_rbf", C.c_int32), ("centers_h", C.POINTER(C.c_double)), ("width", C.c_double),
+                ("n_modes", C.c_int32), ("hidden", C.c_int32), ("max_snap", C.c_int32), ("batch", C.c_int32)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -108,6 +120,24 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_profile": (C.c_int, [VP, C.c_int32]),
         "sgn_profile_read": (C.c_int, [VP, P(KernelProfile), C.c_int32]),
         "sgn_launch_count": (C.c_int64, [VP]),
+        "sgn_last_error": (C.c_char_p, [VP]),
+        "sgn_learn_create": (C.c_int, [VP, P(LearnOpts), P(VP)]),
+        "sgn_learn_device_bytes": (C.c_int, [VP, P(C.c_size_t)]),
+        "sgn_learn_bind": (C.c_int, [VP, VP, C.c_size_t]),
+        "sgn_learn_destroy": (None, [VP]),
+        "sgn_rbf_params": (C.c_int, [VP, VP, VP]),
+        "sgn_learn_basis": (C.c_int, [VP, VP, C.c_int32, C.c_uint64, dp]),
+        "sgn_learn_train": (C.c_int, [VP, VP, VP, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_uint64,
+                                      P(C.c_float)]),
+        "sgn_learn_predict": (C.c_int, [VP, VP, VP]),
+        "sgn_equilibrium_warm": (C.c_int, [VP, VP, VP, VP, VP, P(NewtonOpts), P(NewtonReport),
+                                           P(C.c_int32)]),
+        "sgn_learn_param_count": (C.c_int64, [VP]),
+        "sgn_learn_params": (C.c_int, [VP, P(C.c_float), C.c_int32]),
+        "sgn_learn_grads": (C.c_int, [VP, P(C.c_float), P(C.c_float), C.c_int32, P(C.c_float),
+                                      P(C.c_float)]),
+        "sgn_learn_apply": (C.c_int, [VP, P(C.c_float), C.c_float, C.c_float]),
+        "sgn_learn_basis_get": (C.c_int, [VP, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -132,9 +162,14 @@ def lib() -> C.CDLL:
     return _LIB
 
 
-def _check(code, where):
+def _check(code, where, h=None):
     if code != OK:
-        raise SGNError(code, where, lib().sgn_strerror(code).decode())
+        msg = lib().sgn_strerror(code).decode()
+        if h is not None:
+            detail = lib().sgn_last_error(h).decode()
+            if detail and detail != msg:
+                msg = f"{msg}; {detail}"
+        raise SGNError(code, where, msg)
     return code
 
 
