@@ -78,7 +78,8 @@ typedef enum {
 enum {
   SGN_STORE_FP64 = 1,   /* FP64 saddle-point fronts (SGN_FP64 factor) */
   SGN_STORE_MIXED = 2,  /* FP32 saddle-point fronts (SGN_MIXED factor) */
-  SGN_STORE_KFACT = 4   /* FP64 fronts of K alone (sgn_equilibrium, sgn_gradient) */
+  SGN_STORE_KFACT = 4,  /* FP64 fronts of K alone (sgn_equilibrium, sgn_gradient) */
+  SGN_STORE_KFACT_MIXED = 8  /* FP32 fronts of K alone (sgn_equilibrium with precision SGN_MIXED) */
 };
 
 typedef struct sgn_ctx *sgn_t;
@@ -133,7 +134,8 @@ typedef struct {
 
 typedef struct {
   int32_t max_refine;             /* FP64 refinement steps (default 0 -> 2 FP64 / 30 mixed) */
-  double tol;                     /* stop at ||b - M z|| <= tol ||b|| (default 0 -> 1e-13) */
+  double tol;                     /* stop at ||b - M z|| <= tol ||b|| (default 0 -> 1e-12, just above
+                                     the FP64 round-off floor of the 40^3 system, ~1.4e-13) */
 } sgn_solve_opts;
 
 typedef struct {
@@ -148,6 +150,13 @@ typedef struct {
   double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10); a residual a Newton
                                      step no longer halves also counts once below 1e-7 ||f_ext||
                                      (the round-off floor of c grows with the mesh) */
+  int32_t precision;              /* SGN_FP64 (default): K factored in FP64 (SGN_STORE_KFACT);
+                                     SGN_MIXED: K factored with FP32 fronts on the tensor cores
+                                     (SGN_STORE_KFACT_MIXED) and every Newton direction refined
+                                     in FP64 against the FP64 K until ||K dx + c|| <=
+                                     min(0.1, ||c|| / ||f_ext||) ||c|| (at most 10 solves;
+                                     the stagnation rule above only counts after a
+                                     direction that met this bound) */
 } sgn_newton_opts;
 
 typedef struct {
@@ -156,6 +165,9 @@ typedef struct {
   double residual;                /* final ||c|| / ||f_ext|| */
   double initial_residual;
   double seconds;
+  int32_t solves;                 /* K solves (more than iters with FP32 fronts: refinement) */
+  double history[32];             /* ||c|| / ||f_ext|| at iterate 0, 1, ... (first 32) */
+  double step_length[32];         /* accepted line-search step t of iteration 1, 2, ... */
 } sgn_newton_report;
 
 /* ---- set-up -------------------------------------------------------------
@@ -177,6 +189,9 @@ sgn_status sgn_set_stream(sgn_t h, void *stream);
 sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj);
 void sgn_destroy(sgn_t h);
 const char *sgn_strerror(sgn_status s);
+/* Detail of the last failed call on h (which CUDA call or check failed);
+ * empty if none.  Owned by h, valid until the next call on h. */
+const char *sgn_last_error(sgn_t h);
 
 /* ---- hot path ------------------------------------------------------------
  * sgn_assemble: element kernels evaluate, at positions x_d and parameters

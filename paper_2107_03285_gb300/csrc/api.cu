@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -24,7 +25,7 @@ thread_local std::string g_err;
   do {                                                                      \
     cudaError_t _e = (call);                                                \
     if (_e != cudaSuccess) {                                                \
-      (h)->last_error = std::string(#call) + ": " + cudaGetErrorString(_e); \
+      (h)->last_error = g_err = std::string(#call) + ": " + cudaGetErrorString(_e); \
       return SGN_ECUDA;                                                     \
     }                                                                       \
   } while (0)
@@ -48,6 +49,89 @@ struct Upload {
   size_t bytes;
 };
 
+// Places every contribution block in one arena: the block of front s lives
+// from the assembly of s's level (which writes it) to the assembly of its
+// parent's level (which reads it).  Levels are walked in order; a level's
+// blocks are placed best-fit in the free space (largest first) before its
+// children's blocks are released.  Returns the arena size in elements.
+int64_t plan_cb_arena(const Symbolic &S, int dpn, std::vector<int64_t> &cb_off, int64_t *cb_sum) {
+  cb_off.assign(S.sn.size(), 0);
+  std::map<int64_t, int64_t> free_blocks;  // offset -> size, below `end`
+  int64_t end = 0, high = 0, sum = 0;
+  auto cb_size = [&](int s) {
+    const int64_t m = (int64_t)S.sn[s].nstruct * dpn;
+    return ((m * m + 63) / 64) * 64;  // 256-byte granules (FP32)
+  };
+  auto release = [&](int64_t off, int64_t size) {
+    auto it = free_blocks.emplace(off, size).first;
+    auto nx = std::next(it);
+    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_blocks.erase(nx);
+    }
+    if (it != free_blocks.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_blocks.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == end) {  // free space at the top shrinks the arena
+      end = it->first;
+      free_blocks.erase(it);
+    }
+  };
+  for (const auto &lv : S.level_fronts) {
+    std::vector<int> order(lv.begin(), lv.end());
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cb_size(a) > cb_size(b); });
+    for (int s : order) {
+      const int64_t need = cb_size(s);
+      sum += need;
+      if (need == 0) continue;
+      auto best = free_blocks.end();
+      for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it)
+        if (it->second >= need && (best == free_blocks.end() || it->second < best->second)) best = it;
+      if (best != free_blocks.end()) {
+        cb_off[s] = best->first;
+        const int64_t rest = best->second - need, at = best->first + need;
+        free_blocks.erase(best);
+        if (rest > 0) free_blocks.emplace(at, rest);
+      } else {
+        cb_off[s] = end;
+        end += need;
+        high = std::max(high, end);
+      }
+    }
+    for (int s : lv)
+      for (int j = 0; j < S.sn[s].nchild; ++j) {
+        const int ch = S.children[S.sn[s].child_off + j];
+        if (cb_size(ch) > 0) release(cb_off[ch], cb_size(ch));
+      }
+  }
+  *cb_sum = sum;
+  // self-check: replay the lifetimes and verify that no two live blocks overlap
+  std::map<int64_t, int64_t> live;  // offset -> end
+  for (const auto &lv : S.level_fronts) {
+    for (int s : lv) {
+      const int64_t need = cb_size(s);
+      if (need == 0) continue;
+      const int64_t o = cb_off[s], e = o + need;
+      if (e > high) return -1;
+      auto it = live.lower_bound(o);
+      if (it != live.end() && it->first < e) return -1;
+      if (it != live.begin() && std::prev(it)->second > o) return -1;
+      live.emplace(o, e);
+    }
+    for (int s : lv)
+      for (int j = 0; j < S.sn[s].nchild; ++j) {
+        const int ch = S.children[S.sn[s].child_off + j];
+        if (cb_size(ch) > 0) live.erase(cb_off[ch]);
+      }
+  }
+  return high;
+}
+
 void store_offsets(Ctx &c, Store &s, int dpn) {
   s.dpn = dpn;
   const int n_sn = (int)c.S.sn.size();
@@ -56,7 +140,7 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   int64_t fo = 0, ro = 0, po = 0;
   for (int i = 0; i < n_sn; ++i) {
     int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
-    s.h_front_off[i] = fo; fo += f * f;
+    s.h_front_off[i] = fo; fo += ((f * ns + 63) / 64) * 64;
     s.h_rhs_off[i] = ro; ro += f;
     s.h_piv_off[i] = po; po += ns;
   }
@@ -72,6 +156,7 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
     wmax = std::max(wmax, wo);
   }
   s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po;
+  s.cb_elems = plan_cb_arena(c.S, dpn, s.h_cb_off, &s.cb_sum);
 }
 
 // lays out (base == nullptr: only measures) every device array
@@ -151,13 +236,16 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx);
   c.hx = cv.take<double>(nn); c.hdx = cv.take<double>(nn); c.hdl = cv.take<double>(nn);
   c.hp = cv.take<double>(ne); c.hdp = cv.take<double>(ne);
+  bool plan_ok = true;
   auto store = [&](Store &s, bool on, int dpn, bool kkt, bool fp32) {
     s.enabled = on;
     s.kkt = kkt; s.fp32 = fp32;
     store_offsets(c, s, dpn);
     if (!on) return;
+    if (s.cb_elems < 0) { plan_ok = false; s.cb_elems = 0; }
     size_t es = fp32 ? 4 : 8;
     s.F = cv.take<char>((size_t)s.front_elems * es);
+    s.CB = cv.take<char>((size_t)s.cb_elems * es);
     s.W = cv.take<char>((size_t)s.w_elems * es);
     s.Ldg = cv.take<char>((size_t)s.piv_elems * c.S.opts.panel * es);
     s.rhs = cv.take<double>(s.rhs_elems);
@@ -170,6 +258,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     }
     int64_t *p;
     st_up(p, s.h_front_off); s.front_off = p;
+    st_up(p, s.h_cb_off); s.cb_off = p;
     st_up(p, s.h_w_off); s.w_off = p;
     st_up(p, s.h_rhs_off); s.rhs_off = p;
     st_up(p, s.h_piv_off); s.piv_off = p;
@@ -177,7 +266,8 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   store(c.kkt64, (stores & SGN_STORE_FP64) != 0, 2 * d, true, false);
   store(c.kkt32, (stores & SGN_STORE_MIXED) != 0, 2 * d, true, true);
   store(c.kf, (stores & SGN_STORE_KFACT) != 0, d, false, false);
-  return cv.off + 256;
+  store(c.kf32, (stores & SGN_STORE_KFACT_MIXED) != 0, d, false, true);
+  return plan_ok ? cv.off + 256 : 0;  // 0: the contribution-block plan failed its self-check
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -230,7 +320,7 @@ sgn_status check_status(sgn_ctx *h) {
 sgn_status launch_check(sgn_ctx *h) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    h->last_error = std::string("kernel launch: ") + cudaGetErrorString(e);
+    h->last_error = g_err = std::string("kernel launch: ") + cudaGetErrorString(e);
     return SGN_ECUDA;
   }
   return SGN_OK;
@@ -239,6 +329,8 @@ sgn_status launch_check(sgn_ctx *h) {
 }  // namespace
 
 extern "C" {
+
+const char *sgn_last_error(sgn_t h) { return h ? h->last_error.c_str() : ""; }
 
 const char *sgn_strerror(sgn_status s) {
   switch (s) {
@@ -309,6 +401,7 @@ sgn_status sgn_get_info(sgn_t h, sgn_info *o) {
 sgn_status sgn_device_bytes(sgn_t h, int32_t stores, size_t *bytes) {
   if (!h || !bytes) return SGN_EINVAL;
   *bytes = carve(*h, nullptr, stores, nullptr);
+  if (*bytes == 0) { g_err = "internal: contribution-block arena plan overlaps"; return SGN_EINVAL; }
   return SGN_OK;
 }
 
@@ -322,6 +415,7 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   if (!h || !dev_buf) return SGN_EINVAL;
   if (((uintptr_t)dev_buf & 255) != 0) { g_err = "device buffer must be 256-byte aligned"; return SGN_EINVAL; }
   size_t need = carve(*h, nullptr, stores, nullptr);
+  if (need == 0) { g_err = "internal: contribution-block arena plan overlaps"; return SGN_EINVAL; }
   if (bytes < need) return SGN_ENOMEM;
   h->stream = (cudaStream_t)stream;
   CUDA_TRY(h, cudaGetDevice(&h->device));
@@ -330,13 +424,15 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   h->base = (char *)dev_buf;
   h->bytes = bytes;
   carve(*h, h->base, stores, &ups);
-  std::vector<tc::Maps> maps;
-  if (h->kkt32.enabled) {
-    h->kkt32.tc = false;
-    const char *off = getenv("SGN_DISABLE_TC");
-    if (!(off && off[0] == '1') && encode_maps(*h, h->kkt32, maps)) {
-      ups.push_back({h->kkt32.maps, maps.data(), maps.size() * sizeof(tc::Maps)});
-      h->kkt32.tc = true;
+  std::vector<tc::Maps> maps32, mapsk;
+  const char *tc_off = getenv("SGN_DISABLE_TC");
+  const bool tc_ok = !(tc_off && tc_off[0] == '1');
+  for (auto sm : {std::make_pair(&h->kkt32, &maps32), std::make_pair(&h->kf32, &mapsk)}) {
+    Store &st = *sm.first;
+    st.tc = false;
+    if (st.enabled && tc_ok && encode_maps(*h, st, *sm.second)) {
+      ups.push_back({st.maps, sm.second->data(), sm.second->size() * sizeof(tc::Maps)});
+      st.tc = true;
     }
   }
   for (auto &u : ups) CUDA_TRY(h, cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, h->stream));
@@ -351,11 +447,11 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
     const char *g = getenv("SGN_DISABLE_GRAPHS");
     h->use_graphs = !(g && g[0] == '1');
   }
-  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf);
+  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf); destroy_graphs(h->kf32);
   if (h->step_graph) { cudaGraphExecDestroy(h->step_graph); h->step_graph = nullptr; }
   h->bound = true;
   h->assembled = false;
-  h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
+  h->kkt64.factored = h->kkt32.factored = h->kf.factored = h->kf32.factored = false;
   return SGN_OK;
 }
 
@@ -389,7 +485,7 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
 void sgn_destroy(sgn_t h) {
   if (!h) return;
   if (h->bound) cudaStreamSynchronize(h->stream);
-  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf);
+  destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf); destroy_graphs(h->kf32);
   if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
@@ -409,7 +505,7 @@ sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d) {
     launch_objective_terms(*h, x_d, p_d);
   }
   h->assembled = true;
-  h->kkt64.factored = h->kkt32.factored = h->kf.factored = false;
+  h->kkt64.factored = h->kkt32.factored = h->kf.factored = h->kf32.factored = false;
   return launch_check(h);
 }
 
@@ -458,7 +554,7 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   Ctx &c = *h;
   const int64_t nx = (int64_t)c.S.n_free * c.S.dim, ne = c.S.n_elem;
   int max_refine = opts && opts->max_refine > 0 ? opts->max_refine : (st.fp32 ? 30 : 2);
-  double tol = opts && opts->tol > 0 ? opts->tol : 1e-13;
+  double tol = opts && opts->tol > 0 ? opts->tol : 1e-12;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (rep) {
     CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
@@ -727,7 +823,14 @@ sgn_status sgn_gradient(sgn_t h, double *g_d) {
 sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, double *x_d,
                            const sgn_newton_opts *opts, sgn_newton_report *rep) {
   if (!h || !p_d || !fext_d || !x_d) return SGN_EINVAL;
-  if (!h->bound || !h->kf.enabled) return SGN_ESTATE;
+  if (!h->bound) return SGN_ESTATE;
+  const bool mixed = opts && opts->precision == SGN_MIXED;
+  if (opts && opts->precision != SGN_FP64 && opts->precision != SGN_MIXED) return SGN_EINVAL;
+  Store &kst = mixed ? h->kf32 : h->kf;
+  if (!kst.enabled) {
+    h->last_error = mixed ? "K FP32 store (SGN_STORE_KFACT_MIXED) was not bound" : "K store was not bound";
+    return SGN_ESTATE;
+  }
   Ctx &c = *h;
   auto t0 = std::chrono::steady_clock::now();
   const int d = c.S.dim;
@@ -763,22 +866,43 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
   if (!valid) { c.last_error = "initial guess has an inverted element"; return SGN_EINVERTED; }
   double cn = residual(x_d);
   double init = cn / scale;
-  int it = 0;
-  bool conv = false;
+  int it = 0, solves = 0;
+  bool conv = false, dir_ok = true;
   double cn_prev = -1.0;
+  double hist[32] = {0}, tstep[32] = {0};
   for (;; ++it) {
-    // converged, or stagnating at the round-off floor of ||c|| (a Newton step
-    // no longer halves it and it is already below 1e-7 ||f_ext||)
-    if (cn <= tol * scale || (cn_prev > 0 && cn > 0.5 * cn_prev && cn <= 1e-7 * scale)) { conv = true; break; }
+    if (it < 32) hist[it] = cn / scale;
+    // converged, or stagnating at the round-off floor of ||c|| (a full-accuracy
+    // Newton step no longer halves it and it is already below 1e-7 ||f_ext||)
+    if (cn <= tol * scale || (dir_ok && cn_prev > 0 && cn > 0.5 * cn_prev && cn <= 1e-7 * scale)) {
+      conv = true;
+      break;
+    }
     cn_prev = cn;
     if (it >= max_iter) break;
-    // Newton direction: K dx = -c
+    // Newton direction: K dx = -c.  Every solve goes through (c.rx -> c.zx)
+    // so that the captured substitution graph is reused; with FP32 fronts the
+    // direction is refined against the FP64 K until ||K dx + c|| <= eta ||c||
     launch_slot_gather(c, false);
     c.assembled = true;
-    factor_store(c, c.kf);
+    factor_store(c, kst);
     CUDA_TRY(h, cudaMemsetAsync(tmp, 0, nx * sizeof(double), c.stream));
     launch_axpy(c, tmp, cr, -1.0, nx);
-    solve_store(c, c.kf, tmp, dxr);
+    CUDA_TRY(h, cudaMemsetAsync(dxr, 0, nx * sizeof(double), c.stream));
+    CUDA_TRY(h, cudaMemcpyAsync(c.rx, tmp, nx * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    const double eta = std::min(0.1, cn / scale);
+    dir_ok = !mixed;
+    for (int q = 0;; ++q) {
+      solve_store(c, kst, c.rx, c.zx);
+      launch_axpy(c, dxr, c.zx, 1.0, nx);
+      ++solves;
+      if (!mixed || q >= 9) break;
+      launch_residual_k(c, tmp, dxr, c.rx);
+      if (std::sqrt(device_sumsq3(c, c.rx, nx, nullptr, 0, nullptr, 0)) <= eta * cn) {
+        dir_ok = true;
+        break;
+      }
+    }
     double slope = device_dot(c, cr, dxr, nx);
     CUDA_TRY(h, cudaMemcpyAsync(xsave, x_d, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     double t = 1.0, Pit = 0.0;
@@ -805,10 +929,11 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
         break;
       }
     }
+    if (it < 32) tstep[it] = acc ? t : 1.0;
     Pi = Pit;
     cn = residual(x_d);
   }
-  c.kf.factored = false;  // K factor belongs to an earlier iterate
+  c.kf.factored = c.kf32.factored = false;  // K factor belongs to an earlier iterate
   c.assembled = false;
   if (c.active) c.active->factored = false;
   sgn_status s = launch_check(h);
@@ -817,6 +942,8 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
   if (rep) {
     rep->iters = it; rep->converged = conv ? 1 : 0;
     rep->residual = cn / scale; rep->initial_residual = init;
+    rep->solves = solves;
+    for (int q = 0; q < 32; ++q) { rep->history[q] = hist[q]; rep->step_length[q] = tstep[q]; }
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   int stw = 0;

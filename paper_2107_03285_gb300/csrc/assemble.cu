@@ -306,6 +306,28 @@ __global__ void k_residual_nodes(int n_free, int ne, const int32_t *__restrict__
   }
 }
 
+// r = b - K z (one thread per free node)
+template <int D>
+__global__ void k_residual_k(int n_free, const int32_t *__restrict__ bsr_ptr, const int32_t *__restrict__ bsr_col,
+                             const double *__restrict__ Kv, const double *__restrict__ b,
+                             const double *__restrict__ z, double *__restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_free) return;
+  double acc[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) acc[a] = b[(int64_t)i * D + a];
+  for (int k = bsr_ptr[i]; k < bsr_ptr[i + 1]; ++k) {
+    const int c = bsr_col[k];
+    const double *Kb = Kv + (int64_t)k * D * D;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) acc[a] = fma(-Kb[a * D + bb], z[(int64_t)c * D + bb], acc[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) r[(int64_t)i * D + a] = acc[a];
+}
+
 template <int D>
 __global__ void k_residual_p(int ne, const int32_t *__restrict__ elem_rank, const double *__restrict__ cpv,
                              double alpha, const double *__restrict__ bp, const double *__restrict__ zp,
@@ -507,6 +529,11 @@ void launch_residual(Ctx &c, const double *bx, const double *bp, const double *b
   SGN_DISPATCH_D(c, k_residual_nodes, nblk(d.n_free), TPB, 0, d.n_free, d.n_elem, d.bsr_ptr, d.bsr_col, c.Kv,
                  d.inc_ptr, d.inc, c.cpv, c.wA, bx, bl, zx, zp, zl, rx, rl);
   SGN_DISPATCH_D(c, k_residual_p, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_rank, c.cpv, c.alpha, bp, zp, zl, rp);
+}
+
+void launch_residual_k(Ctx &c, const double *b, const double *z, double *r) {
+  const DevSym &d = c.ds;
+  SGN_DISPATCH_D(c, k_residual_k, nblk(d.n_free), TPB, 0, d.n_free, d.bsr_ptr, d.bsr_col, c.Kv, b, z, r);
 }
 
 double device_sumsq3(Ctx &c, const double *a, int64_t na, const double *b, int64_t nb, const double *c2,

@@ -64,9 +64,16 @@ struct Store {
   double *yz = nullptr;     // per fully-summed DOF: y, then z = D^{-1} y, then v (solves)
   int32_t *piv_type = nullptr, *piv_perm = nullptr;  // per fully-summed DOF
   double *D0 = nullptr, *D1 = nullptr;
-  const int64_t *front_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
-  std::vector<int64_t> h_front_off, h_w_off, h_rhs_off, h_piv_off;
-  int64_t front_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0;
+  // a front of order f with ns fully-summed columns keeps its first ns
+  // columns (f x ns, the factor) at front_off, and its contribution block
+  // (the (f - ns)^2 Schur complement handed to the parent) at cb_off in CB, an
+  // arena shared by contribution blocks whose lifetimes (from their own
+  // level's assembly to their parent's) do not overlap
+  void *CB = nullptr;
+  const int64_t *front_off = nullptr, *cb_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
+  std::vector<int64_t> h_front_off, h_cb_off, h_w_off, h_rhs_off, h_piv_off;
+  int64_t front_elems = 0, cb_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0;
+  int64_t cb_sum = 0;  // sum of all contribution blocks (what the arena saves against)
   bool factored = false;
   // CUDA graphs of the static launch sequences (captured once, replayed)
   cudaGraphExec_t fgraph = nullptr;        // factorization
@@ -131,7 +138,7 @@ struct Ctx {
   double *hx = nullptr, *hdx = nullptr, *hdl = nullptr;  // host-call staging [n_nodes*d]
   double *hp = nullptr, *hdp = nullptr;                  // host-call staging [n_elem]
 
-  Store kkt64, kkt32, kf;
+  Store kkt64, kkt32, kf, kf32;
   Store *active = nullptr;          // saddle-point factor of the last sgn_factor
 
   std::string last_error;
@@ -163,14 +170,24 @@ struct Ctx {
 };
 
 // brackets the launches issued in its scope with a profiled event pair
+// (inside a graph capture the records become event-record nodes, so the pair
+// can be timed after every replay of the graph)
 struct ProfScope {
   Ctx &c;
-  cudaEvent_t *ev;
-  ProfScope(Ctx &ctx, int kind, double flops = 0.0) : c(ctx), ev(ctx.prof_pair(kind, flops)) {
-    if (ev) cudaEventRecord(ev[0], c.stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(Ctx &ctx, int kind, double flops = 0.0) : c(ctx) {
+    if (cudaEvent_t *ev = ctx.prof_pair(kind, flops)) {
+      e0 = ev[0];
+      e1 = ev[1];
+      record(e0);
+    }
   }
   ~ProfScope() {
-    if (ev) cudaEventRecord(ev[1], c.stream);
+    if (e1) record(e1);
+  }
+  void record(cudaEvent_t e) {
+    if (c.capture_events) cudaEventRecordWithFlags(e, c.stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c.stream);
   }
 };
 
@@ -184,6 +201,8 @@ void launch_reduce_rhs(Ctx &c, const double *bx, const double *bp, const double 
 void launch_recover(Ctx &c, const double *red, const double *bp, double *zx, double *zp, double *zl);
 void launch_residual(Ctx &c, const double *bx, const double *bp, const double *bl, const double *zx,
                      const double *zp, const double *zl, double *rx, double *rp, double *rl);
+// r = b - K z over the free-rank DOFs (FP64, assembled K blocks)
+void launch_residual_k(Ctx &c, const double *b, const double *z, double *r);
 // returns sum of squares of the concatenation of (a, na), (b, nb), (c2, nc) on the host (synchronises)
 double device_dot(Ctx &c, const double *a, const double *b, int64_t n);
 // per-block partial sums of squares into partial_out (n_partial doubles), no synchronisation

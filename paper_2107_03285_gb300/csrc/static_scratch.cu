@@ -58,7 +58,7 @@ extern "C" sgn_status sgn_assemble_static(sgn_t h, const double *x_d, const doub
   sgn::launch_slot_gather_from(c, scratch);
   sgn::launch_objective_terms(c, x_d, p_d);
   c.assembled = true;
-  c.kkt64.factored = c.kkt32.factored = c.kf.factored = false;
+  c.kkt64.factored = c.kkt32.factored = c.kf.factored = c.kf32.factored = false;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     c.last_error = std::string("kernel launch: ") + cudaGetErrorString(e);

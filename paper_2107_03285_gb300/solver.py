@@ -38,15 +38,15 @@ class SGN:
         B._check(self.lib.sgn_setup(C.byref(mesh), C.byref(opts), C.byref(h)), "sgn_setup")
         self.h = h
         self.info = B.Info()
-        B._check(self.lib.sgn_get_info(self.h, C.byref(self.info)), "sgn_get_info")
+        B._check(self.lib.sgn_get_info(self.h, C.byref(self.info)), "sgn_get_info", self.h)
         self.stores = int(stores)
         nbytes = C.c_size_t()
-        B._check(self.lib.sgn_device_bytes(self.h, self.stores, C.byref(nbytes)), "sgn_device_bytes")
+        B._check(self.lib.sgn_device_bytes(self.h, self.stores, C.byref(nbytes)), "sgn_device_bytes", self.h)
         self.device = torch.device(device)
         self.buf = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         B._check(self.lib.sgn_bind(self.h, C.c_void_p(self.buf.data_ptr()), int(nbytes.value), self.stores,
-                                   C.c_void_p(self.stream.cuda_stream)), "sgn_bind")
+                                   C.c_void_p(self.stream.cuda_stream)), "sgn_bind", self.h)
 
     @classmethod
     def from_problem(cls, prob, **kw):
@@ -90,16 +90,16 @@ class SGN:
         self._weight = _f64(weight)
         obj = B.Objective(self._track.shape[0], B._dptr(self._track, C.c_int64),
                           B._dptr(self._target, C.c_double), B._dptr(self._weight, C.c_double), float(alpha))
-        B._check(self.lib.sgn_set_objective(self.h, C.byref(obj)), "sgn_set_objective")
+        B._check(self.lib.sgn_set_objective(self.h, C.byref(obj)), "sgn_set_objective", self.h)
 
     def assemble(self, x, p):
         self._x = self._dev(x, (self.n_nodes, self.dim))
         self._pv = self._dev(p, (self.n_elem,))
-        B._check(self.lib.sgn_assemble(self.h, self._p(self._x), self._p(self._pv)), "sgn_assemble")
+        B._check(self.lib.sgn_assemble(self.h, self._p(self._x), self._p(self._pv)), "sgn_assemble", self.h)
 
     def factor(self, precision=B.FP64, report=True):
         rep = B.FactorReport() if report else None
-        B._check(self.lib.sgn_factor(self.h, int(precision), C.byref(rep) if report else None), "sgn_factor")
+        B._check(self.lib.sgn_factor(self.h, int(precision), C.byref(rep) if report else None), "sgn_factor", self.h)
         return rep
 
     def solve(self, mode=B.RHS_KKT, g=None, max_refine=0, tol=0.0, report=True, out=None):
@@ -109,7 +109,7 @@ class SGN:
         opts = B.SolveOpts(int(max_refine), float(tol))
         rep = B.SolveReport() if report else None
         B._check(self.lib.sgn_solve(self.h, int(mode), self._p(gd), self._p(dx), self._p(dp), self._p(dl),
-                                    C.byref(opts), C.byref(rep) if report else None), "sgn_solve")
+                                    C.byref(opts), C.byref(rep) if report else None), "sgn_solve", self.h)
         return dx, dp, dl, rep
 
     def step(self, x, p, precision=B.FP64, mode=B.RHS_KKT, g=None):
@@ -129,7 +129,7 @@ class SGN:
         res = C.c_double(0.0)
         B._check(self.lib.sgn_step_graph(self.h, int(precision), int(refine_steps), self._p(x), self._p(p),
                                          self._p(dx), self._p(dp), self._p(dl),
-                                         C.byref(res) if residual else None), "sgn_step_graph")
+                                         C.byref(res) if residual else None), "sgn_step_graph", self.h)
         self._x, self._pv = x, p
         return dx, dp, dl, res.value
 
@@ -145,50 +145,53 @@ class SGN:
         code = self.lib.sgn_step_host(self.h, int(precision), dptr(xh), dptr(ph), dptr(dx), dptr(dp), dptr(dl),
                                       C.byref(rep))
         if code not in (B.OK, B.EREFINE):
-            B._check(code, "sgn_step_host")
+            B._check(code, "sgn_step_host", self.h)
         return dx, dp, dl, rep
 
-    def equilibrium(self, p, fext, x0=None, max_iter=0, tol=0.0):
+    def equilibrium(self, p, fext, x0=None, max_iter=0, tol=0.0, precision=B.FP64):
+        """Newton equilibrium (K fronts in FP64, or FP32 with FP64-refined
+        directions for precision=MIXED, which needs STORE_KFACT_MIXED)."""
         pd = self._dev(p, (self.n_elem,))
         fd = self._dev(fext, (self.n_nodes, self.dim))
         x = self._dev(self.X if x0 is None else x0, (self.n_nodes, self.dim)).clone()
         rep = B.NewtonReport()
         code = self.lib.sgn_equilibrium(self.h, self._p(pd), self._p(fd), self._p(x),
-                                        C.byref(B.NewtonOpts(int(max_iter), float(tol))), C.byref(rep))
+                                        C.byref(B.NewtonOpts(int(max_iter), float(tol), int(precision))),
+                                        C.byref(rep))
         if code not in (B.OK, B.ENEWTON):  # non-convergence is reported in rep.converged
-            B._check(code, "sgn_equilibrium")
+            B._check(code, "sgn_equilibrium", self.h)
         return x, rep
 
     def export_kkt(self):
         """Assembled saddle-point matrix as (rows, cols, vals) host COO arrays."""
         n = C.c_int64()
-        B._check(self.lib.sgn_export_kkt(self.h, C.byref(n), None, None, None), "sgn_export_kkt")
+        B._check(self.lib.sgn_export_kkt(self.h, C.byref(n), None, None, None), "sgn_export_kkt", self.h)
         rows = np.empty(n.value, dtype=np.int64)
         cols = np.empty(n.value, dtype=np.int64)
         vals = np.empty(n.value, dtype=np.float64)
         B._check(self.lib.sgn_export_kkt(self.h, C.byref(n), B._dptr(rows, C.c_int64), B._dptr(cols, C.c_int64),
-                                         B._dptr(vals, C.c_double)), "sgn_export_kkt")
+                                         B._dptr(vals, C.c_double)), "sgn_export_kkt", self.h)
         return rows, cols, vals
 
     def profile(self, mask=1):
         """Enable CUDA-event timing of the kernel kinds in `mask` (bit k =
         binding.PROF_KINDS[k]); 0 disables.  Resets the timers."""
-        B._check(self.lib.sgn_profile(self.h, int(mask)), "sgn_profile")
+        B._check(self.lib.sgn_profile(self.h, int(mask)), "sgn_profile", self.h)
 
     def profile_read(self):
         """{kind: (launches, seconds, flops)} since the last profile()."""
         n = len(B.PROF_KINDS)
         arr = (B.KernelProfile * n)()
-        B._check(self.lib.sgn_profile_read(self.h, arr, n), "sgn_profile_read")
+        B._check(self.lib.sgn_profile_read(self.h, arr, n), "sgn_profile_read", self.h)
         return {B.PROF_KINDS[k]: (arr[k].launches, arr[k].seconds, arr[k].flops) for k in range(n)}
 
     def launch_count(self):
         return int(self.lib.sgn_launch_count(self.h))
 
     def factor_k(self):
-        B._check(self.lib.sgn_factor_k(self.h), "sgn_factor_k")
+        B._check(self.lib.sgn_factor_k(self.h), "sgn_factor_k", self.h)
 
     def gradient(self):
         g = self._empty(self.n_elem)
-        B._check(self.lib.sgn_gradient(self.h, self._p(g)), "sgn_gradient")
+        B._check(self.lib.sgn_gradient(self.h, self._p(g)), "sgn_gradient", self.h)
         return g

@@ -180,6 +180,27 @@ def test_equilibrium_matches_oracle(sgnmod, name):
     assert _rel(x.cpu().numpy(), c.x) < 1e-9
 
 
+@pytest.mark.parametrize("name", ["grid2d_21", "kuhn3d_11"])
+def test_mixed_equilibrium_matches_oracle(sgnmod, name):
+    """Newton with FP32 K fronts (tensor-core trailing updates on kuhn3d_11)
+    and FP64-refined directions reaches the FP64 equilibrium."""
+    c = case(name)
+    s = make(sgnmod, c, stores=sgnmod.STORE_KFACT | sgnmod.STORE_KFACT_MIXED)
+    x64, rep64 = s.equilibrium(c.p, c.prob.fext)
+    x, rep = s.equilibrium(c.p, c.prob.fext, precision=sgnmod.MIXED)
+    assert rep.converged and rep.residual <= 1e-10
+    assert rep.iters <= rep64.iters + 1
+    assert _rel(x.cpu().numpy(), c.x) < 1e-9
+
+
+def test_mixed_equilibrium_needs_its_store(sgnmod):
+    c = case("kuhn3d_7")
+    s = make(sgnmod, c, stores=sgnmod.STORE_KFACT)
+    with pytest.raises(sgnmod.SGNError) as e:
+        s.equilibrium(c.p, c.prob.fext, precision=sgnmod.MIXED)
+    assert e.value.code == 8  # ESTATE
+
+
 def test_gradient_matches_oracle(sgnmod):
     c = case("kuhn3d_7")
     s = make(sgnmod, c)
