@@ -33,21 +33,22 @@ namespace {
 constexpr int MAXNB = 64;
 
 struct SV {  // store view passed to kernels
-  void *F;
+  void *F;                       // factor columns of every front (f x ns each)
+  void *CB;                      // contribution-block arena
   void *W;
   void *Ldg;                     // staged factored diagonal blocks (panel x panel per panel)
   float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
   double *rhs;
   int32_t *piv_type, *piv_perm;
   double *D0, *D1;
-  const int64_t *front_off, *w_off, *rhs_off, *piv_off;
+  const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off;
   int dpn;
   int kkt;
 };
 
 SV view(Store &s) {
   SV v;
-  v.F = s.F; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
+  v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
   v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
@@ -56,6 +57,29 @@ SV view(Store &s) {
 
 __device__ __forceinline__ int front_order(const DevSym &d, int s, int dpn) {
   return (d.sn_nown[s] + d.sn_nstruct[s]) * dpn;
+}
+
+// The lower triangle of front s (order f, ns fully-summed columns): columns
+// j < ns live in the front array (f x ns, column-major), the contribution
+// block (rows and columns >= ns) in the arena ((f - ns) x (f - ns)).
+template <typename T>
+struct FrontMat {
+  T *L, *C;
+  int64_t f, ns;
+  // element (i, j) of the lower triangle (i >= j)
+  __device__ __forceinline__ T *at(int64_t i, int64_t j) const {
+    return j < ns ? L + i + j * f : C + (i - ns) + (j - ns) * (f - ns);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ FrontMat<T> front_mat(const DevSym &d, const SV &sv, int s) {
+  FrontMat<T> m;
+  m.L = (T *)sv.F + sv.front_off[s];
+  m.C = (T *)sv.CB + sv.cb_off[s];
+  m.ns = (int64_t)d.sn_nown[s] * sv.dpn;
+  m.f = m.ns + (int64_t)d.sn_nstruct[s] * sv.dpn;
+  return m;
 }
 
 // ---------------------------------------------------------------- assembly
@@ -69,13 +93,13 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
   const int dpn = sv.dpn;
   const int nown = d.sn_nown[s];
   const int f = (nown + d.sn_nstruct[s]) * dpn;
-  T *F = (T *)sv.F + sv.front_off[s];
+  const FrontMat<T> F = front_mat<T>(d, sv, s);
   const int col0 = P * dpn;
   const int64_t len = f - col0;
   for (int64_t idx = threadIdx.x; idx < len * dpn; idx += blockDim.x) {
     int k = (int)(idx / len);
     int64_t i = col0 + idx % len;
-    F[i + (int64_t)(col0 + k) * f] = T(0);
+    *F.at(i, col0 + k) = T(0);
   }
   __syncthreads();
   if (P < nown) {
@@ -91,13 +115,13 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
       if (sv.kkt) {
         int rx = Q * dpn + 2 * a, cx = P * dpn + 2 * b;
         double gv = Gv[(int64_t)kk * D * D + b * D + a];
-        if (rx >= cx + 1) F[rx + (int64_t)(cx + 1) * f] += T(kv);        // (x row, lambda col)
-        if (rx + 1 >= cx) F[(rx + 1) + (int64_t)cx * f] += T(kv);        // (lambda row, x col)
-        if (rx + 1 >= cx + 1) F[(rx + 1) + (int64_t)(cx + 1) * f] += T(-gv);
-        if (Q == P && a == b) F[rx + (int64_t)cx * f] += T(wA[(int64_t)r * D + a]);
+        if (rx >= cx + 1) *F.at(rx, cx + 1) += T(kv);        // (x row, lambda col)
+        if (rx + 1 >= cx) *F.at(rx + 1, cx) += T(kv);        // (lambda row, x col)
+        if (rx + 1 >= cx + 1) *F.at(rx + 1, cx + 1) += T(-gv);
+        if (Q == P && a == b) *F.at(rx, cx) += T(wA[(int64_t)r * D + a]);
       } else {
         int ri = Q * D + a, ci = P * D + b;
-        if (ri >= ci) F[ri + (int64_t)ci * f] += T(kv);
+        if (ri >= ci) *F.at(ri, ci) += T(kv);
       }
     }
   }
@@ -107,37 +131,38 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
     const int c = d.children[coff + j];
     const int q = d.cmap[d.cmap_off[coff + j] + P];
     if (q >= 0) {
-      const int nownc = d.sn_nown[c], nstc = d.sn_nstruct[c];
-      const int nsc = nownc * dpn, fc = (nownc + nstc) * dpn;
-      const T *Fc = (const T *)sv.F + sv.front_off[c];
+      const int nstc = d.sn_nstruct[c];
+      const int fcb = nstc * dpn;  // the child's contribution block is fcb x fcb
+      const T *Cc = (const T *)sv.CB + sv.cb_off[c];
       const int32_t *relc = d.relpos + d.sn_struct_off[c];
       const int nq = nstc - q;
       const int64_t rows = (int64_t)nq * dpn;
       const int64_t n = rows * dpn;
       for (int64_t base = threadIdx.x; base < n; base += 4 * (int64_t)blockDim.x) {
         T v[4], o[4];
-        int64_t dst[4];
+        T *dst[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int64_t idx = base + (int64_t)u * blockDim.x;
-          dst[u] = -1;
+          dst[u] = nullptr;
           v[u] = T(0);
           if (idx < n) {
             const int k = (int)(idx / rows);
             const int64_t rem = idx - (int64_t)k * rows;
             const int qq = q + (int)(rem / dpn), kp = (int)(rem % dpn);
-            const int64_t ic = nsc + (int64_t)qq * dpn + kp, jc = nsc + (int64_t)q * dpn + k;
+            // (ic, jc): position in the child's contribution block
+            const int64_t ic = (int64_t)qq * dpn + kp, jc = (int64_t)q * dpn + k;
             if (ic >= jc) {
-              dst[u] = (int64_t)relc[qq] * dpn + kp + (int64_t)(col0 + k) * f;
-              v[u] = Fc[ic + jc * fc];
+              dst[u] = F.at((int64_t)relc[qq] * dpn + kp, col0 + k);
+              v[u] = Cc[ic + jc * fcb];
             }
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) o[u] = dst[u] >= 0 ? F[dst[u]] : T(0);
+        for (int u = 0; u < 4; ++u) o[u] = dst[u] ? *dst[u] : T(0);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (dst[u] >= 0) F[dst[u]] = o[u] + v[u];
+          if (dst[u]) *dst[u] = o[u] + v[u];
       }
     }
     __syncthreads();
@@ -147,144 +172,152 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
 // ------------------------------------------------------- Bunch-Kaufman panel
 // Bunch-Kaufman LDL^T of the w x w block a (lower triangle, a[j][i] = A(i, j))
 // by the whole CTA: 1x1 / 2x2 pivots, alpha = (1 + sqrt 17) / 8, pivot search
-// restricted to the block, every decision on FP64 magnitudes, eliminations in
-// CT.  On return a holds the unit-lower L11 (a[j][j+1] = 0 inside 2x2 pivots),
-// sD0 / sD1 the 1x1 and 2x2 pivots, stype their kinds and sperm the block's
-// permutation (position -> original index).  Deterministic: every CTA that
-// runs it on the same block takes the same decisions.
-// Run by one warp (threads 0..31 of the block): only warp-level barriers.
-template <typename CT>
+// restricted to the block, eliminations in CT.  Magnitudes are compared
+// exactly (max of |CT| values); every pivot test is taken in FP64.
+// Deterministic: every warp, and every CTA that runs it on the same block,
+// takes the same decisions.
+// On return column j of a holds W(:, j) = L(:, j) D_j, unscaled (the caller
+// forms L from it and D: bk_unit_lower), sD0 / sD1 the 1x1 and 2x2 pivots
+// (a 1x1 pivot below the static-pivot threshold already replaced), stype
+// their kinds and sperm the block's permutation (position -> original index).
+// Run by all NT threads (NT a multiple of 32, w <= 64).  Every warp searches
+// the pivot column itself (no barrier for the decision), holds the pivot
+// column(s) in registers (rows lane and lane + 32 below the pivot) and
+// broadcasts the entries it needs by shuffles, and owns the columns warp,
+// warp + NT/32, ... of the update: one barrier per step unless rows swap.
+template <typename CT, int NT>
 __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double eps_rel, int *sperm, int *stype,
                                 double *sD0, double *sD1, unsigned long long *counters, const bool count) {
-  __shared__ int s_kp, s_kstep;
-  __shared__ double s_bmax;
-  const int tid = threadIdx.x;  // 0..31
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
   const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
-  // one warp initialises all w <= 64 entries
-  for (int t = tid; t < w; t += 32) { sperm[t] = t; stype[t] = 0; sD1[t] = 0.0; sD0[t] = 0.0; }
-  __syncwarp();
-  if (tid < 32) {
-    double m = 0.0;
-    for (int idx = tid; idx < w * w; idx += 32) {
-      int j = idx / w, i = idx - j * w;
-      if (i >= j) m = fmax(m, fabs((double)a[j][i]));
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (tid == 0) s_bmax = m;
-  }
-  __syncwarp();
-  const double thresh = eps_rel * fmax(s_bmax, 1e-300);
+  for (int t = tid; t < w; t += NT) { sperm[t] = t; stype[t] = 0; sD1[t] = 0.0; sD0[t] = 0.0; }
+  CT bm = CT(0);
+  for (int jj = 0; jj < w; ++jj)
+    for (int i = jj + lane; i < w; i += 32) bm = max(bm, (CT)fabs(a[jj][i]));
+  for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(FULL, bm, o));
+  const double thresh = eps_rel * fmax((double)bm, 1e-300);
+  __syncthreads();
   int j = 0;
   while (j < w) {
-    if (tid < 32) {
-      // column max below the diagonal (restricted to the panel)
-      double cm = -1.0;
-      int ci = w;
-      for (int i = j + 1 + tid; i < w; i += 32) {
-        double v = fabs((double)a[j][i]);
-        if (v > cm) { cm = v; ci = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, cm, o);
-        int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-        if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
-      }
-      double colmax = fmax(cm, 0.0);
-      int imax = ci;
-      double absakk = fabs((double)a[j][j]);
-      int kstep = 1, kp = j;
-      if (!(fmax(absakk, colmax) > thresh)) {
-        kstep = 1; kp = j;  // (near-)zero column: static pivot below
-      } else if (absakk >= alpha * colmax) {
-        kstep = 1; kp = j;
-      } else {
-        double rm = 0.0;
-        for (int t = j + tid; t < w; t += 32) {
-          if (t == imax) continue;
-          double v = t < imax ? fabs((double)a[t][imax]) : fabs((double)a[imax][t]);
-          rm = fmax(rm, v);
-        }
-        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
-        double rowmax = rm;
-        if (absakk >= alpha * colmax * (colmax / rowmax)) { kstep = 1; kp = j; }
-        else if (fabs((double)a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
-        else { kstep = 2; kp = imax; }
-      }
-      if (tid == 0) { s_kp = kp; s_kstep = kstep; }
+    // ---- pivot search (every warp; the column max is exact in CT)
+    CT cm = CT(-1);
+    int ci = w;
+    for (int i = j + 1 + lane; i < w; i += 32) {
+      const CT v = (CT)fabs(a[j][i]);
+      if (v > cm) { cm = v; ci = i; }
     }
-    __syncwarp();
-    const int kstep = s_kstep, kp = s_kp;
+    for (int o = 16; o > 0; o >>= 1) {
+      const CT ov = __shfl_xor_sync(FULL, cm, o);
+      const int oi = __shfl_xor_sync(FULL, ci, o);
+      if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
+    }
+    const double colmax = fmax((double)cm, 0.0);
+    const int imax = ci;
+    const double absakk = fabs((double)a[j][j]);
+    int kstep = 1, kp = j;
+    bool read_row = false;
+    if (!(fmax(absakk, colmax) > thresh)) {
+      kstep = 1; kp = j;  // (near-)zero column: static pivot below
+    } else if (absakk >= alpha * colmax) {
+      kstep = 1; kp = j;
+    } else {
+      read_row = true;
+      CT rm = CT(0);
+      for (int t = j + lane; t < w; t += 32) {
+        if (t == imax) continue;
+        rm = max(rm, (CT)(t < imax ? fabs(a[t][imax]) : fabs(a[imax][t])));
+      }
+      for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL, rm, o));
+      const double rowmax = (double)rm;
+      if (absakk >= alpha * colmax * (colmax / rowmax)) { kstep = 1; kp = j; }
+      else if (fabs((double)a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
+      else { kstep = 2; kp = imax; }
+    }
     const int kk = j + kstep - 1;
+    // the search read entries the update (or the swap) writes: wait for all warps
+    if (read_row || kp != kk) __syncthreads();
     if (kp != kk) {
       // symmetric interchange of kk and kp in the trailing lower triangle and
       // of the already eliminated part of both rows
-      int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
-      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += 32) {
+      const int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
+      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += NT) {
         if (idx == 0) {
           CT t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
           int tp = sperm[kk]; sperm[kk] = sperm[kp]; sperm[kp] = tp;
         } else if (idx <= n1) {
-          int i = kp + idx;
+          const int i = kp + idx;
           CT t0 = a[kk][i]; a[kk][i] = a[kp][i]; a[kp][i] = t0;
         } else if (idx <= n1 + n2) {
-          int i = kk + (idx - n1);
+          const int i = kk + (idx - n1);
           CT t0 = a[kk][i]; a[kk][i] = a[i][kp]; a[i][kp] = t0;
         } else {
-          int cc = idx - n1 - n2 - 1;
+          const int cc = idx - n1 - n2 - 1;
           CT t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
     if (kstep == 1) {
+      double dj = (double)a[j][j];
+      const bool perturb = !(fabs(dj) > thresh);
+      if (perturb) dj = (dj >= 0.0) ? thresh : -thresh;
       if (tid == 0) {
-        double dj = (double)a[j][j];
-        if (!(fabs(dj) > thresh)) {
-          dj = (dj >= 0.0) ? thresh : -thresh;
-          a[j][j] = (CT)dj;
-          if (count) atomicAdd(counters + 0, 1ull);
-        }
-        sD0[j] = (double)a[j][j]; stype[j] = 0;
+        sD0[j] = (double)(CT)dj; stype[j] = 0;
+        if (perturb && count) atomicAdd(counters + 0, 1ull);
       }
-      __syncwarp();
-      const CT rd = CT(1) / a[j][j];
-      const int m = w - j - 1;
-      for (int idx = tid; idx < m * m; idx += 32) {
-        int cc = j + 1 + idx / m, i = j + 1 + idx % m;
-        if (i >= cc) a[cc][i] -= a[j][i] * a[j][cc] * rd;
+      const CT rd = CT(1) / (CT)dj;
+      const int i0 = j + 1 + lane, i1 = i0 + 32;
+      const CT l0 = i0 < w ? a[j][i0] : CT(0), l1 = i1 < w ? a[j][i1] : CT(0);
+      for (int cc = j + 1 + warp; cc < w; cc += NW) {
+        const int src = cc - j - 1;  // lane holding row cc of the pivot column
+        const CT fc = __shfl_sync(FULL, src < 32 ? l0 : l1, src & 31) * rd;
+        if (i0 < w && i0 >= cc) a[cc][i0] -= l0 * fc;
+        if (i1 < w && i1 >= cc) a[cc][i1] -= l1 * fc;
       }
-      __syncwarp();
-      for (int i = j + 1 + tid; i < w; i += 32) a[j][i] *= rd;
-      __syncwarp();
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
       const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
-      const int m = w - j - 2;
-      for (int idx = tid; idx < m * m; idx += 32) {
-        int cc = j + 2 + idx / m, i = j + 2 + idx % m;
-        if (i >= cc) {
-          CT l1 = a[j][i] * i11 + a[j + 1][i] * i21;
-          CT l2 = a[j][i] * i21 + a[j + 1][i] * i22;
-          a[cc][i] -= l1 * a[j][cc] + l2 * a[j + 1][cc];
-        }
-      }
-      __syncwarp();
-      for (int i = j + 2 + tid; i < w; i += 32) {
-        CT w1 = a[j][i], w2 = a[j + 1][i];
-        a[j][i] = w1 * i11 + w2 * i21;
-        a[j + 1][i] = w1 * i21 + w2 * i22;
-      }
       if (tid == 0) {
         sD0[j] = (double)d11; sD1[j] = (double)d21; sD0[j + 1] = (double)d22;
         stype[j] = 1; stype[j + 1] = 2;
-        a[j][j + 1] = CT(0);
         if (count) atomicAdd(counters + 1, 1ull);
       }
-      __syncwarp();
+      const int i0 = j + 2 + lane, i1 = i0 + 32;
+      const CT u0 = i0 < w ? a[j][i0] : CT(0), v0 = i0 < w ? a[j + 1][i0] : CT(0);
+      const CT u1 = i1 < w ? a[j][i1] : CT(0), v1 = i1 < w ? a[j + 1][i1] : CT(0);
+      const CT p0 = u0 * i11 + v0 * i21, q0 = u0 * i21 + v0 * i22;  // (L1, L2) of row i0
+      const CT p1 = u1 * i11 + v1 * i21, q1 = u1 * i21 + v1 * i22;
+      for (int cc = j + 2 + warp; cc < w; cc += NW) {
+        const int src = cc - j - 2;
+        const CT w1 = __shfl_sync(FULL, src < 32 ? u0 : u1, src & 31);
+        const CT w2 = __shfl_sync(FULL, src < 32 ? v0 : v1, src & 31);
+        if (i0 < w && i0 >= cc) a[cc][i0] -= p0 * w1 + q0 * w2;
+        if (i1 < w && i1 >= cc) a[cc][i1] -= p1 * w1 + q1 * w2;
+      }
     }
+    __syncthreads();
     j += kstep;
   }
+}
+
+// L(i, j) (i > j) of a block factored by bk_factor_block, from its unscaled
+// columns and pivots: a 1x1 column is divided by its pivot, a 2x2 pair is
+// multiplied by the pair's inverse; L is zero inside a 2x2 pivot
+template <typename CT>
+__device__ __forceinline__ CT bk_unit_lower(const CT (*a)[MAXNB + 1], int i, int j, const int *stype,
+                                            const double *sD0, const double *sD1) {
+  const int ty = stype[j];
+  if (ty == 0) return a[j][i] * (CT(1) / (CT)sD0[j]);
+  const int j0 = ty == 1 ? j : j - 1;  // first column of the pair
+  if (i == j0 + 1) return CT(0);
+  const CT d11 = (CT)sD0[j0], d21 = (CT)sD1[j0], d22 = (CT)sD0[j0 + 1];
+  const CT det = d11 * d22 - d21 * d21;
+  const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
+  const CT u = a[j0][i], v = a[j0 + 1][i];
+  return ty == 1 ? u * i11 + v * i21 : u * i21 + v * i22;
 }
 
 // Pivot panel [k, k + w), diagonal block (one CTA per active front):
@@ -345,12 +378,13 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32
     }
   }
   __syncthreads();
-  if (tid < 32) bk_factor_block<CT>(a, w, eps_rel, sperm, stype, sD0, sD1, counters, true);
+  bk_factor_block<CT, 128>(a, w, eps_rel, sperm, stype, sD0, sD1, counters, true);
   __syncthreads();
   T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
     const int jj = idx / w, ii = idx - jj * w;
-    if (ii >= jj) stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : T(a[jj][ii]);
+    if (ii >= jj)
+      stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : T(bk_unit_lower<CT>(a, ii, jj, stype, sD0, sD1));
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
@@ -361,22 +395,36 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32
   }
 }
 
-// Pivot panel [k, k + w), rows below it (128 rows per CTA): the same
-// left-looking update for these rows, then W = F21 P^T L11^{-T} (= L21 D) and
-// L21 = W D^{-1}, written to the front, to the outer block's W and (FP32
-// fronts with tensor cores) to the K-major hi / lo operand copies.
-template <typename T>
+// four consecutive shared-memory values as one vector load (16-byte aligned)
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2 *>(p), q1 = *reinterpret_cast<const double2 *>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// Pivot panel [k, k + w), rows below it (128 rows per CTA, one row per
+// thread, NBT >= w the panel width it is compiled for):
+//   left-looking update of the rows by the earlier panels of the outer block,
+//   F21 -= W[rows, K0:k] L[k:k+w, K0:k]^T (the next chunk of W prefetched into
+//   registers while the current one is applied; L chunks read as vectors);
+//   permutation and forward substitution with L11 in registers (x = F21 P^T
+//   L11^{-T} = L21 D); L21 = x D^{-1}.  Writes L21 to the front, x to the outer
+//   block's W and (FP32 fronts with tensor cores) both as K-major hi / lo
+//   operand copies.
+template <typename T, int NBT>
 __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                      int K0, int nb) {
   using CT = T;
   constexpr int RB = 128, KC = 32, XS = RB + 1;
-  extern __shared__ unsigned char rows_raw[];
-  CT *Lp = reinterpret_cast<CT *>(rows_raw);   // [KC][MAXNB]
-  CT *L11 = Lp + KC * MAXNB;                    // [MAXNB][MAXNB + 1]: L11[t][c] = L(t, c)
-  CT *xs = L11 + MAXNB * (MAXNB + 1);           // [MAXNB][XS]
-  CT *ls = xs + MAXNB * XS;                     // [MAXNB][XS]
-  __shared__ CT sD0[MAXNB], sD1[MAXNB];
-  __shared__ int sperm[MAXNB], stype[MAXNB];
+  extern __shared__ __align__(16) unsigned char rows_raw[];
+  CT *Lp = reinterpret_cast<CT *>(rows_raw);  // [KC][NBT]: L(k + t, K0 + cu + u)
+  CT *L11T = Lp + KC * NBT;                   // [NBT][NBT]: L11T[c][t] = L(t, c) for t > c, else 0
+  CT *xs = L11T + NBT * NBT;                  // [NBT][XS]: this CTA's rows, column t
+  __shared__ CT sD0[NBT], sD1[NBT];
+  __shared__ int sperm[NBT], stype[NBT];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
@@ -395,14 +443,17 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
   const int64_t i = r0 + il;
   const int kp_in = k - K0;
   const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    const int t = idx / w, c = idx - t * w;
-    L11[t * (MAXNB + 1) + c] = c < t ? (CT)stage[(int64_t)t * nb + c] : CT(0);
+  for (int idx = tid; idx < NBT * NBT; idx += blockDim.x) {
+    const int c = idx / NBT, t = idx - c * NBT;
+    L11T[idx] = (c < t && t < w) ? (CT)stage[(int64_t)t * nb + c] : CT(0);
   }
   const int64_t po = sv.piv_off[s] + k;
-  if (tid < w) {
-    sD0[tid] = (CT)sv.D0[po + tid]; sD1[tid] = (CT)sv.D1[po + tid];
-    sperm[tid] = sv.piv_perm[po + tid]; stype[tid] = sv.piv_type[po + tid];
+  if (tid < NBT) {
+    const bool in = tid < w;
+    sD0[tid] = in ? (CT)sv.D0[po + tid] : CT(1);
+    sD1[tid] = in ? (CT)sv.D1[po + tid] : CT(0);
+    sperm[tid] = in ? sv.piv_perm[po + tid] : tid;
+    stype[tid] = in ? sv.piv_type[po + tid] : 0;
   }
   if (row_ok) {
     for (int t0 = 0; t0 < w; t0 += 8) {
@@ -414,64 +465,114 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
         if (t0 + u < w) xs[(t0 + u) * XS + tid] = v[u];
     }
   }
+  // left-looking update
+  CT wr[KC];
+#pragma unroll
+  for (int u = 0; u < KC; ++u) wr[u] = (row_ok && u < kp_in) ? (CT)W[(i - K0) + (int64_t)u * ldw] : CT(0);
   for (int cu = 0; cu < kp_in; cu += KC) {
     const int kc = min(KC, kp_in - cu);
     __syncthreads();
-    for (int idx = tid; idx < kc * w; idx += blockDim.x) {
-      const int u = idx / w, t = idx - u * w;
-      Lp[u * MAXNB + t] = (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f];
+    for (int idx = tid; idx < KC * NBT; idx += blockDim.x) {
+      const int u = idx / NBT, t = idx - u * NBT;
+      Lp[idx] = (u < kc && t < w) ? (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f] : CT(0);
     }
     __syncthreads();
+    CT wn[KC];
+    const int nx = cu + KC;
+#pragma unroll
+    for (int u = 0; u < KC; ++u)
+      wn[u] = (row_ok && nx + u < kp_in) ? (CT)W[(i - K0) + (int64_t)(nx + u) * ldw] : CT(0);
     if (row_ok) {
-      CT wr[KC];
+#pragma unroll 4
+      for (int t0 = 0; t0 < NBT; t0 += 4) {
+        CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
 #pragma unroll
-      for (int u = 0; u < KC; ++u) wr[u] = u < kc ? (CT)W[(i - K0) + (int64_t)(cu + u) * ldw] : CT(0);
-      for (int t = 0; t < w; ++t) {
-        CT acc = CT(0);
+        for (int u = 0; u < KC; ++u) {
+          CT lv[4];
+          ld4(Lp + u * NBT + t0, lv);
 #pragma unroll
-        for (int u = 0; u < KC; ++u) acc += wr[u] * Lp[u * MAXNB + t];
-        xs[t * XS + tid] -= acc;
+          for (int q = 0; q < 4; ++q) acc[q] += wr[u] * lv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xs[(t0 + q) * XS + tid] -= acc[q];
       }
     }
+#pragma unroll
+    for (int u = 0; u < KC; ++u) wr[u] = wn[u];
   }
   __syncthreads();
-  if (row_ok) {
-    for (int t = 0; t < w; ++t) ls[t * XS + tid] = xs[sperm[t] * XS + tid];
-    for (int t = 0; t < w; ++t) xs[t * XS + tid] = ls[t * XS + tid];
-    for (int c = 0; c < w; ++c) {
-      const CT xc = xs[c * XS + tid];
-      for (int t = c + 1; t < w; ++t) xs[t * XS + tid] -= L11[t * (MAXNB + 1) + c] * xc;
+  // permutation and forward substitution, x in registers
+  CT x[NBT];
+#pragma unroll
+  for (int t = 0; t < NBT; ++t) x[t] = (row_ok && t < w) ? xs[sperm[t] * XS + tid] : CT(0);
+#pragma unroll
+  for (int c = 0; c < NBT - 1; ++c) {
+    const CT xc = x[c];
+#pragma unroll
+    for (int t0 = ((c + 1) / 4) * 4; t0 < NBT; t0 += 4) {
+      CT lv[4];
+      ld4(L11T + c * NBT + t0, lv);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[t0 + q] -= lv[q] * xc;
     }
-    for (int t = 0; t < w; ++t) {
-      const CT xt = xs[t * XS + tid];
-      W[(i - K0) + (int64_t)(k - K0 + t) * ldw] = T(xt);
+  }
+  // x = L21 D: to the outer block's W; L21 = x D^{-1} to the front
+  if (row_ok) {
+#pragma unroll
+    for (int t = 0; t < NBT; ++t) {
+      if (t >= w) break;
+      W[(i - K0) + (int64_t)(k - K0 + t) * ldw] = T(x[t]);
       CT l;
       if (stype[t] == 0) {
-        l = xt / sD0[t];
-      } else if (stype[t] == 1) {
-        l = (xt * sD0[t + 1] - xs[(t + 1) * XS + tid] * sD1[t]) / (sD0[t] * sD0[t + 1] - sD1[t] * sD1[t]);
+        l = x[t] / sD0[t];
+      } else if (stype[t] == 1) {  // first of a 2x2 pair (t + 1 < w)
+        const int tn = t + 1 < NBT ? t + 1 : t;
+        l = (x[t] * sD0[tn] - x[tn] * sD1[t]) / (sD0[t] * sD0[tn] - sD1[t] * sD1[t]);
       } else {
-        l = (xt * sD0[t - 1] - xs[(t - 1) * XS + tid] * sD1[t - 1]) / (sD0[t - 1] * sD0[t] - sD1[t - 1] * sD1[t - 1]);
+        const int tp = t > 0 ? t - 1 : 0;
+        l = (x[t] * sD0[tp] - x[tp] * sD1[tp]) / (sD0[tp] * sD0[t] - sD1[tp] * sD1[tp]);
       }
       F[i + (int64_t)(k + t) * f] = T(l);
-      ls[t * XS + tid] = l;
     }
   }
   if (sv.wk0) {
-    __syncthreads();
+    // K-major hi / lo copies, written warp-cooperatively (lanes along t)
     const int warp = tid >> 5, lane = tid & 31;
     const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
-    for (int rr = 0; rr < 32; ++rr) {
-      const int rloc = warp * 32 + rr;
-      const int ilr = blockIdx.x * RB + rloc;
-      if (ilr >= nrows) break;
-      const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
-      for (int t = lane; t < wpad; t += 32) {
-        const float wf = t < w ? (float)xs[t * XS + rloc] : 0.f;
-        const float lf = t < w ? (float)ls[t * XS + rloc] : 0.f;
-        const float wh = tc::tf32_hi(wf), lh = tc::tf32_hi(lf);
-        sv.wk0[base + t] = wh; sv.wk1[base + t] = wf - wh;
-        sv.wk2[base + t] = lh; sv.wk3[base + t] = lf - lh;
+    for (int pass = 0; pass < 2; ++pass) {
+      __syncthreads();
+      if (row_ok) {
+#pragma unroll
+        for (int t = 0; t < NBT; ++t) {
+          if (t >= w) break;
+          CT v = x[t];
+          if (pass == 1) {
+            if (stype[t] == 0) {
+              v = x[t] / sD0[t];
+            } else if (stype[t] == 1) {
+              const int tn = t + 1 < NBT ? t + 1 : t;
+              v = (x[t] * sD0[tn] - x[tn] * sD1[t]) / (sD0[t] * sD0[tn] - sD1[t] * sD1[t]);
+            } else {
+              const int tp = t > 0 ? t - 1 : 0;
+              v = (x[t] * sD0[tp] - x[tp] * sD1[tp]) / (sD0[tp] * sD0[t] - sD1[tp] * sD1[tp]);
+            }
+          }
+          xs[t * XS + tid] = v;
+        }
+      }
+      __syncthreads();
+      float *hi = pass == 0 ? sv.wk0 : sv.wk2, *lo = pass == 0 ? sv.wk1 : sv.wk3;
+      for (int rr = 0; rr < 32; ++rr) {
+        const int rloc = warp * 32 + rr;
+        const int ilr = blockIdx.x * RB + rloc;
+        if (ilr >= nrows) break;
+        const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
+        for (int t = lane; t < wpad; t += 32) {
+          const float v = t < w ? (float)xs[t * XS + rloc] : 0.f;
+          const float h = tc::tf32_hi(v);
+          hi[base + t] = h;
+          lo[base + t] = v - h;
+        }
       }
     }
   }
@@ -538,10 +639,11 @@ __global__ void __launch_bounds__(256) k_row_swap(DevSym d, SV sv, const int32_t
 
 // C -= A B^T on a 64 x 64 output tile, 4 x 4 per thread, K staged in chunks
 // of 32: A(r, t) = A[r + t * lda] (r < ma), B(c, t) = B[c + t * ldb] (c < nbc);
-// only entries with row + roff >= col (lower triangle) are written
+// C(r, c) is front element (row0 + r, col0 + c); only entries with
+// row + roff >= col (lower triangle) are written
 template <typename T>
-__device__ __forceinline__ void tile_gemm_sub(T *__restrict__ C, int64_t ldc, const T *__restrict__ A, int64_t lda,
-                                              int ma, const T *__restrict__ B,
+__device__ __forceinline__ void tile_gemm_sub(const FrontMat<T> &Fm, int64_t row0, int64_t col0,
+                                              const T *__restrict__ A, int64_t lda, int ma, const T *__restrict__ B,
                                               int64_t ldb, int nbc, int kk, int roff) {
   constexpr int KC = 32;
   __shared__ T As[KC][64];
@@ -588,24 +690,23 @@ __device__ __forceinline__ void tile_gemm_sub(T *__restrict__ C, int64_t ldc, co
   }
   // all 16 loads first, then the stores (distinct addresses)
   T cur[4][4];
+  T *cp[4][4];
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
     const int jl = ty + 16 * n;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int il = tx + 16 * m;
-      cur[m][n] = (jl < nbc && il < ma && il + roff >= jl) ? C[il + (int64_t)jl * ldc] : T(0);
+      const bool ok = jl < nbc && il < ma && il + roff >= jl;
+      cp[m][n] = ok ? Fm.at(row0 + il, col0 + jl) : nullptr;
+      cur[m][n] = ok ? *cp[m][n] : T(0);
     }
   }
 #pragma unroll
-  for (int n = 0; n < 4; ++n) {
-    const int jl = ty + 16 * n;
+  for (int n = 0; n < 4; ++n)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int il = tx + 16 * m;
-      if (jl < nbc && il < ma && il + roff >= jl) C[il + (int64_t)jl * ldc] = cur[m][n] - acc[m][n];
-    }
-  }
+    for (int m = 0; m < 4; ++m)
+      if (cp[m][n]) *cp[m][n] = cur[m][n] - acc[m][n];
 }
 
 // trailing update after the outer block [K0, kend):
@@ -628,39 +729,12 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
   while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
   while (bi * (bi + 1) / 2 > tile) --bi;
   const int bj = tile - bi * (bi + 1) / 2;
-  T *F = (T *)sv.F + sv.front_off[s];
+  const FrontMat<T> Fm = front_mat<T>(d, sv, s);
   const T *W = (const T *)sv.W + sv.w_off[s];
   const int64_t ldw = f - K0;
   const int r = bi * 64, cc = bj * 64;
-  tile_gemm_sub<T>(F + (int64_t)(kend + r) + (int64_t)(kend + cc) * f, f, W + (kend - K0 + r), ldw,
-                   min(64, nrows - r), F + (int64_t)(kend + cc) + (int64_t)K0 * f, f, min(64, nrows - cc), kw,
-                   r - cc);
-}
-
-// tensor-core version of k_update for FP32 fronts: 128 x 128 tiles of the
-// lower triangle, 3xTF32 products accumulated in TMEM
-__global__ void __launch_bounds__(tc::THREADS, 1) k_update_tc(DevSym d, SV sv, const int32_t *__restrict__ fronts,
-                                                               int K0, int NB, const tc::Maps *__restrict__ maps,
-                                                               int *status) {
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (K0 >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int kend = min(K0 + NB, ns);
-  const int nrows = f - kend;
-  const int nt = (nrows + tc::TILE - 1) / tc::TILE;
-  const int tile = blockIdx.x;
-  if (tile >= nt * (nt + 1) / 2) return;
-  int bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-  while (bi * (bi + 1) / 2 > tile) --bi;
-  const int bj = tile - bi * (bi + 1) / 2;
-  const int r = bi * tc::TILE, cc = bj * tc::TILE;
-  float *F = (float *)sv.F + sv.front_off[s];
-  tc::tile_update_tc(&maps[s], F + (int64_t)(kend + r) + (int64_t)(kend + cc) * f, f, min(tc::TILE, nrows - r),
-                     min(tc::TILE, nrows - cc), r - cc, kend + r, kend + cc, (kend - K0 + 31) / 32, status,
-                     DEV_TIMEOUT);
+  tile_gemm_sub<T>(Fm, kend + r, kend + cc, W + (kend - K0 + r), ldw, min(64, nrows - r),
+                   Fm.L + (int64_t)(kend + cc) + (int64_t)K0 * f, f, min(64, nrows - cc), kw, r - cc);
 }
 
 // persistent tensor-core trailing update: CTA x of front y walks tiles
@@ -679,8 +753,10 @@ __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv,
   tc::TileJob job;
   job.ntiles = nt * (nt + 1) / 2;
   if ((int)blockIdx.x >= job.ntiles) return;
-  job.C0 = (float *)sv.F + sv.front_off[s] + (int64_t)kend + (int64_t)kend * f;
-  job.ldc = f;
+  job.L = (float *)sv.F + sv.front_off[s];
+  job.CB = (float *)sv.CB + sv.cb_off[s];
+  job.f = f;
+  job.ns = ns;
   job.nrows = nrows;
   job.kend = kend;
   job.kchunks = (kend - K0 + 31) / 32;
@@ -732,69 +808,72 @@ constexpr int SB = 128;  // solve block width (independent of the pivot panel wi
 // with FP32 fronts every solve is the correction solve of mixed-precision
 // iterative refinement, whose residual and update are formed in FP64 outside.
 
-// forward, diagonal block: y_b = L_bb^{-1} r_b for every active front (one
-// CTA each); y_b goes to yz, r stays untouched for the GEMV kernel
+// Inverse of every SB x SB unit-lower diagonal block of the factor, stored
+// in the block's (otherwise unused) strict upper triangle: front element
+// (k + i, k + j), i < j, holds X(j, i) with X = L_bb^{-1}.  One CTA per block,
+// thread c computes column c of X by forward substitution (no cross-thread
+// dependency).  Run once per level after its factorization, so that every
+// later solve replaces the sequential triangular solve of a block by a
+// triangular matrix-vector product.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                   double *__restrict__ yz) {
-  using AT = T;
-  extern __shared__ unsigned char diag_raw[];
-  AT(*Ld)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(diag_raw);
-  __shared__ AT y[SB];
-  const int s = fronts[blockIdx.x];
+__global__ void __launch_bounds__(SB) k_diag_inverse(DevSym d, SV sv, const int32_t *__restrict__ fronts) {
+  extern __shared__ unsigned char inv_raw[];
+  T(*A)[SB + 1] = reinterpret_cast<T(*)[SB + 1]>(inv_raw);  // A[t][i] = L(t, i) (i < t), A[c][t] = X(t, c) (t > c)
+  const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
+  const int k = blockIdx.x * SB;
   if (k >= ns) return;
   const int f = front_order(d, s, dpn);
   const int w = min(SB, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const double *rhs = sv.rhs + sv.rhs_off[s];
-  const int tid = threadIdx.x, lane = tid & 31;
-  // strict lower triangle of the block, 8 loads in flight per thread
+  T *F = (T *)sv.F + sv.front_off[s];
+  const int c = threadIdx.x;
+  for (int i = 0; i < w; ++i)
+    if (c > i && c < w) A[c][i] = F[(int64_t)(k + c) + (int64_t)(k + i) * f];
+  __syncthreads();
+  if (c < w) {
+    for (int t = c + 1; t < w; ++t) {
+      T acc = A[t][c];
+      for (int i = c + 1; i < t; ++i) acc += A[t][i] * A[c][i];
+      A[c][t] = -acc;
+    }
+  }
+  __syncthreads();
+  for (int j = 1; j < w; ++j)
+    if (c < j) F[(int64_t)(k + c) + (int64_t)(k + j) * f] = A[c][j];  // X(j, c)
+}
+
+// loads the strict lower part of X = L_bb^{-1} of the block at k as U[j][i] = X(j, i)
+template <typename T, typename AT>
+__device__ __forceinline__ void load_block_inverse(const T *__restrict__ F, int64_t f, int k, int w,
+                                                   AT (*U)[SB + 1]) {
   const int n = w * w;
-  for (int base = tid; base < n; base += 8 * blockDim.x) {
+  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
     T v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
-      const int c = idx / w, t = idx - c * w;
-      v[u] = (idx < n && t > c) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
+      const int j = idx / w, i = idx - j * w;
+      v[u] = (idx < n && i < j) ? F[(int64_t)(k + i) + (int64_t)(k + j) * f] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
-      if (idx < n) Ld[idx % w][idx / w] = v[u];
+      if (idx < n) U[idx / w][idx % w] = (AT)v[u];
     }
   }
-  if (tid < w) y[tid] = (AT)rhs[k + tid];
-  __syncthreads();
-  for (int q = 0; q < w; q += 32) {
-    const int wq = min(32, w - q);
-    if (tid < 32) {
-      AT yl = lane < wq ? y[q + lane] : AT(0);
-      for (int c = 0; c < wq; ++c) {
-        AT yc = __shfl_sync(0xffffffffu, yl, c);
-        if (lane > c && lane < wq) yl -= Ld[q + lane][q + c] * yc;
-      }
-      if (lane < wq) y[q + lane] = yl;
-    }
-    __syncthreads();
-    for (int t = q + wq + tid; t < w; t += blockDim.x) {
-      AT acc = AT(0);
-      for (int c = 0; c < wq; ++c) acc += Ld[t][q + c] * y[q + c];
-      y[t] -= acc;
-    }
-    __syncthreads();
-  }
-  if (tid < w) yz[sv.piv_off[s] + k + tid] = (double)y[tid];
 }
 
-// forward, rows below the block: r_i -= L_ib y_b; each thread owns 2 rows
+// forward step of block [k, k + w) of every active front: y_b = X r_b (every
+// CTA forms it from the block inverse; CTA 0 stores it), then rows below:
+// r_i -= L_ib y_b, each thread owning 2 of the CTA's 512 rows
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_gemv(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                   const double *__restrict__ yz) {
+__global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                    double *__restrict__ yz) {
   using AT = T;
-  __shared__ AT y[SB];
+  extern __shared__ unsigned char blk_raw[];
+  AT(*U)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(blk_raw);
+  __shared__ AT r[SB], y[SB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
@@ -803,11 +882,22 @@ __global__ void __launch_bounds__(256) k_fwd_gemv(DevSym d, SV sv, const int32_t
   const int w = min(SB, ns - k);
   const int r0 = k + w, nrows = f - r0;
   const int row0 = blockIdx.x * 512;
-  if (row0 >= nrows) return;
-  if (threadIdx.x < w) y[threadIdx.x] = (AT)yz[sv.piv_off[s] + k + threadIdx.x];
-  __syncthreads();
-  const T *F = (const T *)sv.F + sv.front_off[s] + (int64_t)k * f;
+  if (blockIdx.x > 0 && row0 >= nrows) return;
+  const T *Ff = (const T *)sv.F + sv.front_off[s];
   double *rhs = sv.rhs + sv.rhs_off[s];
+  load_block_inverse<T, AT>(Ff, f, k, w, U);
+  if (threadIdx.x < w) r[threadIdx.x] = (AT)rhs[k + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < w) {
+    const int j = threadIdx.x;
+    AT acc = r[j];
+    for (int i = 0; i < j; ++i) acc += U[j][i] * r[i];
+    y[j] = acc;
+    if (blockIdx.x == 0) yz[sv.piv_off[s] + k + j] = (double)acc;
+  }
+  __syncthreads();
+  if (row0 >= nrows) return;
+  const T *F = Ff + (int64_t)k * f;
   const int i0 = r0 + row0 + threadIdx.x, i1 = i0 + 256;
   const bool ok0 = i0 < f, ok1 = i1 < f;
   AT a0 = AT(0), a1 = AT(0);
@@ -901,96 +991,52 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
   }
 }
 
-// backward, diagonal block: x_b = L_bb^{-T} v_b (one CTA per front); x_b is
-// written un-pivoted into the solution and, pivoted, into yz for the GEMV
+// backward step of block [k, k + w) of every active front: x_b = X^T v_b
+// (every CTA forms it from the block inverse; CTA 0 writes it, un-pivoted,
+// into the solution), then the columns left of the block: v_c -= sum_t
+// L(k + t, c) x_t, 256 columns per CTA.  v_b itself is only read here.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k, int nb,
-                                                   double *__restrict__ yz, double *__restrict__ sol) {
+__global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+                                                    int nb, double *__restrict__ yz, double *__restrict__ sol) {
   using AT = T;
-  extern __shared__ unsigned char diag_raw[];
-  AT(*Ld)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(diag_raw);
-  __shared__ AT x[SB];
-  const int s = fronts[blockIdx.x];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(SB, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const int64_t po = sv.piv_off[s];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int n = w * w;
-  for (int base = tid; base < n; base += 8 * blockDim.x) {
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int c = idx / w, t = idx - c * w;
-      v[u] = (idx < n && t > c) ? F[(int64_t)(k + t) + (int64_t)(k + c) * f] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < n) Ld[idx % w][idx / w] = v[u];
-    }
-  }
-  if (tid < w) x[tid] = (AT)yz[po + k + tid];
-  __syncthreads();
-  const int nq = (w + 31) / 32;
-  for (int qi = nq - 1; qi >= 0; --qi) {
-    const int q = qi * 32;
-    const int wq = min(32, w - q);
-    if (tid < 32) {
-      AT xl = lane < wq ? x[q + lane] : AT(0);
-      for (int c = wq - 1; c >= 0; --c) {
-        AT xc = __shfl_sync(0xffffffffu, xl, c);
-        if (lane < c) xl -= Ld[q + c][q + lane] * xc;
-      }
-      if (lane < wq) x[q + lane] = xl;
-    }
-    __syncthreads();
-    for (int t = tid; t < q; t += blockDim.x) {
-      AT acc = AT(0);
-      for (int c = 0; c < wq; ++c) acc += Ld[q + c][t] * x[q + c];
-      x[t] -= acc;
-    }
-    __syncthreads();
-  }
-  if (tid < w) {
-    yz[po + k + tid] = (double)x[tid];
-    // piv_perm is local to the pivot panel (width nb) holding position k + tid
-    const int pos = k + tid, pstart = (pos / nb) * nb;
-    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)x[tid];
-  }
-}
-
-// backward, columns left of the block: v_c -= sum_t L(k + t, c) x_t
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_gemv(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                   double *__restrict__ yz) {
-  using AT = T;
-  __shared__ AT x[SB];
+  extern __shared__ unsigned char blk_raw[];
+  AT(*U)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(blk_raw);
+  __shared__ AT v[SB], x[SB];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
   if (k >= ns) return;
-  const int col = blockIdx.x * 256 + threadIdx.x;
-  if (blockIdx.x * 256 >= k) return;
+  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= k) return;
   const int f = front_order(d, s, dpn);
   const int w = min(SB, ns - k);
   const int64_t po = sv.piv_off[s];
-  if (threadIdx.x < w) x[threadIdx.x] = (AT)yz[po + k + threadIdx.x];
+  const T *Ff = (const T *)sv.F + sv.front_off[s];
+  load_block_inverse<T, AT>(Ff, f, k, w, U);
+  if (threadIdx.x < w) v[threadIdx.x] = (AT)yz[po + k + threadIdx.x];
   __syncthreads();
+  if (threadIdx.x < w) {
+    const int i = threadIdx.x;
+    AT acc = v[i];
+    for (int j = i + 1; j < w; ++j) acc += U[j][i] * v[j];
+    x[i] = acc;
+    if (blockIdx.x == 0) {
+      // piv_perm is local to the pivot panel (width nb) holding position k + i
+      const int pos = k + i, pstart = (pos / nb) * nb;
+      sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)acc;
+    }
+  }
+  __syncthreads();
+  const int col = blockIdx.x * 256 + threadIdx.x;
   if (col >= k) return;
-  const T *Fc = (const T *)sv.F + sv.front_off[s] + (int64_t)col * f + k;
+  const T *Fc = Ff + (int64_t)col * f + k;
   AT acc = AT(0);
   int t = 0;
   for (; t + 16 <= w; t += 16) {
-    T v[16];
+    T q[16];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = Fc[t + u];
+    for (int u = 0; u < 16; ++u) q[u] = Fc[t + u];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc += (AT)v[u] * x[t + u];
+    for (int u = 0; u < 16; ++u) acc += (AT)q[u] * x[t + u];
   }
   for (; t < w; ++t) acc += (AT)Fc[t] * x[t];
   yz[po + col] -= (double)acc;
@@ -1048,7 +1094,9 @@ void factor_impl(Ctx &c, Store &st) {
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
   unsigned long long *ctr = (unsigned long long *)c.counters;
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
-  const size_t rows_smem = (size_t)(32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(T);
+  // panel kernels compiled for 16, 32 and 64 columns
+  const int nbt = nb <= 16 ? 16 : (nb <= 32 ? 32 : 64);
+  const size_t rows_smem = (size_t)(32 * nbt + nbt * nbt + nbt * 129) * sizeof(T);
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, st.dpn);
     int64_t nitems = li.i1 - li.i0;
@@ -1082,7 +1130,9 @@ void factor_impl(Ctx &c, Store &st) {
         if (max_rows > 0) {
           ProfScope ps(c, SGN_PROF_TRSM, fl);
           dim3 gp((max_rows + 127) / 128, na);
-          k_panel_rows<T><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
+          if (nbt == 16) k_panel_rows<T, 16><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
+          else if (nbt == 32) k_panel_rows<T, 32><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
+          else k_panel_rows<T, 64><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
           c.count();
         }
       }
@@ -1120,6 +1170,12 @@ void factor_impl(Ctx &c, Store &st) {
         c.count();
       }
     }
+    if (max_ns > 0) {
+      ProfScope ps(c, SGN_PROF_SOLVE);
+      dim3 gi((max_ns + SB - 1) / SB, (unsigned)(li.f1 - li.f0));
+      k_diag_inverse<T><<<gi, SB, (size_t)SB * (SB + 1) * sizeof(T), c.stream>>>(c.ds, sv, fronts);
+      c.count();
+    }
   }
   st.factored = true;
 }
@@ -1147,13 +1203,9 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
       int na = n_active(li, k);
       int max_rows = 0;
       for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - k - std::min(SB, li.ns[q] - k));
-      k_fwd_diag<T><<<na, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
+      dim3 g(std::max(1, (max_rows + 511) / 512), na);
+      k_fwd_block<T><<<g, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
       c.count();
-      if (max_rows > 0) {
-        dim3 g((max_rows + 511) / 512, na);
-        k_fwd_gemv<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, st.yz);
-        c.count();
-      }
     }
     dim3 gd((max_ns + 255) / 256, nf);
     k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts, st.yz);
@@ -1171,13 +1223,9 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     int last = ((max_ns - 1) / SB) * SB;
     for (int k = last; k >= 0; k -= SB) {
       int na = n_active(li, k);
-      k_bwd_diag<T><<<na, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
+      dim3 g(std::max(1, (k + 255) / 256), na);
+      k_bwd_block<T><<<g, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
       c.count();
-      if (k > 0) {
-        dim3 g((k + 255) / 256, na);
-        k_bwd_gemv<T><<<g, 256, 0, c.stream>>>(c.ds, sv, fronts, k, st.yz);
-        c.count();
-      }
     }
   }
 }
@@ -1315,16 +1363,19 @@ void set_kernel_attributes() {
   static bool done = false;
   if (done) return;
   done = true;
-  cudaFuncSetAttribute(k_panel_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)((32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(double)));
-  cudaFuncSetAttribute(k_panel_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)((32 * MAXNB + MAXNB * (MAXNB + 1) + 2 * MAXNB * 129) * sizeof(float)));
-  cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  cudaFuncSetAttribute(k_panel_rows<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((32 * 64 + 64 * 64 + 64 * 129) * sizeof(double)));
+  cudaFuncSetAttribute(k_panel_rows<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((32 * 64 + 64 * 64 + 64 * 129) * sizeof(float)));
+  cudaFuncSetAttribute(k_panel_rows<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((32 * 32 + 32 * 32 + 32 * 129) * sizeof(double)));
   cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
-  cudaFuncSetAttribute(k_fwd_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_fwd_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-  cudaFuncSetAttribute(k_bwd_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_bwd_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_fwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_fwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_bwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_bwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
 }
 
 void destroy_graphs(Store &s) {

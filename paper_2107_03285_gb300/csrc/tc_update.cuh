@@ -24,11 +24,8 @@ namespace tc {
 
 constexpr int TILE = 128;          // output tile (M = N)
 constexpr int KCH = 32;            // K per stage: 32 FP32 = one 128-byte swizzle row
-constexpr int STAGES = 2;
 constexpr int TILE_BYTES = TILE * KCH * 4;           // 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // Whi, Wlo, Lhi, Llo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
-constexpr int THREADS = 128;
 constexpr long long WAIT_CYCLES = 1ll << 31;         // ~1 s at 2 GHz
 
 struct Maps {                      // one set of tensor maps per front
@@ -128,147 +125,20 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 // the hi / lo split used for the 3xTF32 products
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// One 128 x 128 tile of C -= W L^T.
-//   C      : column-major, leading dimension ldc, tile origin already applied
-//   rows   : valid rows of the tile (<= 128), cols: valid columns
-//   roff   : global row offset minus global column offset of the tile origin
-//            (only entries with row + roff >= col are written: lower triangle)
-//   r0, c0 : row coordinates of the W and L tiles in their tensor maps
-//   kchunks: number of 32-wide K chunks (zero-padded beyond the true K)
-__device__ __forceinline__ void tile_update_tc(const Maps *maps, float *C, int64_t ldc, int rows, int cols, int roff,
-                                               int r0, int c0, int kchunks, int *status, int flag_timeout) {
-  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  unsigned char *sm = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-    mbar_init(&done_bar, 1);
-    abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TILE)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-
-  if (warp == 0 && lane == 0) {
-    // ---- producer
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->whi) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->wlo) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->lhi) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->llo) : "memory");
-    int issued = 0;
-    for (int kc = 0; kc < kchunks; ++kc) {
-      const int s = kc % STAGES;
-      if (kc >= STAGES) {
-        if (!mbar_wait(&empty_bar[s], ((kc / STAGES) - 1) & 1, status, flag_timeout)) { abort_flag = 1; break; }
-      }
-      if (*(volatile int *)&abort_flag) break;
-      unsigned char *st = sm + s * STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      tma_load_2d(st + 0 * TILE_BYTES, &maps->whi, &full_bar[s], kc * KCH, r0);
-      tma_load_2d(st + 1 * TILE_BYTES, &maps->wlo, &full_bar[s], kc * KCH, r0);
-      tma_load_2d(st + 2 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, c0);
-      tma_load_2d(st + 3 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, c0);
-      ++issued;
-    }
-    // drain: every issued stage must have landed before the CTA may exit
-    for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
-      mbar_wait(&full_bar[kc % STAGES], (kc / STAGES) & 1, status, flag_timeout);
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    const uint32_t idesc = idesc_tf32_128x128();
-    uint32_t acc = 0;
-    bool ok = true;
-    for (int kc = 0; kc < kchunks; ++kc) {
-      const int s = kc % STAGES;
-      if (!mbar_wait(&full_bar[s], (kc / STAGES) & 1, status, flag_timeout)) { ok = false; abort_flag = 1; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(sm + s * STAGE_BYTES);
-#pragma unroll
-      for (int k = 0; k < KCH / 8; ++k) {
-        const uint32_t off = k * 32;  // 8 TF32 = 32 bytes along the swizzled row
-        const uint64_t ahi = umma_desc_sw128(base + 0 * TILE_BYTES + off);
-        const uint64_t alo = umma_desc_sw128(base + 1 * TILE_BYTES + off);
-        const uint64_t bhi = umma_desc_sw128(base + 2 * TILE_BYTES + off);
-        const uint64_t blo = umma_desc_sw128(base + 3 * TILE_BYTES + off);
-        umma_tf32(tmem, ahi, bhi, idesc, acc);
-        acc = 1;
-        umma_tf32(tmem, ahi, blo, idesc, 1);
-        umma_tf32(tmem, alo, bhi, idesc, 1);
-      }
-      umma_commit(&empty_bar[s]);  // frees the stage once these MMAs complete
-    }
-    if (ok && kchunks > 0) umma_commit(&done_bar);
-    else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&done_bar)) : "memory");
-  }
-  __syncwarp();
-  // ---- epilogue: all four warps, warp w owns TMEM lanes 32w .. 32w + 31
-  bool done_ok = mbar_wait(&done_bar, 0, status, flag_timeout);
-  // tcgen05.ld is warp-collective: the whole warp takes the same branch
-  done_ok = __all_sync(0xffffffffu, done_ok && !*(volatile int *)&abort_flag);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (done_ok && kchunks > 0) {
-    const int r = warp * 32 + lane;
-    float *__restrict__ Cr = C + r;
-#pragma unroll 1
-    for (int cb = 0; cb < TILE; cb += 32) {
-      uint32_t v[32];
-      __syncwarp();
-      tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      if (r < rows) {
-        // all loads first, then all stores: the 32 columns are distinct
-        // addresses, so nothing serialises a load behind a store
-        float cv[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int cc = cb + j;
-          cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(Cr + (int64_t)cc * ldc) : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int cc = cb + j;
-          if (cc < cols && r + roff >= cc) __stcg(Cr + (int64_t)cc * ldc, cv[j] - __uint_as_float(v[j]));
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
-  }
-}
-
-}  // namespace tc
-}  // namespace sgn
-
-namespace sgn {
-namespace tc {
-
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised version: each CTA walks a list of tiles of one
-// front; two TMEM accumulators (2 x 128 columns) let the epilogue of tile i
+// Persistent, warp-specialised trailing update: each CTA walks a list of tiles
+// of one front; two TMEM accumulators (2 x 128 columns) let the epilogue of tile i
 // run while the producer and MMA warps already work on tile i + 1.
 //   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
 //   warps 2..5    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31)
 constexpr int PSTAGES = 3;
 constexpr int PTHREADS = 192;
-constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;
+constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;  // + alignment slack
 
 struct TileJob {                 // one front's part of a trailing update
-  float *C0;                     // F + kend + kend * f (origin of the trailing block)
-  int64_t ldc;                   // f
+  float *L;                      // the front's factor columns (f x ns, column-major)
+  float *CB;                     // its contribution block ((f - ns) x (f - ns))
+  int64_t f, ns;
   int nrows;                     // f - kend
   int kend;                      // first trailing row (TMA row coordinate of tile row 0)
   int kchunks;                   // 32-wide K chunks
@@ -394,22 +264,28 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
       tile_coords(first + lt * stride, bi, bj);
       const int rows = min(TILE, job.nrows - bi * TILE), cols = min(TILE, job.nrows - bj * TILE);
       const int roff = (bi - bj) * TILE;
-      float *__restrict__ Cr = job.C0 + (int64_t)(bi * TILE + r) + (int64_t)(bj * TILE) * job.ldc;
+      // element (gi, gj) of the front: factor column (gj < ns) or
+      // contribution block (gj >= ns, then gi >= gj >= ns)
+      const int64_t gi = (int64_t)job.kend + bi * TILE + r, gj0 = (int64_t)job.kend + bj * TILE;
+      const int64_t fcb = job.f - job.ns;
 #pragma unroll 1
       for (int cb = 0; cb < TILE; cb += 32) {
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + cb), v);
         if (r < rows) {
           float cv[32];
+          float *cp[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int cc = cb + j;
-            cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(Cr + (int64_t)cc * job.ldc) : 0.f;
+            const int64_t gj = gj0 + cc;
+            cp[j] = gj < job.ns ? job.L + gi + gj * job.f : job.CB + (gi - job.ns) + (gj - job.ns) * fcb;
+            cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(cp[j]) : 0.f;
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int cc = cb + j;
-            if (cc < cols && r + roff >= cc) __stcg(Cr + (int64_t)cc * job.ldc, cv[j] - __uint_as_float(v[j]));
+            if (cc < cols && r + roff >= cc) __stcg(cp[j], cv[j] - __uint_as_float(v[j]));
           }
         }
       }

@@ -105,3 +105,21 @@ def test_calls_before_bind_are_rejected(B):
     assert lib.sgn_assemble(h, one, one) == B.ESTATE
     assert lib.sgn_factor(h, B.FP64, None) == B.ESTATE
     lib.sgn_destroy(h)
+
+
+@pytest.mark.parametrize("which", ["kuhn3d_9", "batch2d_12"])
+def test_contribution_block_arena_plan_is_consistent(B, which):
+    """sgn_device_bytes replays the contribution-block lifetimes and fails if
+    two live blocks would share memory; the arena must also need less than
+    keeping every front whole."""
+    from sgn_inputs import make_preset
+    prob = make_preset(which)
+    lib, code, h, keep = _setup(B, prob)
+    assert code == B.OK
+    sizes = {}
+    for m in (B.STORE_FP64, B.STORE_MIXED, B.STORE_KFACT, B.STORE_KFACT_MIXED, 15):
+        n = C.c_size_t()
+        assert lib.sgn_device_bytes(h, m, C.byref(n)) == B.OK
+        sizes[m] = n.value
+    assert sizes[15] < sizes[B.STORE_FP64] + sizes[B.STORE_MIXED] + sizes[B.STORE_KFACT] + sizes[B.STORE_KFACT_MIXED]
+    lib.sgn_destroy(h)
