@@ -18,11 +18,40 @@ struct NDBuilder {
   const std::vector<std::vector<int>> &adj;   // over original node ids (free nodes only)
   int leaf;
   std::vector<uint8_t> mark;                  // scratch: 0 none, 1 L, 2 R
+  std::vector<int> comp;                      // scratch: component label, -1 outside the current set
   // output: supernodes as lists of original node ids in postorder
   std::vector<std::vector<int>> groups;
 
   NDBuilder(int d, const double *x, const std::vector<std::vector<int>> &a, int lf, int n)
-      : dim(d), X(x), adj(a), leaf(lf), mark(n, 0) {}
+      : dim(d), X(x), adj(a), leaf(lf), mark(n, 0), comp(n, -1) {}
+
+  // A disconnected node set (e.g. many independent design instances in one
+  // mesh) needs no separator: each connected component is dissected on its
+  // own and becomes its own subtree of the elimination forest.  Returns
+  // false (and leaves the scratch clean) when ids is connected.
+  bool split_components(const std::vector<int> &ids) {
+    for (int v : ids) comp[v] = -2;  // member, not yet labelled
+    std::vector<std::vector<int>> parts;
+    std::vector<int> stack;
+    for (int v0 : ids) {
+      if (comp[v0] != -2) continue;
+      const int label = (int)parts.size();
+      parts.emplace_back();
+      comp[v0] = label;
+      stack.push_back(v0);
+      while (!stack.empty()) {
+        const int u = stack.back();
+        stack.pop_back();
+        parts[label].push_back(u);
+        for (int w : adj[u])
+          if (comp[w] == -2) { comp[w] = label; stack.push_back(w); }
+      }
+    }
+    for (int v : ids) comp[v] = -1;
+    if (parts.size() < 2) return false;
+    for (auto &p : parts) build(std::move(p));
+    return true;
+  }
 
   double coord(int v, int ax) const { return X[(int64_t)v * dim + ax]; }
 
@@ -44,6 +73,7 @@ struct NDBuilder {
       groups.push_back(std::move(ids));
       return;
     }
+    if (split_components(ids)) return;
     // split along the axis of largest extent
     int axis = 0;
     double best = -1.0;

@@ -202,21 +202,22 @@ def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, si
     Instance i is a side_i x side_i grid (side_i ~ U{side_lo..side_hi}),
     clamped on its left edge, body-loaded, with its right edge tracked towards
     rest + (0, -0.05) + s_i where s_i ~ N(0, shift_sigma^2) (one 2-vector per
-    instance); p ~ N(0, p_sigma^2).  Instances are translated along x by
-    (1 + gap) apart so they never share nodes; meta["node_offsets"] and
-    meta["elem_offsets"] delimit them."""
+    instance); p ~ N(0, p_sigma^2).  Instances sit on a square grid of cells
+    (1 + gap) apart, so they never share nodes and the coordinates stay small
+    (positions far from the origin would raise the round-off floor of the
+    equilibrium residual); meta["node_offsets"] and meta["elem_offsets"]
+    delimit them, meta["origins"] holds each instance's translation."""
     rng = np.random.default_rng(seed)
     sides = rng.integers(side_lo, side_hi + 1, size=n_instances)
     Xs, conns, fixeds, fexts, tracks, targets, weights, ps = [], [], [], [], [], [], [], []
     node_off, elem_off = [0], [0]
+    per_row = int(np.ceil(np.sqrt(n_instances)))
+    origins = np.array([((i % per_row) * (1.0 + gap), (i // per_row) * (1.0 + gap)) for i in range(n_instances)])
     for i, n in enumerate(sides):
         shift = (0.0, -0.05) + rng.normal(0.0, shift_sigma, size=2)
         sub = problem_2d(int(n), seed=int(rng.integers(0, 2**31 - 1)), shift=tuple(shift), p_sigma=p_sigma)
-        dx = i * (1.0 + gap)
-        X = sub.X.copy()
-        X[:, 0] += dx
-        tgt = sub.target.reshape(-1, 2).copy()
-        tgt[:, 0] += dx
+        X = sub.X + origins[i]
+        tgt = sub.target.reshape(-1, 2) + origins[i]
         Xs.append(X)
         conns.append(sub.conn + node_off[-1])
         fixeds.append(sub.fixed_node)
@@ -232,7 +233,7 @@ def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, si
                    np.concatenate(targets), np.concatenate(weights), 1e-4, 1e4, 0.3, np.concatenate(ps),
                    meta={"sides": sides, "node_offsets": np.array(node_off), "elem_offsets": np.array(elem_off),
                          "seed": seed, "side_lo": side_lo, "side_hi": side_hi, "shift_sigma": shift_sigma,
-                         "p_sigma": p_sigma})
+                         "p_sigma": p_sigma, "origins": origins})
 
 
 def problem_rbf3d(n: int = 40, n_rbf: int = 64, width: float = 0.15, seed: int = 0,
@@ -242,11 +243,11 @@ def problem_rbf3d(n: int = 40, n_rbf: int = 64, width: float = 0.15, seed: int =
     exp(-|X_e - c_k|^2 / (2 width^2)) at the tet centroid X_e, with centres
     c_k ~ U[0,1]^3 (seeded).  meta holds the centres, the width and theta_sigma
     (coefficient vectors theta ~ N(0, theta_sigma^2), see draw_thetas).
-    load_scale defaults to (41 / (n + 1))^2: every resolution carries the
-    total top-face load of the 40-cell cube (about 15% peak displacement,
-    four Newton iterations from the rest shape)."""
+    load_scale defaults to (40 / n)^2 (n nodes per side): every resolution
+    carries the total top-face load of the 40^3-node cube (about 15% peak
+    displacement, four to five Newton iterations from the rest shape)."""
     if load_scale is None:
-        load_scale = (41.0 / (n + 1)) ** 2
+        load_scale = (40.0 / n) ** 2
     prob = problem_3d(n, seed=seed, load_scale=load_scale)
     rng = np.random.default_rng(seed + 7919)
     centers = rng.uniform(0.0, 1.0, size=(n_rbf, 3))
@@ -267,8 +268,9 @@ PRESETS = {
     "grid2d_21": lambda seed=0: problem_2d(21, seed=seed),
     # 40^3 Kuhn tets, 355,914 elements, p = 0
     "kuhn3d_40": lambda seed=0: problem_3d(40, seed=seed),
-    # 80^3 Kuhn tets, 2,958,234 elements
-    "kuhn3d_80": lambda seed=0: problem_3d(80, seed=seed),
+    # 80^3 Kuhn tets, 2,958,234 elements; the same cube under the same total
+    # top-face load as kuhn3d_40 (per-node loads scaled by (40/80)^2)
+    "kuhn3d_80": lambda seed=0: problem_3d(80, seed=seed, load_scale=0.25, name="kuhn3d_80"),
     # 40^3 cube with 64 RBF design coefficients (learned warm start)
     "rbf3d_40": lambda seed=0: problem_rbf3d(40, seed=seed),
     # 256 plane-strain instances, sides ~ U{10..60}

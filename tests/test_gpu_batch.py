@@ -45,8 +45,7 @@ def _batch_state(batch, subs):
     for i, sub in enumerate(subs):
         xi, info = EQ.newton(sub, sub.p0)
         assert info["converged"]
-        shift = batch.X[no[i], 0] - sub.X[0, 0]
-        x[no[i]:no[i + 1]] = xi + np.array([shift, 0.0])
+        x[no[i]:no[i + 1]] = xi + batch.meta["origins"][i]
         b = S.blocks(sub, xi, sub.p0)
         refs.append(S.sgn_step(b, "kkt")[1])
     return x, refs
@@ -94,8 +93,7 @@ def test_batch_of_256_runs_and_samples_match_oracle(P):
     for i in sample:
         # GPU equilibrium of the batch == oracle equilibrium of the instance
         xi, _ = refs[i]
-        shift = batch.X[no[i], 0] - subs[i].X[0, 0]
-        np.testing.assert_allclose(xg[no[i]:no[i + 1]] - [shift, 0.0], xi, rtol=0, atol=1e-8)
+        np.testing.assert_allclose(xg[no[i]:no[i + 1]] - batch.meta["origins"][i], xi, rtol=0, atol=1e-8)
     _, dp64, _, _, _ = s.step(xg, batch.p0, P.FP64)
     dp64 = dp64.cpu().numpy()
     _, dpm, _, _, srep = s.step(xg, batch.p0, P.MIXED)
@@ -128,4 +126,26 @@ def test_graph_step_equals_stepwise_calls(P):
     dpn = out[1].cpu().numpy()
     for i, ref in enumerate(refs):
         assert np.linalg.norm(dpn[eo[i]:eo[i + 1]] - ref) / np.linalg.norm(ref) < 1e-8
+    s.close()
+
+
+def test_autotuned_setup_keeps_parity(P, tmp_path):
+    """The autotuner times the graph-captured step for a few (leaf, panel)
+    pairs, caches the fastest, and the chosen set-up still matches the oracle
+    instance by instance."""
+    from paper_2107_03285_gb300 import autotune as A
+    batch = problem_batch2d(12, seed=7, side_lo=5, side_hi=24)
+    subs = _instances(batch)
+    x, refs = _batch_state(batch, subs)
+    cands = [(8, 16), (16, 32), (32, 64)]
+    path = str(tmp_path / "tune.json")
+    best = A.tune(P, batch, P.MIXED, cache_path=path, x=x, cands=cands, reps=3, warmup=1)
+    assert (best.leaf_nodes, best.panel) in cands and best.ms > 0
+    assert A.tune(P, batch, P.MIXED, cache_path=path, x=x, cands=cands) == best
+    s = P.SGN.from_problem(batch, stores=P.STORE_MIXED, leaf_nodes=best.leaf_nodes, panel=best.panel)
+    _, dp, _, _, _ = s.step(x, batch.p0, P.MIXED)
+    dp = dp.cpu().numpy()
+    eo = batch.meta["elem_offsets"]
+    for i, ref in enumerate(refs):
+        assert np.linalg.norm(dp[eo[i]:eo[i + 1]] - ref) / np.linalg.norm(ref) < 1e-8, i
     s.close()
