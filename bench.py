@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--cpu-sample", default="kuhn3d_12", help="oracle sample workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--batch-workload", default="batch2d_256",
+                    help="batched form: many uneven 2D instances in one graph-captured step ('' skips)")
+    ap.add_argument("--warm-workload", default="rbf3d_40", help="learned warm start form ('' skips)")
+    ap.add_argument("--scale-workload", default="kuhn3d_80",
+                    help="largest single-GPU mixed-precision workload, timed once ('' skips)")
+    ap.add_argument("--warm-snapshots", type=int, default=128)
+    ap.add_argument("--warm-tests", type=int, default=6)
     return ap.parse_args()
 
 
@@ -117,26 +124,40 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_step_rate(sample: str, seconds: float, seed: int):
-    """The CPU oracle, as it stands: element blocks + SuperLU solve of the
-    saddle-point system, on a smaller mesh of the same family."""
+def oracle_state(sample: str, seed: int):
+    """A smaller mesh of the same family at its oracle equilibrium."""
     from oracle import equilibrium as EQ
-    from oracle import system as S
     from sgn_inputs import make_preset
     prob = make_preset(sample, seed=seed)
     x, _ = EQ.newton(prob, prob.p0)
+    return prob, x
+
+
+def oracle_step(prob, x):
+    """One SGN step of the CPU oracle, as it stands: element blocks and a
+    SuperLU solve of the saddle-point system."""
+    from oracle import system as S
+    b = S.blocks(prob, x, prob.p0)
+    S.sgn_step(b, "kkt")
+
+
+def oracle_info(sample, prob, n, dt):
+    N = 2 * prob.n_free * prob.dim + prob.n_elem
+    return {"kind": "oracle", "cores": os.cpu_count(),
+            "sample": f"{sample}: {prob.n_elem} elements, N={N}; {n} steps in {dt:.1f} s "
+                      f"(NumPy elements + SciPy SuperLU, host cores; equilibrium computed before timing)"}
+
+
+def oracle_step_rate(sample: str, seconds: float, seed: int):
+    prob, x = oracle_state(sample, seed)
     n, t0 = 0, time.perf_counter()
     while True:
-        b = S.blocks(prob, x, prob.p0)
-        S.sgn_step(b, "kkt")
+        oracle_step(prob, x)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    N = 2 * prob.n_free * prob.dim + prob.n_elem
-    return n / dt, {"kind": "oracle", "cores": os.cpu_count(),
-                    "sample": f"{sample}: {prob.n_elem} elements, N={N}; {n} steps in {dt:.1f} s "
-                              f"(NumPy elements + SciPy SuperLU, host cores)"}
+    return n / dt, oracle_info(sample, prob, n, dt)
 
 
 def run_reference(args):
@@ -144,16 +165,17 @@ def run_reference(args):
     if ws > 1 and rank != 0:
         return
     from sgn_inputs import make_preset
-    rate_w = None
+    prob_s, x_s = oracle_state(args.cpu_sample, args.seed)
     for _ in range(max(args.warmup, 0)):
-        rate_w, _ = oracle_step_rate(args.cpu_sample, 0.0, args.seed)
+        oracle_step(prob_s, x_s)
     t0 = time.perf_counter()
     n = 0
     for _ in range(args.steps):
-        r, info = oracle_step_rate(args.cpu_sample, 0.0, args.seed)
+        oracle_step(prob_s, x_s)
         n += 1
     dt = time.perf_counter() - t0
     value = n / dt
+    info = oracle_info(args.cpu_sample, prob_s, n, dt)
     info["value"] = value
     info["unit"] = UNIT
     prob = make_preset(args.workload)
@@ -165,6 +187,193 @@ def run_reference(args):
             "cpu_baseline": info,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def form_batched(P, torch, args):
+    """Many uneven plane-strain instances (one disjoint mesh, one elimination
+    forest): the mixed step as one CUDA-graph launch (assemble, factor, solve,
+    4 refinement solves) against the stepwise plain FP64 path on the same
+    batch."""
+    from sgn_inputs import make_preset
+    prob = make_preset(args.batch_workload, seed=args.seed)
+    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED)
+    try:
+        (x64, r64), t64e = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.FP64))
+        (x, rep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.MIXED))
+        eq64 = {"iters": r64.iters, "residual": r64.residual, "seconds": t64e,
+                "history": list(r64.history)[:r64.iters + 1], "max_abs_dx_vs_mixed": float((x64 - x).abs().max())}
+        del x64
+        p = torch.as_tensor(prob.p0, device=x.device)
+        out = (torch.empty_like(x), torch.empty_like(p), torch.empty_like(x))
+        s.step(x, p, P.FP64)
+        (_, dp64, _, _, _), t64 = _timed(torch, lambda: s.step(x, p, P.FP64))
+        dp64 = dp64.clone()
+        for _ in range(3):
+            s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=False)
+        n = 10
+        l0 = s.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(n):
+            s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=False)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        launches = (s.launch_count() - l0) / n
+        _, dpg, _, res = s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=True)
+        err = float(torch.linalg.norm(dpg - dp64) / torch.linalg.norm(dp64))
+        k = len(prob.meta["sides"])
+        return {"workload": f"{args.batch_workload}: {k} instances, sides {min(prob.meta['sides'])}.."
+                            f"{max(prob.meta['sides'])}, {prob.n_nodes} nodes, {prob.n_elem} triangles, "
+                            f"N={int(s.info.n_kkt)}",
+                "graph_mixed": {"steps_per_s": 1e3 / ms, "instance_steps_per_s": k * 1e3 / ms, "ms_per_step": ms,
+                                "launches_per_graph": launches, "kkt_residual": res,
+                                "dp_rel_err_vs_fp64_gpu": err},
+                "stepwise_fp64": {"steps_per_s": 1.0 / t64, "ms_per_step": 1e3 * t64},
+                "speedup_vs_fp64": (1e3 / ms) * t64,
+                "equilibrium_mixed": {"iters": rep.iters, "solves": rep.solves, "residual": rep.residual,
+                                      "seconds": t_eq, "history": list(rep.history)[:rep.iters + 1]},
+                "equilibrium_fp64": eq64,
+                "levels": int(s.info.n_levels), "supernodes": int(s.info.n_supernodes)}
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
+
+
+def form_scale(P, torch, args):
+    """The 80^3-node cube in the mixed path (FP32 fronts on the tensor cores,
+    FP64 refinement): mixed Newton to the equilibrium, then timed SGN steps;
+    the FP64 path does not fit beside it (its fronts alone need 298 GB) and
+    would take minutes per factorization, so accuracy is shown by the FP64
+    residual of the full system and the inertia."""
+    from sgn_inputs import make_preset
+    prob = make_preset(args.scale_workload, seed=args.seed)
+    (s, t_setup) = _timed(torch, lambda: P.SGN.from_problem(prob, stores=P.STORE_MIXED | P.STORE_KFACT_MIXED))
+    try:
+        (x, rep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.MIXED))
+        p = torch.as_tensor(prob.p0, device=x.device)
+        out = (torch.empty_like(x), torch.empty_like(p), torch.empty_like(x))
+        s.assemble(x, p)
+        frep = s.factor(P.MIXED)
+        _, _, _, srep = s.solve(P.RHS_KKT, out=out)
+        n = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            s.assemble(x, p)
+            s.factor(P.MIXED, report=False)
+            s.solve(P.RHS_KKT, report=False, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        n_x = prob.n_free * prob.dim
+        return {"workload": f"{args.scale_workload}: {prob.n_elem} tets, {prob.n_nodes} nodes, "
+                            f"N={int(s.info.n_kkt)}",
+                "precision": "mixed", "steps_per_s": 1e3 / ms, "ms_per_step": ms,
+                "factor_tflops": s.info.factor_flops / (ms * 1e-3) / 1e12,
+                "device_gb": s.buf.numel() / 1e9, "setup_and_bind_s": t_setup,
+                "kkt_residual": srep.residual, "refine_steps": srep.refine_steps,
+                "inertia_ok": (frep.n_pos, frep.n_neg, frep.n_zero) == (n_x + prob.n_elem, n_x, 0),
+                "factor_flops": s.info.factor_flops, "nnz_factor": s.info.nnz_factor,
+                "equilibrium_mixed": {"iters": rep.iters, "residual": rep.residual, "seconds": t_eq}}
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
+
+
+def form_warm_start(P, torch, args):
+    """Learned warm start on the RBF-parameterised cube: equilibria at seeded
+    designs theta ~ N(0, 0.3^2) as snapshots (mixed Newton from the rest
+    shape), randomised-SVD basis, BF16 MLP trained by the library's AdamW
+    kernels, then Newton on held-out designs from (a) the rest shape, (b) the
+    previous iterate (the equilibrium of a design one step away) and (c) the
+    better of the learned prediction and (b)."""
+    from sgn_inputs import draw_thetas, make_preset
+    prob = make_preset(args.warm_workload, seed=args.seed)
+    ns, nt = args.warm_snapshots, args.warm_tests
+    s = P.SGN.from_problem(prob, stores=P.STORE_KFACT_MIXED)
+    n_modes = min(128, ns - 1)
+    ws = P.WarmStart(s, prob.meta["rbf_centers"], prob.meta["rbf_width"], n_modes=n_modes, hidden=512,
+                     max_snap=ns, batch=min(64, ns))
+    try:
+        thetas = draw_thetas(prob, ns + nt, seed=args.seed + 101)
+        X = torch.as_tensor(prob.X, device="cuda")
+        snaps = torch.empty((ns,) + tuple(X.shape), dtype=torch.float64, device="cuda")
+        cold_it, cold_t = [], []
+        for i in range(ns):
+            (x, rep), dt = _timed(torch, lambda: s.equilibrium(ws.rbf_params(thetas[i]), prob.fext,
+                                                               precision=P.MIXED))
+            if not rep.converged:
+                raise RuntimeError("snapshot equilibrium did not converge")
+            snaps[i] = x - X
+            cold_it.append(rep.iters)
+            cold_t.append(dt)
+        _, t_basis = _timed(torch, lambda: ws.fit_basis(snaps, seed=1))
+        steps = 3000
+        loss, t_train = _timed(torch, lambda: ws.train(thetas[:ns], snaps, steps=steps, lr=1e-3,
+                                                       weight_decay=1e-5, seed=2))
+        rng = np.random.default_rng(args.seed + 7)
+        arms = ("rest", "learned", "prev_small", "learned_or_prev_small", "prev_large", "learned_or_prev_large")
+        res = {a: [] for a in arms}
+
+        def rec(arm, r, t, used=None):
+            e = {"iters": r.iters, "initial_residual": r.initial_residual, "residual": r.residual,
+                 "converged": bool(r.converged), "seconds": t}
+            if used is not None:
+                e["used_learned"] = bool(used)
+            res[arm].append(e)
+
+        for th in thetas[ns:]:
+            pd = ws.rbf_params(th)
+            (_, r), t = _timed(torch, lambda: s.equilibrium(pd, prob.fext, precision=P.MIXED))
+            rec("rest", r, t)
+            (_, r, used), t = _timed(torch, lambda: ws.equilibrium(th, prob.fext, precision=P.MIXED))
+            rec("learned", r, t, used)
+            # previous iterate: the equilibrium of a design one SGN step away
+            # (small: 10% of theta's spread per coefficient; large: 50%)
+            for tag, sig in (("small", 0.03), ("large", 0.15)):
+                xp, _ = s.equilibrium(ws.rbf_params(th + rng.normal(0.0, sig, size=th.shape)), prob.fext,
+                                      precision=P.MIXED)
+                (_, r), t = _timed(torch, lambda: s.equilibrium(pd, prob.fext, x0=xp, precision=P.MIXED))
+                rec("prev_" + tag, r, t)
+                (_, r, used), t = _timed(torch, lambda: ws.equilibrium(th, prob.fext, x_prev=xp,
+                                                                        precision=P.MIXED))
+                rec("learned_or_prev_" + tag, r, t, used)
+
+        def summ(v):
+            out = {"mean_iters": float(np.mean([e["iters"] for e in v])),
+                   "median_initial_residual": float(np.median([e["initial_residual"] for e in v])),
+                   "max_final_residual": float(max(e["residual"] for e in v)),
+                   "all_converged": all(e["converged"] for e in v),
+                   "mean_seconds": float(np.mean([e["seconds"] for e in v]))}
+            if "used_learned" in v[0]:
+                out["used_learned"] = int(sum(e["used_learned"] for e in v))
+            return out
+        out = {k: summ(v) for k, v in res.items()}
+        return {"workload": f"{args.warm_workload}: {prob.n_elem} tets, {prob.n_nodes} nodes, "
+                            f"{prob.meta['n_rbf']} RBF coefficients",
+                "reduced": f"{ns} snapshots (not 4,096), {n_modes} modes, MLP {prob.meta['n_rbf']}-512-512-"
+                           f"{n_modes}, {steps} AdamW steps; held-out designs: {nt}",
+                "snapshots": {"mean_iters": float(np.mean(cold_it)), "mean_seconds": float(np.mean(cold_t))},
+                "basis_seconds": t_basis, "train_seconds": t_train, "train_final_loss": loss,
+                "newton_from": out,
+                "iters_saved_vs_rest": out["rest"]["mean_iters"] - out["learned"]["mean_iters"],
+                "iters_saved_vs_prev_small": out["prev_small"]["mean_iters"]
+                - out["learned_or_prev_small"]["mean_iters"],
+                "iters_saved_vs_prev_large": out["prev_large"]["mean_iters"]
+                - out["learned_or_prev_large"]["mean_iters"]}
+    finally:
+        ws.close()
+        s.close()
+        torch.cuda.empty_cache()
 
 
 def main():
@@ -188,13 +397,19 @@ def main():
 
     prob = make_preset(args.workload, seed=args.seed)
     prec = P.MIXED if args.precision == "mixed" else P.FP64
-    stores = P.STORE_KFACT | P.STORE_FP64 | (P.STORE_MIXED if prec == P.MIXED else 0)
+    stores = P.STORE_KFACT | P.STORE_FP64 | (P.STORE_MIXED | P.STORE_KFACT_MIXED if prec == P.MIXED else 0)
     t_setup = time.perf_counter()
     s = P.SGN.from_problem(prob, stores=stores)
     t_setup = time.perf_counter() - t_setup
     info = s.info
     # forward simulation to the equilibrium the step is taken at (reported separately)
-    xeq, nrep = s.equilibrium(prob.p0, prob.fext)
+    (xeq, nrep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=prec))
+    equilibrium = {"precision": args.precision, "iters": nrep.iters, "residual": nrep.residual, "seconds": t_eq}
+    if prec == P.MIXED:
+        (x64, r64), t64 = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.FP64))
+        equilibrium["fp64"] = {"iters": r64.iters, "residual": r64.residual, "seconds": t64,
+                               "max_abs_dx_vs_mixed": float((x64 - xeq).abs().max())}
+        del x64
     p = torch.as_tensor(prob.p0, device=dev)
     out = (torch.empty_like(xeq), torch.empty_like(p), torch.empty_like(xeq))
 
@@ -325,15 +540,29 @@ def main():
                    "factor_flops": info.factor_flops,
                    "nnz_factor": info.nnz_factor, "fp64_path": fp64,
                    "phases": phases, "kernel_kinds_profiled_step": kinds, "setup_s": info.setup_seconds, "bind_s": t_setup,
-                   "equilibrium": {"iters": nrep.iters, "residual": nrep.residual, "seconds": nrep.seconds}},
+                   "equilibrium": equilibrium},
         "roofline": roofline,
         "cpu_baseline": cpu_info,
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
-    print(json.dumps(line))
     s.close()
+    del s
+    torch.cuda.empty_cache()
+    if ws == 1:
+        forms = {}
+        for name, fn, wl in (("batched", form_batched, args.batch_workload),
+                             ("learned_warm_start", form_warm_start, args.warm_workload),
+                             ("scale", form_scale, args.scale_workload)):
+            if not wl:
+                continue
+            try:
+                forms[name] = fn(P, torch, args)
+            except Exception as e:  # a form that fails is reported, not hidden
+                forms[name] = {"error": f"{type(e).__name__}: {e}"}
+        line["config"]["forms"] = forms
+    print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
 
