@@ -204,7 +204,11 @@ def form_batched(P, torch, args):
     batch."""
     from sgn_inputs import make_preset
     prob = make_preset(args.batch_workload, seed=args.seed)
-    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED)
+    from paper_2107_03285_gb300 import autotune
+    tuned = autotune.lookup(prob, P.MIXED)
+    leaf, panel = tuned if tuned else (0, 0)
+    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED,
+                           leaf_nodes=leaf, panel=panel)
     try:
         (x64, r64), t64e = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.FP64))
         (x, rep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.MIXED))
@@ -242,7 +246,44 @@ def form_batched(P, torch, args):
                 "equilibrium_mixed": {"iters": rep.iters, "solves": rep.solves, "residual": rep.residual,
                                       "seconds": t_eq, "history": list(rep.history)[:rep.iters + 1]},
                 "equilibrium_fp64": eq64,
-                "levels": int(s.info.n_levels), "supernodes": int(s.info.n_supernodes)}
+                "levels": int(s.info.n_levels), "supernodes": int(s.info.n_supernodes),
+                "setup_options": {"leaf_nodes": leaf or 16, "panel": panel or 32,
+                                  "source": "autotuned" if tuned else "defaults"}}
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
+
+
+def form_batched_sharded(P, torch, args, ws, rank):
+    """The batched workload split over the ranks (cost-balanced, no data
+    exchange): every rank builds and times its own share as one graph step;
+    the batch's rate is set by the slowest rank."""
+    from paper_2107_03285_gb300 import shard
+    from sgn_inputs import make_preset, select_instances
+    batch = make_preset(args.batch_workload, seed=args.seed)
+    parts = shard.partition(shard.instance_costs(batch.meta["sides"]), ws)
+    prob = select_instances(batch, parts[rank])
+    s = P.SGN.from_problem(prob, stores=P.STORE_MIXED | P.STORE_KFACT_MIXED)
+    try:
+        x, rep = s.equilibrium(prob.p0, prob.fext, precision=P.MIXED)
+        p = torch.as_tensor(prob.p0, device=x.device)
+        out = (torch.empty_like(x), torch.empty_like(p), torch.empty_like(x))
+        for _ in range(3):
+            s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=False)
+        n = 10
+        torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(n):
+            s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=False)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = shard.max_over_ranks(e0.elapsed_time(e1) / n, device=x.device)
+        k = len(batch.meta["sides"])
+        return {"workload": f"{args.batch_workload} over {ws} ranks (cost-balanced, no collective on the data path)",
+                "instances_per_rank": [int(len(q)) for q in parts], "ms_per_step_slowest_rank": ms,
+                "steps_per_s": 1e3 / ms, "instance_steps_per_s": k * 1e3 / ms, "scaling": "strong"}
     finally:
         s.close()
         torch.cuda.empty_cache()
@@ -398,9 +439,13 @@ def main():
     prob = make_preset(args.workload, seed=args.seed)
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     stores = P.STORE_KFACT | P.STORE_FP64 | (P.STORE_MIXED | P.STORE_KFACT_MIXED if prec == P.MIXED else 0)
+    from paper_2107_03285_gb300 import autotune
+    tuned = autotune.lookup(prob, prec)
+    leaf, panel = tuned if tuned else (0, 0)
     t_setup = time.perf_counter()
-    s = P.SGN.from_problem(prob, stores=stores)
+    s = P.SGN.from_problem(prob, stores=stores, leaf_nodes=leaf, panel=panel)
     t_setup = time.perf_counter() - t_setup
+    buf_gb = s.buf.numel() / 1e9
     info = s.info
     # forward simulation to the equilibrium the step is taken at (reported separately)
     (xeq, nrep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=prec))
@@ -497,8 +542,15 @@ def main():
     e2e = {"value": ws / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(xnp.nbytes + pnp.nbytes),
            "d2h_bytes_per_step": int(2 * xnp.nbytes + pnp.nbytes)}
 
-    if rank != 0:
+    sharded = None
+    if ws > 1 and args.batch_workload:
         s.close()
+        torch.cuda.empty_cache()
+        try:
+            sharded = form_batched_sharded(P, torch, args, ws, rank)
+        except Exception as e:  # reported, not hidden
+            sharded = {"error": f"{type(e).__name__}: {e}"}
+    if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
@@ -522,9 +574,12 @@ def main():
                     "traffic": None, "peak_source": "measured FP64 FMA-chain probe on this pool's GB300"}
     roofline["launches_per_step"] = prof_launches / args.steps
     roofline["share_of_step"] = prof_seconds / (ms * 1e-3 * args.steps)
-    cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
-    cpu_info["value"] = cpu_rate
-    cpu_info["unit"] = UNIT
+    if ws == 1:
+        cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
+        cpu_info["value"] = cpu_rate
+        cpu_info["unit"] = UNIT
+    else:
+        cpu_info = None  # the oracle baseline is timed at N = 1 only
     N = int(info.n_kkt)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -533,7 +588,10 @@ def main():
         "config": {"workload": f"{args.workload}: {prob.n_elem} tets, {prob.n_nodes} nodes, N={N} saddle-point "
                                f"unknowns, p = per-tet log-modulus",
                    "precision": args.precision, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                   "l2": f"not flushed: the step's working set ({s.buf.numel() / 1e9:.1f} GB) exceeds L2",
+                   "setup_options": {"leaf_nodes": leaf or 16, "panel": panel or 32,
+                                     "source": "autotuned (paper_2107_03285_gb300/tuned.json)" if tuned
+                                     else "defaults"},
+                   "l2": f"not flushed: the step's working set ({buf_gb:.1f} GB) exceeds L2",
                    "dp_rel_err_vs_fp64_gpu": dp_err, "refine_steps": srep.refine_steps,
                    "kkt_residual": srep.residual,
                    "refine_history": [float(v) for v in list(srep.history)[:srep.refine_steps + 1]],
@@ -547,9 +605,12 @@ def main():
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
-    s.close()
+    if s.h is not None:
+        s.close()
     del s
     torch.cuda.empty_cache()
+    if sharded is not None:
+        line["config"]["forms"] = {"batched_sharded": sharded}
     if ws == 1:
         forms = {}
         for name, fn, wl in (("batched", form_batched, args.batch_workload),

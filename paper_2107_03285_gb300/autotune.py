@@ -30,6 +30,19 @@ from . import binding as B
 PANELS = (16, 32, 64)
 LEAVES = (8, 16, 32, 64)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sgn_autotune.json")
+# tuned choices for the standard workloads, shipped with the package
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def lookup(prob, precision, paths=(SHIPPED, DEFAULT_CACHE)):
+    """(leaf_nodes, panel) tuned for prob's pattern in the first cache that
+    has it, else None."""
+    key = pattern_key(prob, precision)
+    for path in paths:
+        e = load_cache(path).get(key) if path else None
+        if e is not None:
+            return int(e["leaf_nodes"]), int(e["panel"])
+    return None
 
 
 @dataclass(frozen=True)
@@ -142,3 +155,25 @@ def tune(P, prob, precision=B.MIXED, cache_path: str | None = DEFAULT_CACHE, x=N
                       "timings": {f"{l}/{p}": t for (l, p), t in timings.items()}}
         store_cache(cache_path, cache)
     return best
+
+
+def main(argv=None):
+    """python -m paper_2107_03285_gb300.autotune --workload kuhn3d_40 [--precision mixed] [--out PATH]"""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", action="append", required=True)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--out", default=SHIPPED)
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args(argv)
+    import paper_2107_03285_gb300 as P
+    from sgn_inputs import make_preset
+    prec = B.MIXED if args.precision == "mixed" else B.FP64
+    for wl in args.workload:
+        prob = make_preset(wl)
+        best = tune(P, prob, prec, cache_path=args.out, force=True, reps=args.reps)
+        print(json.dumps({"workload": wl, "leaf_nodes": best.leaf_nodes, "panel": best.panel, "ms": best.ms}))
+
+
+if __name__ == "__main__":
+    main()

@@ -848,16 +848,16 @@ template <typename T, typename AT>
 __device__ __forceinline__ void load_block_inverse(const T *__restrict__ F, int64_t f, int k, int w,
                                                    AT (*U)[SB + 1]) {
   const int n = w * w;
-  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
-    T v[8];
+  for (int base = threadIdx.x; base < n; base += 16 * blockDim.x) {
+    T v[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int idx = base + u * blockDim.x;
       const int j = idx / w, i = idx - j * w;
       v[u] = (idx < n && i < j) ? F[(int64_t)(k + i) + (int64_t)(k + j) * f] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int idx = base + u * blockDim.x;
       if (idx < n) U[idx / w][idx % w] = (AT)v[u];
     }
@@ -866,9 +866,9 @@ __device__ __forceinline__ void load_block_inverse(const T *__restrict__ F, int6
 
 // forward step of block [k, k + w) of every active front: y_b = X r_b (every
 // CTA forms it from the block inverse; CTA 0 stores it), then rows below:
-// r_i -= L_ib y_b, each thread owning 2 of the CTA's 512 rows
+// r_i -= L_ib y_b, one row per thread (256 per CTA), 32 loads in flight
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+__global__ void __launch_bounds__(256, 2) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                     double *__restrict__ yz) {
   using AT = T;
   extern __shared__ unsigned char blk_raw[];
@@ -881,46 +881,34 @@ __global__ void __launch_bounds__(256) k_fwd_block(DevSym d, SV sv, const int32_
   const int f = front_order(d, s, dpn);
   const int w = min(SB, ns - k);
   const int r0 = k + w, nrows = f - r0;
-  const int row0 = blockIdx.x * 512;
+  const int row0 = blockIdx.x * 256;
   if (blockIdx.x > 0 && row0 >= nrows) return;
   const T *Ff = (const T *)sv.F + sv.front_off[s];
   double *rhs = sv.rhs + sv.rhs_off[s];
   load_block_inverse<T, AT>(Ff, f, k, w, U);
-  if (threadIdx.x < w) r[threadIdx.x] = (AT)rhs[k + threadIdx.x];
+  if (threadIdx.x < SB) r[threadIdx.x] = threadIdx.x < w ? (AT)rhs[k + threadIdx.x] : AT(0);
   __syncthreads();
-  if (threadIdx.x < w) {
+  if (threadIdx.x < SB) {
     const int j = threadIdx.x;
     AT acc = r[j];
-    for (int i = 0; i < j; ++i) acc += U[j][i] * r[i];
-    y[j] = acc;
-    if (blockIdx.x == 0) yz[sv.piv_off[s] + k + j] = (double)acc;
+    for (int i = 0; i < min(j, w); ++i) acc += U[j][i] * r[i];
+    y[j] = j < w ? acc : AT(0);
+    if (blockIdx.x == 0 && j < w) yz[sv.piv_off[s] + k + j] = (double)acc;
   }
   __syncthreads();
   if (row0 >= nrows) return;
   const T *F = Ff + (int64_t)k * f;
-  const int i0 = r0 + row0 + threadIdx.x, i1 = i0 + 256;
-  const bool ok0 = i0 < f, ok1 = i1 < f;
-  AT a0 = AT(0), a1 = AT(0);
-  int t = 0;
-  for (; t + 8 <= w; t += 8) {
-    T v0[8], v1[8];
+  const int i0 = r0 + row0 + threadIdx.x;
+  if (i0 >= f) return;
+  AT a0 = AT(0);
+  for (int t = 0; t < w; t += 32) {
+    T v0[32];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      v0[u] = ok0 ? F[(int64_t)(t + u) * f + i0] : T(0);
-      v1[u] = ok1 ? F[(int64_t)(t + u) * f + i1] : T(0);
-    }
+    for (int u = 0; u < 32; ++u) v0[u] = t + u < w ? F[(int64_t)(t + u) * f + i0] : T(0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      a0 += (AT)v0[u] * y[t + u];
-      a1 += (AT)v1[u] * y[t + u];
-    }
+    for (int u = 0; u < 32; ++u) a0 += (AT)v0[u] * y[t + u];
   }
-  for (; t < w; ++t) {
-    if (ok0) a0 += (AT)F[(int64_t)t * f + i0] * y[t];
-    if (ok1) a1 += (AT)F[(int64_t)t * f + i1] * y[t];
-  }
-  if (ok0) rhs[i0] -= (double)a0;
-  if (ok1) rhs[i1] -= (double)a1;
+  rhs[i0] -= (double)a0;
 }
 
 __global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts, double *__restrict__ yz) {
@@ -996,7 +984,7 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
 // into the solution), then the columns left of the block: v_c -= sum_t
 // L(k + t, c) x_t, 256 columns per CTA.  v_b itself is only read here.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
+__global__ void __launch_bounds__(256, 2) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                     int nb, double *__restrict__ yz, double *__restrict__ sol) {
   using AT = T;
   extern __shared__ unsigned char blk_raw[];
@@ -1025,21 +1013,35 @@ __global__ void __launch_bounds__(256) k_bwd_block(DevSym d, SV sv, const int32_
       sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)acc;
     }
   }
+  if (threadIdx.x >= w && threadIdx.x < SB) x[threadIdx.x] = AT(0);
   __syncthreads();
-  const int col = blockIdx.x * 256 + threadIdx.x;
-  if (col >= k) return;
-  const T *Fc = Ff + (int64_t)col * f + k;
-  AT acc = AT(0);
-  int t = 0;
-  for (; t + 16 <= w; t += 16) {
-    T q[16];
+  // columns c < k of this CTA (256 of them): each warp takes 4 columns at a
+  // time with its lanes along t (coalesced), partial sums joined by shuffles
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cend = min((int)blockIdx.x * 256 + 256, k);
+  for (int c0 = blockIdx.x * 256 + warp * 4; c0 < cend; c0 += 32) {
+    T q[4][4];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) q[u] = Fc[t + u];
+    for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc += (AT)q[u] * x[t + u];
+      for (int m = 0; m < 4; ++m) {
+        const int col = c0 + cc, t = lane + 32 * m;
+        q[cc][m] = (col < cend && t < w) ? Ff[(int64_t)col * f + k + t] : T(0);
+      }
+    AT part[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      part[cc] = AT(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) part[cc] += (AT)q[cc][m] * x[lane + 32 * m];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part[cc] += __shfl_xor_sync(0xffffffffu, part[cc], o);
+    }
+    if (lane < 4 && c0 + lane < cend) {
+      const AT pv = lane == 0 ? part[0] : lane == 1 ? part[1] : lane == 2 ? part[2] : part[3];
+      yz[po + c0 + lane] -= (double)pv;
+    }
   }
-  for (; t < w; ++t) acc += (AT)Fc[t] * x[t];
-  yz[po + col] -= (double)acc;
 }
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
@@ -1203,7 +1205,7 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
       int na = n_active(li, k);
       int max_rows = 0;
       for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - k - std::min(SB, li.ns[q] - k));
-      dim3 g(std::max(1, (max_rows + 511) / 512), na);
+      dim3 g(std::max(1, (max_rows + 255) / 256), na);
       k_fwd_block<T><<<g, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
       c.count();
     }

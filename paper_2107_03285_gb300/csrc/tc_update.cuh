@@ -273,19 +273,34 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + cb), v);
         if (r < rows) {
-          float cv[32];
-          float *cp[32];
+          const int64_t gjc = gj0 + cb;
+          if (gjc + 31 < job.ns || gjc >= job.ns) {
+            // the 32 columns lie in one region: one base pointer, one stride
+            const bool in_l = gjc < job.ns;
+            float *__restrict__ base = in_l ? job.L + gi + gjc * job.f : job.CB + (gi - job.ns) + (gjc - job.ns) * fcb;
+            const int64_t stride = in_l ? job.f : fcb;
+            float cv[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int cc = cb + j;
-            const int64_t gj = gj0 + cc;
-            cp[j] = gj < job.ns ? job.L + gi + gj * job.f : job.CB + (gi - job.ns) + (gj - job.ns) * fcb;
-            cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(cp[j]) : 0.f;
-          }
+            for (int j = 0; j < 32; ++j) {
+              const int cc = cb + j;
+              cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(base + j * stride) : 0.f;
+            }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int cc = cb + j;
-            if (cc < cols && r + roff >= cc) __stcg(cp[j], cv[j] - __uint_as_float(v[j]));
+            for (int j = 0; j < 32; ++j) {
+              const int cc = cb + j;
+              if (cc < cols && r + roff >= cc) __stcg(base + j * stride, cv[j] - __uint_as_float(v[j]));
+            }
+          } else {
+            // the chunk straddles the last factor column ns (one chunk per tile row)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int cc = cb + j;
+              const int64_t gj = gjc + j;
+              if (cc < cols && r + roff >= cc) {
+                float *p = gj < job.ns ? job.L + gi + gj * job.f : job.CB + (gi - job.ns) + (gj - job.ns) * fcb;
+                __stcg(p, __ldcg(p) - __uint_as_float(v[j]));
+              }
+            }
           }
         }
       }

@@ -236,6 +236,37 @@ def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, si
                          "p_sigma": p_sigma, "origins": origins})
 
 
+def select_instances(batch: Problem, idx) -> Problem:
+    """The sub-batch of problem_batch2d's instances idx (in that order), with
+    their own node / element numbering, loads, targets and parameters."""
+    no, eo = batch.meta["node_offsets"], batch.meta["elem_offsets"]
+    idx = [int(i) for i in idx]
+    node_map = -np.ones(batch.n_nodes, dtype=np.int64)
+    nodes, elems, node_off, elem_off = [], [], [0], [0]
+    for i in idx:
+        nn = np.arange(no[i], no[i + 1])
+        node_map[nn] = node_off[-1] + np.arange(nn.size)
+        nodes.append(nn)
+        elems.append(np.arange(eo[i], eo[i + 1]))
+        node_off.append(node_off[-1] + nn.size)
+        elem_off.append(elem_off[-1] + eo[i + 1] - eo[i])
+    nodes = np.concatenate(nodes)
+    elems = np.concatenate(elems)
+    tr = batch.track_dof.reshape(-1)
+    keep = np.isin(tr // 2, nodes)
+    track = node_map[tr[keep] // 2] * 2 + tr[keep] % 2
+    order = np.argsort(track, kind="stable")
+    target = batch.target.reshape(-1)[keep]
+    weight = batch.weight.reshape(-1)[keep]
+    meta = dict(batch.meta)
+    meta.update({"sides": np.asarray(batch.meta["sides"])[idx], "node_offsets": np.array(node_off),
+                 "elem_offsets": np.array(elem_off), "origins": np.asarray(batch.meta["origins"])[idx],
+                 "instances": np.array(idx)})
+    return Problem(f"{batch.name}_sel{len(idx)}", 2, batch.X[nodes], node_map[batch.conn[elems]].astype(np.int32),
+                   batch.fixed_node[nodes], batch.fext[nodes], track[order].astype(np.int64), target[order],
+                   weight[order], batch.alpha, batch.E0, batch.nu, batch.p0[elems], meta=meta)
+
+
 def problem_rbf3d(n: int = 40, n_rbf: int = 64, width: float = 0.15, seed: int = 0,
                   theta_sigma: float = 0.3, load_scale: float | None = None) -> Problem:
     """The 3D cube of problem_3d whose per-tet log-modulus field is given by

@@ -149,3 +149,26 @@ def test_autotuned_setup_keeps_parity(P, tmp_path):
     for i, ref in enumerate(refs):
         assert np.linalg.norm(dp[eo[i]:eo[i + 1]] - ref) / np.linalg.norm(ref) < 1e-8, i
     s.close()
+
+
+def test_sharded_sub_batches_match_oracle(P):
+    """Each rank's share of a batch (cost-balanced partition) is itself a
+    batch whose step equals the oracle instance by instance."""
+    from paper_2107_03285_gb300 import shard
+    from sgn_inputs import select_instances
+    batch = problem_batch2d(12, seed=7, side_lo=5, side_hi=24)
+    subs = _instances(batch)
+    x, refs = _batch_state(batch, subs)
+    parts = shard.partition(shard.instance_costs(batch.meta["sides"]), 2)
+    no = batch.meta["node_offsets"]
+    for part in parts:
+        sb = select_instances(batch, part)
+        xs = np.concatenate([x[no[i]:no[i + 1]] for i in part])
+        s = P.SGN.from_problem(sb, stores=P.STORE_MIXED)
+        _, dp, _, _, _ = s.step(xs, sb.p0, P.MIXED)
+        dp = dp.cpu().numpy()
+        seo = sb.meta["elem_offsets"]
+        for k, i in enumerate(part):
+            ref = refs[i]
+            assert np.linalg.norm(dp[seo[k]:seo[k + 1]] - ref) / np.linalg.norm(ref) < 1e-8, i
+        s.close()
