@@ -321,18 +321,16 @@ __device__ __forceinline__ CT bk_unit_lower(const CT (*a)[MAXNB + 1], int i, int
 }
 
 // Pivot panel [k, k + w), diagonal block (one CTA per active front):
-//   left-looking update by the earlier panels of the outer block,
-//   A_bb -= W[k:k+w, K0:k] L[k:k+w, K0:k]^T (all threads), then Bunch-Kaufman
-//   by warp 0 (warp-level barriers only).  L11 (D on its diagonal) is staged,
-//   D and the permutation go to the pivot arrays; the front's diagonal block
-//   itself is rewritten by the end-of-block kernel.
+// Bunch-Kaufman of the block, which already holds every update (the
+// trailing updates of earlier outer blocks and, through k_panel_rows, those
+// of the earlier panels of this block).  L11 (D on its diagonal) is staged,
+// D and the permutation go to the pivot arrays; the front's diagonal block
+// itself is rewritten by the end-of-block kernel.
 template <typename T>
 __global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int K0, int nb, double eps_rel, unsigned long long *counters) {
+                                                     int nb, double eps_rel, unsigned long long *counters) {
   using CT = T;
-  constexpr int KC = sizeof(T) == 8 ? 8 : 32;  // keeps static shared memory under 48 KB
   __shared__ CT a[MAXNB][MAXNB + 1];
-  __shared__ CT Lp[KC][MAXNB], Wd[KC][MAXNB];
   __shared__ double sD0[MAXNB], sD1[MAXNB];
   __shared__ int sperm[MAXNB], stype[MAXNB];
   const int s = fronts[blockIdx.x];
@@ -342,8 +340,6 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32
   const int f = front_order(d, s, dpn);
   const int w = min(nb, ns - k);
   const T *F = (const T *)sv.F + sv.front_off[s];
-  const T *W = (const T *)sv.W + sv.w_off[s];
-  const int64_t ldw = f - K0;
   const int tid = threadIdx.x;
   for (int base = tid; base < w * w; base += 8 * blockDim.x) {
     CT v[8];
@@ -357,24 +353,6 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32
     for (int u = 0; u < 8; ++u) {
       const int idx = base + u * blockDim.x;
       if (idx < w * w) a[idx / w][idx % w] = v[u];
-    }
-  }
-  const int kp_in = k - K0;
-  for (int cu = 0; cu < kp_in; cu += KC) {
-    const int kc = min(KC, kp_in - cu);
-    __syncthreads();
-    for (int idx = tid; idx < kc * w; idx += blockDim.x) {
-      const int u = idx / w, t = idx - u * w;
-      Lp[u][t] = (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f];
-      Wd[u][t] = (CT)W[(int64_t)(k - K0 + t) + (int64_t)(cu + u) * ldw];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < w * w; idx += blockDim.x) {
-      const int jj = idx / w, ii = idx - jj * w;
-      if (ii < jj) continue;
-      CT acc = CT(0);
-      for (int u = 0; u < kc; ++u) acc += Wd[u][ii] * Lp[u][jj];
-      a[jj][ii] -= acc;
     }
   }
   __syncthreads();
@@ -413,7 +391,9 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
 //   permutation and forward substitution with L11 in registers (x = F21 P^T
 //   L11^{-T} = L21 D); L21 = x D^{-1}.  Writes L21 to the front, x to the outer
 //   block's W and (FP32 fronts with tensor cores) both as K-major hi / lo
-//   operand copies.
+//   operand copies.  The CTAs whose rows belong to the later panels of the
+//   same outer block also apply this panel's contribution to those panels'
+//   diagonal blocks (right-looking), so that k_panel_diag finds them ready.
 template <typename T, int NBT>
 __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
                                                      int K0, int nb) {
@@ -423,7 +403,7 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
   CT *Lp = reinterpret_cast<CT *>(rows_raw);  // [KC][NBT]: L(k + t, K0 + cu + u)
   CT *L11T = Lp + KC * NBT;                   // [NBT][NBT]: L11T[c][t] = L(t, c) for t > c, else 0
   CT *xs = L11T + NBT * NBT;                  // [NBT][XS]: this CTA's rows, column t
-  __shared__ CT sD0[NBT], sD1[NBT];
+  __shared__ CT sD0[NBT], sD1[NBT], sI0[NBT], sI1[NBT];
   __shared__ int sperm[NBT], stype[NBT];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
@@ -443,27 +423,50 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
   const int64_t i = r0 + il;
   const int kp_in = k - K0;
   const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
-  for (int idx = tid; idx < NBT * NBT; idx += blockDim.x) {
-    const int c = idx / NBT, t = idx - c * NBT;
-    L11T[idx] = (c < t && t < w) ? (CT)stage[(int64_t)t * nb + c] : CT(0);
-  }
-  const int64_t po = sv.piv_off[s] + k;
-  if (tid < NBT) {
-    const bool in = tid < w;
-    sD0[tid] = in ? (CT)sv.D0[po + tid] : CT(1);
-    sD1[tid] = in ? (CT)sv.D1[po + tid] : CT(0);
-    sperm[tid] = in ? sv.piv_perm[po + tid] : tid;
-    stype[tid] = in ? sv.piv_type[po + tid] : 0;
-  }
-  if (row_ok) {
-    for (int t0 = 0; t0 < w; t0 += 8) {
-      CT v[8];
+  // every operand in one round trip: the row's panel entries, L11, pivots
+  {
+    CT v[NBT];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (t0 + u < w) ? (CT)F[i + (int64_t)(k + t0 + u) * f] : CT(0);
+    for (int t = 0; t < NBT; ++t) v[t] = (row_ok && t < w) ? (CT)F[i + (int64_t)(k + t) * f] : CT(0);
+    constexpr int PER = (NBT * NBT + 127) / 128;
+    CT lt[PER];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (t0 + u < w) xs[(t0 + u) * XS + tid] = v[u];
+    for (int q = 0; q < PER; ++q) {
+      const int idx = tid + q * 128;
+      const int c = idx / NBT, t = idx - c * NBT;
+      lt[q] = (idx < NBT * NBT && c < t && t < w) ? (CT)stage[(int64_t)t * nb + c] : CT(0);
     }
+    const int64_t po = sv.piv_off[s] + k;
+    if (tid < NBT) {
+      const bool in = tid < w;
+      sD0[tid] = in ? (CT)sv.D0[po + tid] : CT(1);
+      sD1[tid] = in ? (CT)sv.D1[po + tid] : CT(0);
+      sperm[tid] = in ? sv.piv_perm[po + tid] : tid;
+      stype[tid] = in ? sv.piv_type[po + tid] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (tid + q * 128 < NBT * NBT) L11T[tid + q * 128] = lt[q];
+#pragma unroll
+    for (int t = 0; t < NBT; ++t) xs[t * XS + tid] = v[t];
+  }
+  __syncthreads();
+  // D^{-1} per pivot: 1 / d for 1x1, the inverse of the 2x2 block for pairs
+  // (entry (0,0) in sI0 of the first, (1,1) in sI0 of the second, (0,1) in sI1)
+  if (tid < NBT) {
+    const int t = tid;
+    CT i0 = CT(1), i1 = CT(0);
+    if (stype[t] == 0) {
+      i0 = CT(1) / sD0[t];
+    } else {
+      const int a = stype[t] == 1 ? t : t - 1;
+      const CT d11 = sD0[a], d21 = sD1[a], d22 = sD0[a + 1];
+      const CT det = d11 * d22 - d21 * d21;
+      i0 = (stype[t] == 1 ? d22 : d11) / det;
+      i1 = -d21 / det;
+    }
+    sI0[t] = i0;
+    sI1[t] = i1;
   }
   // left-looking update
   CT wr[KC];
@@ -524,54 +527,83 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
       W[(i - K0) + (int64_t)(k - K0 + t) * ldw] = T(x[t]);
       CT l;
       if (stype[t] == 0) {
-        l = x[t] / sD0[t];
+        l = x[t] * sI0[t];
       } else if (stype[t] == 1) {  // first of a 2x2 pair (t + 1 < w)
         const int tn = t + 1 < NBT ? t + 1 : t;
-        l = (x[t] * sD0[tn] - x[tn] * sD1[t]) / (sD0[t] * sD0[tn] - sD1[t] * sD1[t]);
+        l = x[t] * sI0[t] + x[tn] * sI1[t];
       } else {
         const int tp = t > 0 ? t - 1 : 0;
-        l = (x[t] * sD0[tp] - x[tp] * sD1[tp]) / (sD0[tp] * sD0[t] - sD1[tp] * sD1[tp]);
+        l = x[tp] * sI1[t] + x[t] * sI0[t];
       }
       F[i + (int64_t)(k + t) * f] = T(l);
+      xs[t * XS + tid] = l;  // own column of xs: no other thread reads it before the barrier
+    }
+  }
+  __syncthreads();
+  {
+    // later panels of this outer block: A(i, j) -= sum_t W(i, t) L(j, t) for
+    // rows i >= j of one panel; both rows belong to this CTA (panels are
+    // w-aligned from r0 and w divides the CTA's 128 rows)
+    const int kend_blk = min(K0 + FACTOR_BLOCK, ns);
+    const int rowbase = r0 + blockIdx.x * RB;
+    if (row_ok && i < kend_blk) {
+      const int pa = r0 + ((int)(i - r0) / w) * w;
+      const int pl = pa - rowbase;  // first local row of the panel
+      const int ni = (int)i - pa;   // columns pa .. i: ni + 1 of them
+      // all of this row's entries of the block loaded at once, then updated
+      CT cur[NBT];
+#pragma unroll
+      for (int q = 0; q < NBT; ++q) cur[q] = q <= ni ? (CT)F[i + (int64_t)(pa + q) * f] : CT(0);
+#pragma unroll
+      for (int t = 0; t < NBT; ++t) {
+        if (t >= w) break;
+        const CT xt = x[t];
+#pragma unroll
+        for (int q = 0; q < NBT; ++q) cur[q] -= xt * xs[t * XS + min(pl + q, RB - 1)];
+      }
+#pragma unroll
+      for (int q = 0; q < NBT; ++q)
+        if (q <= ni) F[i + (int64_t)(pa + q) * f] = T(cur[q]);
     }
   }
   if (sv.wk0) {
-    // K-major hi / lo copies, written warp-cooperatively (lanes along t)
+    // K-major hi / lo copies, written warp-cooperatively (lanes along t):
+    // first L (already in xs), then W
     const int warp = tid >> 5, lane = tid & 31;
     const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
     for (int pass = 0; pass < 2; ++pass) {
-      __syncthreads();
-      if (row_ok) {
+      if (pass == 1) {
+        __syncthreads();
+        if (row_ok) {
 #pragma unroll
-        for (int t = 0; t < NBT; ++t) {
-          if (t >= w) break;
-          CT v = x[t];
-          if (pass == 1) {
-            if (stype[t] == 0) {
-              v = x[t] / sD0[t];
-            } else if (stype[t] == 1) {
-              const int tn = t + 1 < NBT ? t + 1 : t;
-              v = (x[t] * sD0[tn] - x[tn] * sD1[t]) / (sD0[t] * sD0[tn] - sD1[t] * sD1[t]);
-            } else {
-              const int tp = t > 0 ? t - 1 : 0;
-              v = (x[t] * sD0[tp] - x[tp] * sD1[tp]) / (sD0[tp] * sD0[t] - sD1[tp] * sD1[tp]);
-            }
+          for (int t = 0; t < NBT; ++t) {
+            if (t >= w) break;
+            xs[t * XS + tid] = x[t];
           }
-          xs[t * XS + tid] = v;
         }
+        __syncthreads();
       }
-      __syncthreads();
-      float *hi = pass == 0 ? sv.wk0 : sv.wk2, *lo = pass == 0 ? sv.wk1 : sv.wk3;
-      for (int rr = 0; rr < 32; ++rr) {
-        const int rloc = warp * 32 + rr;
+      float *hi = pass == 1 ? sv.wk0 : sv.wk2, *lo = pass == 1 ? sv.wk1 : sv.wk3;
+      // rows are FACTOR_BLOCK floats apart and k - K0, wpad are multiples of 4:
+      // every lane stores 4 consecutive entries as one 16-byte vector
+      const int q4 = wpad / 4;                 // vectors per row
+      const int rows_per_it = 32 / q4 > 0 ? 32 / q4 : 1;
+      const int sub = lane / q4, t4 = (lane % q4) * 4;
+      for (int rr = 0; rr < 32; rr += rows_per_it) {
+        const int rloc = warp * 32 + rr + sub;
         const int ilr = blockIdx.x * RB + rloc;
-        if (ilr >= nrows) break;
+        if (sub >= rows_per_it || rr + sub >= 32 || ilr >= nrows) continue;
         const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
-        for (int t = lane; t < wpad; t += 32) {
-          const float v = t < w ? (float)xs[t * XS + rloc] : 0.f;
-          const float h = tc::tf32_hi(v);
-          hi[base + t] = h;
-          lo[base + t] = v - h;
+        for (int t = t4; t < wpad; t += 4 * q4) {
+          float v[4], h[4], l[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            v[q] = t + q < w ? (float)xs[(t + q) * XS + rloc] : 0.f;
+            h[q] = tc::tf32_hi(v[q]);
+            l[q] = v[q] - h[q];
+          }
+          *reinterpret_cast<float4 *>(hi + base + t) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4 *>(lo + base + t) = make_float4(l[0], l[1], l[2], l[3]);
         }
       }
     }
@@ -1126,7 +1158,7 @@ void factor_impl(Ctx &c, Store &st) {
         }
         {
           ProfScope ps(c, SGN_PROF_PIVOT);
-          k_panel_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, K0, nb, eps_rel, ctr);
+          k_panel_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
           c.count();
         }
         if (max_rows > 0) {
