@@ -198,6 +198,10 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
     for (int i = jj + lane; i < w; i += 32) bm = max(bm, (CT)fabs(a[jj][i]));
   for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(FULL, bm, o));
   const double thresh = eps_rel * fmax((double)bm, 1e-300);
+  // the largest CT not above thresh: |x| > thresh  <=>  |x| > thresh_c for
+  // every CT value x, so the static-pivot test needs no FP64 arithmetic
+  CT thresh_c = (CT)thresh;
+  if ((double)thresh_c > thresh) thresh_c = nextafter(thresh_c, CT(0));
   __syncthreads();
   int j = 0;
   while (j < w) {
@@ -213,27 +217,36 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
       const int oi = __shfl_xor_sync(FULL, ci, o);
       if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
     }
-    const double colmax = fmax((double)cm, 0.0);
     const int imax = ci;
-    const double absakk = fabs((double)a[j][j]);
+    // the FP64 tests run in lane 0 only (FP64 issue is scarce); the
+    // decision reaches the other lanes by shuffles
+    const CT akk = a[j][j];
+    int code = 0;  // 0: 1x1 at j, 1: needs the row of imax
+    if (lane == 0) {
+      const double colmax = fmax((double)cm, 0.0), absakk = fabs((double)akk);
+      code = (!(fmax(absakk, colmax) > thresh) || absakk >= alpha * colmax) ? 0 : 1;
+    }
+    code = __shfl_sync(FULL, code, 0);
     int kstep = 1, kp = j;
-    bool read_row = false;
-    if (!(fmax(absakk, colmax) > thresh)) {
-      kstep = 1; kp = j;  // (near-)zero column: static pivot below
-    } else if (absakk >= alpha * colmax) {
-      kstep = 1; kp = j;
-    } else {
-      read_row = true;
+    const bool read_row = code == 1;
+    if (read_row) {
       CT rm = CT(0);
       for (int t = j + lane; t < w; t += 32) {
         if (t == imax) continue;
         rm = max(rm, (CT)(t < imax ? fabs(a[t][imax]) : fabs(a[imax][t])));
       }
       for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL, rm, o));
-      const double rowmax = (double)rm;
-      if (absakk >= alpha * colmax * (colmax / rowmax)) { kstep = 1; kp = j; }
-      else if (fabs((double)a[imax][imax]) >= alpha * rowmax) { kstep = 1; kp = imax; }
-      else { kstep = 2; kp = imax; }
+      const CT aii = a[imax][imax];
+      int dec = 0;  // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
+      if (lane == 0) {
+        const double colmax = fmax((double)cm, 0.0), absakk = fabs((double)akk), rowmax = (double)rm;
+        if (absakk >= alpha * colmax * (colmax / rowmax)) dec = 0;
+        else if (fabs((double)aii) >= alpha * rowmax) dec = 1;
+        else dec = 2;
+      }
+      dec = __shfl_sync(FULL, dec, 0);
+      if (dec == 1) { kstep = 1; kp = imax; }
+      else if (dec == 2) { kstep = 2; kp = imax; }
     }
     const int kk = j + kstep - 1;
     // the search read entries the update (or the swap) writes: wait for all warps
@@ -260,14 +273,14 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
       __syncthreads();
     }
     if (kstep == 1) {
-      double dj = (double)a[j][j];
-      const bool perturb = !(fabs(dj) > thresh);
-      if (perturb) dj = (dj >= 0.0) ? thresh : -thresh;
+      CT dj = a[j][j];
+      const bool perturb = !(fabs(dj) > thresh_c);
+      if (perturb) dj = (dj >= CT(0)) ? (CT)thresh : (CT)-thresh;
       if (tid == 0) {
-        sD0[j] = (double)(CT)dj; stype[j] = 0;
+        sD0[j] = (double)dj; stype[j] = 0;
         if (perturb && count) atomicAdd(counters + 0, 1ull);
       }
-      const CT rd = CT(1) / (CT)dj;
+      const CT rd = CT(1) / dj;
       const int i0 = j + 1 + lane, i1 = i0 + 32;
       const CT l0 = i0 < w ? a[j][i0] : CT(0), l1 = i1 < w ? a[j][i1] : CT(0);
       for (int cc = j + 1 + warp; cc < w; cc += NW) {
