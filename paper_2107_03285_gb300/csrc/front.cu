@@ -83,24 +83,31 @@ __device__ __forceinline__ FrontMat<T> front_mat(const DevSym &d, const SV &sv, 
 }
 
 // ---------------------------------------------------------------- assembly
-template <typename T, int D>
+// One CTA per (front, node column group P): zero the group's DPN columns,
+// add the original entries of K (and, for the saddle-point store, A and -G)
+// and extend-add the children's contribution blocks.  Column k of the group
+// lives in one region (factor columns or contribution block), so it is
+// addressed as region[off0_k + row] without a per-element test.
+template <typename T, int D, int DPN>
 __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t item_base,
                                                         const double *__restrict__ Kv,
                                                         const double *__restrict__ Gv,
                                                         const double *__restrict__ wA) {
   const int64_t item = item_base + blockIdx.x;
   const int s = d.item_sn[item], P = d.item_P[item];
-  const int dpn = sv.dpn;
   const int nown = d.sn_nown[s];
-  const int f = (nown + d.sn_nstruct[s]) * dpn;
+  const int f = (nown + d.sn_nstruct[s]) * DPN;
   const FrontMat<T> F = front_mat<T>(d, sv, s);
-  const int col0 = P * dpn;
-  const int64_t len = f - col0;
-  for (int64_t idx = threadIdx.x; idx < len * dpn; idx += blockDim.x) {
-    int k = (int)(idx / len);
-    int64_t i = col0 + idx % len;
-    *F.at(i, col0 + k) = T(0);
-  }
+  const int col0 = P * DPN;
+  const bool in_cb = col0 >= F.ns;
+  T *const R = in_cb ? F.C : F.L;
+  int64_t off0[DPN];
+#pragma unroll
+  for (int k = 0; k < DPN; ++k)
+    off0[k] = in_cb ? (int64_t)(col0 + k - F.ns) * (F.f - F.ns) - F.ns : (int64_t)(col0 + k) * F.f;
+#pragma unroll
+  for (int k = 0; k < DPN; ++k)
+    for (int i = col0 + threadIdx.x; i < f; i += blockDim.x) R[off0[k] + i] = T(0);
   __syncthreads();
   if (P < nown) {
     const int r = d.sn_first[s] + P;
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
       if (Q < 0) continue;
       double kv = Kv[(int64_t)kk * D * D + b * D + a];  // K[(c,a),(r,b)]
       if (sv.kkt) {
-        int rx = Q * dpn + 2 * a, cx = P * dpn + 2 * b;
+        int rx = Q * DPN + 2 * a, cx = P * DPN + 2 * b;
         double gv = Gv[(int64_t)kk * D * D + b * D + a];
         if (rx >= cx + 1) *F.at(rx, cx + 1) += T(kv);        // (x row, lambda col)
         if (rx + 1 >= cx) *F.at(rx + 1, cx) += T(kv);        // (lambda row, x col)
@@ -132,37 +139,35 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
     const int q = d.cmap[d.cmap_off[coff + j] + P];
     if (q >= 0) {
       const int nstc = d.sn_nstruct[c];
-      const int fcb = nstc * dpn;  // the child's contribution block is fcb x fcb
+      const int fcb = nstc * DPN;  // the child's contribution block is fcb x fcb
       const T *Cc = (const T *)sv.CB + sv.cb_off[c];
       const int32_t *relc = d.relpos + d.sn_struct_off[c];
-      const int nq = nstc - q;
-      const int64_t rows = (int64_t)nq * dpn;
-      const int64_t n = rows * dpn;
-      for (int64_t base = threadIdx.x; base < n; base += 4 * (int64_t)blockDim.x) {
-        T v[4], o[4];
-        T *dst[4];
+      const int rows = (nstc - q) * DPN;  // child rows q*DPN .. fcb-1 of its column q*DPN + k
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t idx = base + (int64_t)u * blockDim.x;
-          dst[u] = nullptr;
-          v[u] = T(0);
-          if (idx < n) {
-            const int k = (int)(idx / rows);
-            const int64_t rem = idx - (int64_t)k * rows;
-            const int qq = q + (int)(rem / dpn), kp = (int)(rem % dpn);
-            // (ic, jc): position in the child's contribution block
-            const int64_t ic = (int64_t)qq * dpn + kp, jc = (int64_t)q * dpn + k;
-            if (ic >= jc) {
-              dst[u] = F.at((int64_t)relc[qq] * dpn + kp, col0 + k);
-              v[u] = Cc[ic + jc * fcb];
+      for (int k = 0; k < DPN; ++k) {
+        const int64_t jc = (int64_t)q * DPN + k;
+        const T *ccol = Cc + jc * fcb;
+        for (int rr0 = threadIdx.x + k; rr0 < rows; rr0 += 4 * blockDim.x) {
+          // rows rr >= k (lower triangle of the child's block: ic >= jc)
+          T v[4], o[4];
+          int64_t dst[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int rr = rr0 + u * blockDim.x;
+            dst[u] = -1;
+            v[u] = T(0);
+            if (rr < rows) {
+              const int qq = q + rr / DPN, kp = rr % DPN;
+              dst[u] = off0[k] + (int64_t)relc[qq] * DPN + kp;
+              v[u] = ccol[(int64_t)q * DPN + rr];
             }
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) o[u] = dst[u] >= 0 ? R[dst[u]] : T(0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (dst[u] >= 0) R[dst[u]] = o[u] + v[u];
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) o[u] = dst[u] ? *dst[u] : T(0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (dst[u]) *dst[u] = o[u] + v[u];
       }
     }
     __syncthreads();
@@ -976,51 +981,55 @@ __global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts
   }
 }
 
-// v_own = z_own - L21^T x_struct: a CTA owns 32 own columns; its 8 warps
-// split the struct rows, each lane reads 4 consecutive rows of 4 columns
+// v_own = z_own - L21^T x_struct: a CTA owns 64 own columns, 8 per warp.
+// The solution at the front's struct rows is gathered into shared memory in
+// chunks; each warp reads its columns with the lanes along the rows
+// (coalesced) and joins the lanes' partial sums by shuffles.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                    const double *__restrict__ sol, double *__restrict__ yz) {
   using AT = T;
-  __shared__ AT part[8][32];
+  constexpr int CB = 64, CPW = 8, CHUNK = 4096;
+  __shared__ AT xsh[CHUNK];
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int nown = d.sn_nown[s];
   const int ns = nown * dpn;
-  const int t0 = blockIdx.x * 32;
+  const int t0 = blockIdx.x * CB;
   if (t0 >= ns) return;
   const int f = front_order(d, s, dpn);
+  const int nst = f - ns;
+  if (nst == 0) return;
   const T *F = (const T *)sv.F + sv.front_off[s];
   const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncol = min(32, ns - t0);
-  // each warp handles columns t0 + [0, 32) over rows ns + warp + 8 j
-  AT acc = AT(0);
-  const int col = t0 + lane;
-  if (lane < ncol) {
-    const T *Fc = F + (int64_t)col * f;
-    int i = ns + warp;
-    for (; i + 24 < f; i += 32) {
-      T v[4];
-      double xv[4];
+  const int cw = t0 + warp * CPW;  // this warp's first column
+  AT acc[CPW];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int ii = i + 8 * u;
-        v[u] = Fc[ii];
-        xv[u] = sol[(int64_t)sr[ii / dpn - nown] * dpn + ii % dpn];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc += (AT)v[u] * (AT)xv[u];
+  for (int c = 0; c < CPW; ++c) acc[c] = AT(0);
+  for (int r0 = 0; r0 < nst; r0 += CHUNK) {
+    const int nr = min(CHUNK, nst - r0);
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      const int ii = ns + r0 + r;
+      xsh[r] = (AT)sol[(int64_t)sr[ii / dpn - nown] * dpn + ii % dpn];
     }
-    for (; i < f; i += 8) acc += (AT)Fc[i] * (AT)sol[(int64_t)sr[i / dpn - nown] * dpn + i % dpn];
-  }
-  part[warp][lane] = acc;
-  __syncthreads();
-  if (warp == 0 && lane < ncol) {
-    AT tot = AT(0);
+    __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 8; ++u) tot += part[u][lane];
-    yz[sv.piv_off[s] + col] -= (double)tot;
+    for (int c = 0; c < CPW; ++c) {
+      if (cw + c >= ns) break;
+      const T *Fc = F + (int64_t)(cw + c) * f + ns + r0;
+      AT a = AT(0);
+#pragma unroll 8
+      for (int r = lane; r < nr; r += 32) a += (AT)Fc[r] * xsh[r];
+      acc[c] += a;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0 && cw + c < ns) yz[sv.piv_off[s] + cw + c] -= (double)acc[c];
   }
 }
 
@@ -1149,10 +1158,11 @@ void factor_impl(Ctx &c, Store &st) {
     int64_t nitems = li.i1 - li.i0;
     {
       ProfScope ps(c, SGN_PROF_FRONT_ASSEMBLY);
-      if (D == 2)
-        k_front_assemble<T, 2><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-      else
-        k_front_assemble<T, 3><<<(unsigned)nitems, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      const dim3 ga((unsigned)nitems);
+      if (D == 2 && st.dpn == 4) k_front_assemble<T, 2, 4><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      else if (D == 2) k_front_assemble<T, 2, 2><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      else if (st.dpn == 6) k_front_assemble<T, 3, 6><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      else k_front_assemble<T, 3, 3><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
       c.count();
     }
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
@@ -1264,7 +1274,7 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
     int nf = (int)(li.f1 - li.f0);
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     if (max_ns == 0) continue;
-    dim3 gi((max_ns + 31) / 32, nf);
+    dim3 gi((max_ns + 63) / 64, nf);
     k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x, st.yz);
     c.count();
     int last = ((max_ns - 1) / SB) * SB;
