@@ -210,7 +210,9 @@ sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *report);
 /* sgn_solve: (dx, dp, dl) of Eq. sparseSystemGN by forward, diagonal and
  * backward substitution with the factor, followed by FP64 iterative
  * refinement against the assembled matrix.  g_d = df/dp for SGN_RHS_PAPER
- * (ignored otherwise).  Any of dx_d / dl_d may be NULL. */
+ * (ignored otherwise).  Any of dx_d / dl_d may be NULL.  Each level's
+ * substitution is one launch whose CTAs wait, bounded, for the blocks they
+ * depend on: ETIMEOUT if such a wait expired (the result is then invalid). */
 sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d,
                      double *dp_d, double *dl_d, const sgn_solve_opts *opts,
                      sgn_solve_report *report);

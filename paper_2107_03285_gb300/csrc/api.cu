@@ -136,14 +136,19 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   s.dpn = dpn;
   const int n_sn = (int)c.S.sn.size();
   s.h_front_off.assign(n_sn, 0); s.h_w_off.assign(n_sn, 0);
-  s.h_rhs_off.assign(n_sn, 0); s.h_piv_off.assign(n_sn, 0);
-  int64_t fo = 0, ro = 0, po = 0;
+  s.h_rhs_off.assign(n_sn, 0); s.h_piv_off.assign(n_sn, 0); s.h_xinv_off.assign(n_sn, 0);
+  int64_t fo = 0, ro = 0, po = 0, xo = 0;
+  constexpr int64_t SBK = 128;  // solve block width
   for (int i = 0; i < n_sn; ++i) {
     int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
     s.h_front_off[i] = fo; fo += ((f * ns + 63) / 64) * 64;
     s.h_rhs_off[i] = ro; ro += f;
     s.h_piv_off[i] = po; po += ns;
+    // full blocks of SBK^2, the last one (w < SBK) of w^2, 16-byte aligned
+    const int64_t nfull = ns / SBK, wl = ns - nfull * SBK;
+    s.h_xinv_off[i] = xo; xo += nfull * SBK * SBK + ((wl * wl + 3) / 4) * 4;
   }
+  s.xinv_elems = xo;
   // W (= L21 D of the current outer block) is only live while its level is
   // factored, so all levels share one workspace sized for the largest level
   int64_t wmax = 0;
@@ -154,6 +159,30 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
       wo += (int64_t)c.S.sn[i].fnodes() * dpn * FACTOR_BLOCK;
     }
     wmax = std::max(wmax, wo);
+  }
+  // substitution schedules (one CTA per item): forward items are the
+  // front's 128-row bands, own bands (key b) before its struct bands (key
+  // nbo + j); backward items its 128-column blocks, last first (key nbo - 1 -
+  // b).  Sorting a level's items by key puts every dependency first.
+  s.h_fwd_items.clear(); s.h_bwd_items.clear();
+  s.h_fwd_lvl.assign(1, 0); s.h_bwd_lvl.assign(1, 0);
+  int32_t q = 0;
+  for (const auto &lv : c.S.level_fronts) {
+    const size_t f0 = s.h_fwd_items.size(), b0 = s.h_bwd_items.size();
+    for (int i : lv) {
+      const int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
+      const int32_t nbo = (int32_t)((ns + SBK - 1) / SBK), nbs = (int32_t)((f - ns + SBK - 1) / SBK);
+      if (ns > 0) {
+        for (int32_t k = 0; k < nbo + nbs; ++k) s.h_fwd_items.push_back({q, k});
+        for (int32_t k = 0; k < nbo; ++k) s.h_bwd_items.push_back({q, k});
+      }
+      ++q;
+    }
+    auto by_key = [](const SolveItem &a, const SolveItem &b) { return a.key != b.key ? a.key < b.key : a.q < b.q; };
+    std::sort(s.h_fwd_items.begin() + f0, s.h_fwd_items.end(), by_key);
+    std::sort(s.h_bwd_items.begin() + b0, s.h_bwd_items.end(), by_key);
+    s.h_fwd_lvl.push_back((int64_t)s.h_fwd_items.size());
+    s.h_bwd_lvl.push_back((int64_t)s.h_bwd_items.size());
   }
   s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po;
   s.cb_elems = plan_cb_arena(c.S, dpn, s.h_cb_off, &s.cb_sum);
@@ -246,12 +275,21 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     size_t es = fp32 ? 4 : 8;
     s.F = cv.take<char>((size_t)s.front_elems * es);
     s.CB = cv.take<char>((size_t)s.cb_elems * es);
+    s.Xinv = cv.take<char>((size_t)s.xinv_elems * es);
     s.W = cv.take<char>((size_t)s.w_elems * es);
     s.Ldg = cv.take<char>((size_t)s.piv_elems * c.S.opts.panel * es);
     s.rhs = cv.take<double>(s.rhs_elems);
     s.piv_type = cv.take<int32_t>(s.piv_elems); s.piv_perm = cv.take<int32_t>(s.piv_elems);
     s.D0 = cv.take<double>(s.piv_elems); s.D1 = cv.take<double>(s.piv_elems);
     s.yz = cv.take<double>(s.piv_elems);
+    s.pub = cv.take<unsigned long long>(s.piv_elems);
+    s.pflag = fp32 ? nullptr : cv.take<unsigned>(s.piv_elems);
+    s.ctl = cv.take<unsigned>(16);
+    {
+      SolveItem *it;
+      st_up(it, s.h_fwd_items); s.fwd_items = it;
+      st_up(it, s.h_bwd_items); s.bwd_items = it;
+    }
     if (fp32) {
       for (int q = 0; q < 4; ++q) s.wk[q] = cv.take<float>(s.w_elems);
       s.maps = cv.take<char>(S.sn.size() * sizeof(tc::Maps));
@@ -259,6 +297,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     int64_t *p;
     st_up(p, s.h_front_off); s.front_off = p;
     st_up(p, s.h_cb_off); s.cb_off = p;
+    st_up(p, s.h_xinv_off); s.xinv_off = p;
     st_up(p, s.h_w_off); s.w_off = p;
     st_up(p, s.h_rhs_off); s.rhs_off = p;
     st_up(p, s.h_piv_off); s.piv_off = p;
@@ -437,6 +476,13 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   }
   for (auto &u : ups) CUDA_TRY(h, cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
+  // published solve values start untagged (no solve uses tag 0)
+  for (Store *st : {&h->kkt64, &h->kkt32, &h->kf, &h->kf32}) {
+    if (!st->enabled) continue;
+    CUDA_TRY(h, cudaMemsetAsync(st->pub, 0, (size_t)st->piv_elems * sizeof(unsigned long long), h->stream));
+    if (st->pflag) CUDA_TRY(h, cudaMemsetAsync(st->pflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(st->ctl, 0, 16 * sizeof(unsigned), h->stream));
+  }
   // uploads read host vectors owned by h->S or by the carve's thread-local
   // staging; wait for them before those can change
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -603,6 +649,8 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   if (dl_d) launch_to_nodes_plain(c, c.zl, dl_d);
   CUDA_TRY(h, cudaMemcpyAsync(dp_d, c.zp, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   sgn_status s = launch_check(h);
+  if (s != SGN_OK) return s;
+  s = check_status(h);  // bounded waits of the substitutions
   if (s != SGN_OK) return s;
   if (rep) {
     CUDA_TRY(h, cudaEventRecord(e1, c.stream));

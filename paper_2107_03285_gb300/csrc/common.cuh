@@ -45,6 +45,12 @@ struct DevSym {
   const int32_t *item_sn = nullptr, *item_P = nullptr;  // per-level (front, node column) items
 };
 
+// one band or block of a front in a level's substitution schedule: q indexes
+// the level-ordered front list, key orders the work inside the front
+struct SolveItem {
+  int32_t q, key;
+};
+
 // one multifrontal store: fronts + pivots + solve buffers of one kind
 struct Store {
   bool enabled = false;
@@ -70,9 +76,24 @@ struct Store {
   // arena shared by contribution blocks whose lifetimes (from their own
   // level's assembly to their parent's) do not overlap
   void *CB = nullptr;
+  // inverses of the 128-wide unit-lower diagonal blocks of the factor, each
+  // a dense row-major w x w block (X(j, i) at j * w + i), contiguous per front
+  void *Xinv = nullptr;
+  // dataflow substitutions: one CTA per 128-row band (forward) or 128-column
+  // block (backward) of a front, listed per level in an order where every
+  // band depends only on earlier entries; pub holds each published block
+  // value (FP32 fronts: the value's bits with the solve's 32-bit tag in one
+  // 64-bit word; FP64 fronts: the value, announced by the tag in pflag at the
+  // block's first position); ctl = {solve counter, ticket, finished CTAs}
+  unsigned long long *pub = nullptr;
+  unsigned *pflag = nullptr, *ctl = nullptr;
+  const SolveItem *fwd_items = nullptr, *bwd_items = nullptr;
+  std::vector<SolveItem> h_fwd_items, h_bwd_items;
+  std::vector<int64_t> h_fwd_lvl, h_bwd_lvl;  // per level: range in the item lists
   const int64_t *front_off = nullptr, *cb_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
-  std::vector<int64_t> h_front_off, h_cb_off, h_w_off, h_rhs_off, h_piv_off;
-  int64_t front_elems = 0, cb_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0;
+  const int64_t *xinv_off = nullptr;
+  std::vector<int64_t> h_front_off, h_cb_off, h_w_off, h_rhs_off, h_piv_off, h_xinv_off;
+  int64_t front_elems = 0, cb_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0, xinv_elems = 0;
   int64_t cb_sum = 0;  // sum of all contribution blocks (what the arena saves against)
   bool factored = false;
   // CUDA graphs of the static launch sequences (captured once, replayed)

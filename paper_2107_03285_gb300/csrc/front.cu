@@ -35,13 +35,17 @@ constexpr int MAXNB = 64;
 struct SV {  // store view passed to kernels
   void *F;                       // factor columns of every front (f x ns each)
   void *CB;                      // contribution-block arena
+  void *Xinv;                    // diagonal-block inverses
   void *W;
   void *Ldg;                     // staged factored diagonal blocks (panel x panel per panel)
   float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
   double *rhs;
   int32_t *piv_type, *piv_perm;
   double *D0, *D1;
-  const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off;
+  double *yz;                    // y, z = D^{-1} y, v of the substitutions (pivot order)
+  unsigned long long *pub;       // published block values of the substitutions
+  unsigned *pflag;               // their tags (FP64 fronts)
+  const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off, *xinv_off;
   int dpn;
   int kkt;
 };
@@ -49,6 +53,7 @@ struct SV {  // store view passed to kernels
 SV view(Store &s) {
   SV v;
   v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
+  v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz;
   v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
@@ -833,38 +838,19 @@ __global__ void k_fwd_gather(DevSym d, SV sv, int64_t item_base, int64_t n, cons
   sv.rhs[sv.rhs_off[s] + (int64_t)P * dpn + kd] = v;
 }
 
-// the factor holds L rows in their final pivoted order (later panels also
-// permute the rows of earlier L columns), so the fully-summed right-hand
-// side is permuted once, panel by panel, before the forward substitution
-__global__ void __launch_bounds__(64) k_fwd_permute(DevSym d, SV sv, const int32_t *__restrict__ fronts, int nb) {
-  __shared__ double y[MAXNB];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  const int k = blockIdx.x * nb;
-  if (k >= ns) return;
-  const int w = min(nb, ns - k);
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  const int64_t po = sv.piv_off[s] + k;
-  const int t = threadIdx.x;
-  if (t < w) y[t] = rhs[k + sv.piv_perm[po + t]];
-  __syncthreads();
-  if (t < w) rhs[k + t] = y[t];
-}
-
 constexpr int SB = 128;  // solve block width (independent of the pivot panel width)
 
 // Arithmetic of the substitutions is done in the factor's precision (AT = T):
 // with FP32 fronts every solve is the correction solve of mixed-precision
 // iterative refinement, whose residual and update are formed in FP64 outside.
 
-// Inverse of every SB x SB unit-lower diagonal block of the factor, stored
-// in the block's (otherwise unused) strict upper triangle: front element
-// (k + i, k + j), i < j, holds X(j, i) with X = L_bb^{-1}.  One CTA per block,
-// thread c computes column c of X by forward substitution (no cross-thread
+// Inverse X = L_bb^{-1} of every SB x SB unit-lower diagonal block of the
+// factor, stored as a dense row-major w x w block (unit diagonal, zeros
+// above) in the store's inverse array.  One CTA per block, thread c
+// computes column c of X by forward substitution (no cross-thread
 // dependency).  Run once per level after its factorization, so that every
 // later solve replaces the sequential triangular solve of a block by a
-// triangular matrix-vector product.
+// matrix-vector product read with vector loads.
 template <typename T>
 __global__ void __launch_bounds__(SB) k_diag_inverse(DevSym d, SV sv, const int32_t *__restrict__ fronts) {
   extern __shared__ unsigned char inv_raw[];
@@ -889,96 +875,298 @@ __global__ void __launch_bounds__(SB) k_diag_inverse(DevSym d, SV sv, const int3
     }
   }
   __syncthreads();
-  for (int j = 1; j < w; ++j)
-    if (c < j) F[(int64_t)(k + c) + (int64_t)(k + j) * f] = A[c][j];  // X(j, c)
+  T *X = (T *)sv.Xinv + sv.xinv_off[s] + (int64_t)blockIdx.x * SB * SB;
+  for (int j = 0; j < w; ++j)  // row j, the threads along its columns c
+    if (c < w) X[(int64_t)j * w + c] = c < j ? A[c][j] : (c == j ? T(1) : T(0));
 }
 
-// loads the strict lower part of X = L_bb^{-1} of the block at k as U[j][i] = X(j, i)
+// loads X = L_bb^{-1} of the block at k (block index k / SB) as U[j][i] =
+// X(j, i): the dense row-major block is read as 16-byte vectors, 8 per thread
+// in flight (one round trip for a 128 x 128 FP32 block and 512 threads)
 template <typename T, typename AT>
-__device__ __forceinline__ void load_block_inverse(const T *__restrict__ F, int64_t f, int k, int w,
-                                                   AT (*U)[SB + 1]) {
-  const int n = w * w;
-  for (int base = threadIdx.x; base < n; base += 16 * blockDim.x) {
-    T v[16];
+__device__ __forceinline__ void load_block_inverse(const SV &sv, int s, int k, int w, AT (*U)[SB + 1]) {
+  const T *X = (const T *)sv.Xinv + sv.xinv_off[s] + (int64_t)(k / SB) * SB * SB;
+  constexpr int VE = 16 / sizeof(T);  // elements per vector
+  constexpr int NV = 8;               // vectors in flight per thread
+  const int nv = (w * w + VE - 1) / VE;
+  for (int base = threadIdx.x; base < nv; base += NV * blockDim.x) {
+    T v[NV][VE];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int j = idx / w, i = idx - j * w;
-      v[u] = (idx < n && i < j) ? F[(int64_t)(k + i) + (int64_t)(k + j) * f] : T(0);
+    for (int u = 0; u < NV; ++u) {
+      const int q = base + u * blockDim.x;
+      if (q < nv) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 t = reinterpret_cast<const float4 *>(X)[q];
+          v[u][0] = t.x; v[u][1] = t.y; v[u][2] = t.z; v[u][3] = t.w;
+        } else {
+          const double2 t = reinterpret_cast<const double2 *>(X)[q];
+          v[u][0] = t.x; v[u][1] = t.y;
+        }
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < n) U[idx / w][idx % w] = (AT)v[u];
+    for (int u = 0; u < NV; ++u) {
+      const int q = base + u * blockDim.x;
+      if (q >= nv) continue;
+#pragma unroll
+      for (int e = 0; e < VE; ++e) {
+        const int idx = q * VE + e;
+        if (idx < w * w) U[idx / w][idx % w] = (AT)v[u][e];
+      }
     }
   }
 }
 
-// forward step of block [k, k + w) of every active front: y_b = X r_b (every
-// CTA forms it from the block inverse; CTA 0 stores it), then rows below:
-// r_i -= L_ib y_b, one row per thread (256 per CTA), 32 loads in flight
+// ---------------------------------------------------------------------------
+// Dataflow substitutions.  The forward (backward) substitution of a level is
+// one launch with one CTA per item of the level's schedule: a 128-row band of
+// a front (forward) or a 128-column block (backward).  A CTA takes its item by
+// ticket, so every item it depends on belongs to a CTA that started before
+// it; it streams its part of the factor while waiting, bounded, for the
+// values of the blocks it depends on, and publishes its own block's values
+// for the CTAs after it.  The sequential chain of 128-wide blocks thus costs
+// one publish-and-observe latency per block instead of a kernel launch.
+
+constexpr int SBT = 4 * SB;                          // threads of a substitution CTA
+constexpr long long SOLVE_WAIT_CYCLES = 1ll << 31;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool timed_out(const int *status) {
+  return (*(volatile const int *)status & DEV_TIMEOUT) != 0;
+}
+
+// compensated (Kahan) running sum in the substitution's precision
+template <typename AT>
+__device__ __forceinline__ void kahan_add(AT &sum, AT &comp, AT x) {
+  const AT y = x - comp;
+  const AT t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+template <typename AT>
+struct SolveShared {
+  AT xs[2][SB];       // values of the block being consumed (double-buffered)
+  double dp[4][SB];   // per-quarter partial sums
+  AT ap[4][SB];       // per-quarter partial block products
+  AT rb[SB];          // right-hand side of the own block
+  AT yb[SB];          // the own block's values
+  int item, abort;
+};
+
+// publishes the w values of the block at pivot position p under tag (thread
+// t < w holds value t); every thread calls it
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_fwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                    double *__restrict__ yz) {
-  using AT = T;
-  extern __shared__ unsigned char blk_raw[];
-  AT(*U)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(blk_raw);
-  __shared__ AT r[SB], y[SB];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(SB, ns - k);
-  const int r0 = k + w, nrows = f - r0;
-  const int row0 = blockIdx.x * 256;
-  if (blockIdx.x > 0 && row0 >= nrows) return;
-  const T *Ff = (const T *)sv.F + sv.front_off[s];
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  load_block_inverse<T, AT>(Ff, f, k, w, U);
-  if (threadIdx.x < SB) r[threadIdx.x] = threadIdx.x < w ? (AT)rhs[k + threadIdx.x] : AT(0);
-  __syncthreads();
-  if (threadIdx.x < SB) {
-    const int j = threadIdx.x;
-    AT acc = r[j];
-    for (int i = 0; i < min(j, w); ++i) acc += U[j][i] * r[i];
-    y[j] = j < w ? acc : AT(0);
-    if (blockIdx.x == 0 && j < w) yz[sv.piv_off[s] + k + j] = (double)acc;
+__device__ __forceinline__ void publish_block(const SV &sv, int64_t p, int w, unsigned tag, T val) {
+  const int t = threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    if (t < w) st_relaxed_u64(sv.pub + p + t, ((unsigned long long)tag << 32) | __float_as_uint(val));
+  } else {
+    if (t < w) reinterpret_cast<double *>(sv.pub)[p + t] = val;
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();
+      st_release_u32(sv.pflag + p, tag);
+    }
   }
-  __syncthreads();
-  if (row0 >= nrows) return;
-  const T *F = Ff + (int64_t)k * f;
-  const int i0 = r0 + row0 + threadIdx.x;
-  if (i0 >= f) return;
-  AT a0 = AT(0);
-  for (int t = 0; t < w; t += 32) {
-    T v0[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) v0[u] = t + u < w ? F[(int64_t)(t + u) * f + i0] : T(0);
-#pragma unroll
-    for (int u = 0; u < 32; ++u) a0 += (AT)v0[u] * y[t + u];
-  }
-  rhs[i0] -= (double)a0;
 }
 
-__global__ void k_diag_scale(DevSym d, SV sv, const int32_t *__restrict__ fronts, double *__restrict__ yz) {
-  const int s = fronts[blockIdx.y];
+// waits for the block at pivot position p published under tag and copies its
+// w values to dst[0, w) (zeros up to SB); every thread calls it, and it ends
+// with a barrier.  False (DEV_TIMEOUT recorded) when the wait bound expires
+// or another CTA already gave up.
+template <typename T>
+__device__ __forceinline__ bool wait_block(const SV &sv, int64_t p, int w, unsigned tag, T *dst, int *status,
+                                           int *abort) {
+  const int t = threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    if (t < w) {
+      const unsigned long long *a = sv.pub + p + t;
+      unsigned long long v = ld_relaxed_u64(a);
+      if ((unsigned)(v >> 32) != tag) {
+        const long long t0 = clock64();
+        for (int n = 1; (unsigned)((v = ld_relaxed_u64(a)) >> 32) != tag; ++n) {
+          if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
+            atomicOr(status, DEV_TIMEOUT);
+            *abort = 1;
+            break;
+          }
+        }
+      }
+      dst[t] = __uint_as_float((unsigned)v);
+    } else if (t < SB) {
+      dst[t] = 0.f;
+    }
+  } else {
+    if (t == 0 && ld_acquire_u32(sv.pflag + p) != tag) {
+      const long long t0 = clock64();
+      for (int n = 1; ld_acquire_u32(sv.pflag + p) != tag; ++n) {
+        if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
+          atomicOr(status, DEV_TIMEOUT);
+          *abort = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (t < w) dst[t] = __ldcg(reinterpret_cast<const double *>(sv.pub) + p + t);
+    else if (t < SB) dst[t] = 0.0;
+  }
+  __syncthreads();
+  return *abort == 0;
+}
+
+// item ticket and completion: the last CTA of a launch resets the counters
+// for the next launch of the same store
+template <typename AT>
+__device__ __forceinline__ bool solve_item_begin(unsigned *ctl, int *status, SolveShared<AT> &sm) {
+  if (threadIdx.x == 0) {
+    sm.item = (int)atomicAdd(&ctl[1], 1u);
+    sm.abort = 0;
+    if (sm.item >= (int)gridDim.x) {  // counters not reset by the previous launch
+      atomicOr(status, DEV_TIMEOUT);
+      sm.abort = 1;
+    } else if (timed_out(status)) {
+      sm.abort = 1;
+    }
+  }
+  __syncthreads();
+  return sm.abort == 0;
+}
+
+__device__ __forceinline__ void solve_item_end(unsigned *ctl) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[2], 1u) == gridDim.x - 1) {
+      atomicExch(&ctl[1], 0u);
+      atomicExch(&ctl[2], 0u);
+    }
+  }
+}
+
+// a new solve: new tags (2e forward, 2e + 1 backward), counters cleared
+__global__ void k_solve_begin(unsigned *ctl) {
+  ctl[0] += 1u;
+  ctl[1] = 0u;
+  ctl[2] = 0u;
+}
+
+// Forward item: rows [r0, r0 + nr) of front s.  Thread (row, quarter qq)
+// accumulates sum_j L(row, block j) y_j over its 32 columns of every own
+// block j the band depends on.  A struct band subtracts the sums from its
+// right-hand side (read by the parent's gather); own band b forms r_b =
+// P rhs_b - sums, y_b = X_b r_b with X_b = L_bb^{-1}, publishes y_b and writes
+// z_b = D_b^{-1} y_b.
+template <typename T>
+__device__ __forceinline__ void fwd_item(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
+                                         SolveItem itm, int nb, unsigned tag, int *status, T (*U)[SB + 1],
+                                         SolveShared<T> &sm) {
+  using AT = T;
+  const int s = lvl_fronts[itm.q];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ns) return;
+  const int f = front_order(d, s, dpn);
+  const int nbo = (ns + SB - 1) / SB;
+  const bool own = itm.key < nbo;
+  const int r0 = own ? itm.key * SB : ns + (itm.key - nbo) * SB;
+  const int nr = min(SB, (own ? ns : f) - r0);  // an own band ends at the last own row
+  const int ndep = own ? itm.key : nbo;
+  const T *F = (const T *)sv.F + sv.front_off[s];
   const int64_t po = sv.piv_off[s];
-  double *z = yz + po;
-  int ty = sv.piv_type[po + t];
-  if (ty == 0) {
-    z[t] = z[t] / sv.D0[po + t];
-  } else if (ty == 1) {
-    double d11 = sv.D0[po + t], d21 = sv.D1[po + t], d22 = sv.D0[po + t + 1];
-    double det = d11 * d22 - d21 * d21;
-    double y1 = z[t], y2 = z[t + 1];
-    z[t] = (d22 * y1 - d21 * y2) / det;
-    z[t + 1] = (d11 * y2 - d21 * y1) / det;
+  const int tid = threadIdx.x, row = tid & (SB - 1), qq = tid >> 7;
+  if (own) load_block_inverse<T, AT>(sv, s, r0, nr, U);
+  AT sum = AT(0), comp = AT(0);
+  for (int j = 0; j < ndep; ++j) {
+    const int kc = j * SB, wc = min(SB, ns - kc);
+    const T *Fc = F + (int64_t)(kc + 32 * qq) * f + r0 + row;
+    T v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = (row < nr && 32 * qq + u < wc) ? Fc[(int64_t)u * f] : T(0);
+    AT *y = sm.xs[j & 1];
+    if (!wait_block<T>(sv, po + kc, wc, tag, y, status, &sm.abort)) return;
+    AT a = AT(0);
+#pragma unroll
+    for (int u = 0; u < 32; ++u) a += (AT)v[u] * y[32 * qq + u];
+    kahan_add(sum, comp, a);
   }
+  sm.dp[qq][row] = (double)sum - (double)comp;
+  __syncthreads();
+  if (!own) {
+    if (tid < nr) {
+      double *rhs = sv.rhs + sv.rhs_off[s];
+      rhs[r0 + tid] -= (sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid]);
+    }
+    return;
+  }
+  const int w = nr;
+  if (tid < SB) {
+    AT r = AT(0);
+    if (tid < w) {
+      // the factor's rows are in final pivoted order; the pivots permute
+      // positions inside their panel of nb columns
+      const int pos = r0 + tid, pstart = (pos / nb) * nb;
+      const double b = sv.rhs[sv.rhs_off[s] + pstart + sv.piv_perm[po + pos]];
+      r = (AT)(b - ((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid])));
+    }
+    sm.rb[tid] = r;
+  }
+  __syncthreads();
+  {
+    AT a = AT(0);
+    const int i1 = min(32 * qq + 32, row);
+    for (int i = 32 * qq; i < i1; ++i) a += U[row][i] * sm.rb[i];
+    sm.ap[qq][row] = a;
+  }
+  __syncthreads();
+  AT y = AT(0);
+  if (tid < w) {
+    y = sm.rb[tid] + ((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
+    sm.yb[tid] = y;
+  }
+  publish_block<T>(sv, po + r0, w, tag, y);
+  __syncthreads();
+  if (tid < w) {
+    const int64_t p = po + r0 + tid;
+    const int ty = sv.piv_type[p];
+    if (ty == 0) {
+      sv.yz[p] = (double)y / sv.D0[p];
+    } else if (ty == 1) {
+      const double d11 = sv.D0[p], d21 = sv.D1[p], d22 = sv.D0[p + 1];
+      const double det = d11 * d22 - d21 * d21;
+      const double y1 = (double)y, y2 = (double)sm.yb[tid + 1];
+      sv.yz[p] = (d22 * y1 - d21 * y2) / det;
+      sv.yz[p + 1] = (d11 * y2 - d21 * y1) / det;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
+    k_fwd_level(DevSym d, SV sv, const int32_t *__restrict__ lvl_fronts, const SolveItem *__restrict__ items, int nb,
+                unsigned *ctl, int *status) {
+  extern __shared__ unsigned char blk_raw[];
+  __shared__ SolveShared<T> sm;
+  if (solve_item_begin(ctl, status, sm)) {
+    const unsigned tag = 2u * *(volatile unsigned *)ctl;
+    fwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, reinterpret_cast<T(*)[SB + 1]>(blk_raw), sm);
+  }
+  solve_item_end(ctl);
 }
 
 // v_own = z_own - L21^T x_struct: a CTA owns 64 own columns, 8 per warp.
@@ -1033,69 +1221,93 @@ __global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t
   }
 }
 
-// backward step of block [k, k + w) of every active front: x_b = X^T v_b
-// (every CTA forms it from the block inverse; CTA 0 writes it, un-pivoted,
-// into the solution), then the columns left of the block: v_c -= sum_t
-// L(k + t, c) x_t, 256 columns per CTA.  v_b itself is only read here.
+// Backward item: own block b = [k, k + w) of front s.  Warp wq owns columns
+// k + 8 wq .. + 8 with its lanes along the rows (coalesced) and accumulates
+// sum_j L(block j, column)^T x_j over every later block j; then v_b (z_b less
+// the struct rows' part, formed by k_bwd_init) minus those sums gives
+// x_b = X_b^T v_b, which is published for the earlier blocks and written,
+// un-pivoted, into the solution.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_bwd_block(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                    int nb, double *__restrict__ yz, double *__restrict__ sol) {
+__device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
+                                         SolveItem itm, int nb, unsigned tag, int *status, double *__restrict__ sol,
+                                         T (*U)[SB + 1], SolveShared<T> &sm) {
   using AT = T;
-  extern __shared__ unsigned char blk_raw[];
-  AT(*U)[SB + 1] = reinterpret_cast<AT(*)[SB + 1]>(blk_raw);
-  __shared__ AT v[SB], x[SB];
-  const int s = fronts[blockIdx.y];
+  const int s = lvl_fronts[itm.q];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  if (blockIdx.x > 0 && (int)blockIdx.x * 256 >= k) return;
   const int f = front_order(d, s, dpn);
-  const int w = min(SB, ns - k);
+  const int nbo = (ns + SB - 1) / SB;
+  const int b = nbo - 1 - itm.key;
+  const int k = b * SB, w = min(SB, ns - k);
+  const T *F = (const T *)sv.F + sv.front_off[s];
   const int64_t po = sv.piv_off[s];
-  const T *Ff = (const T *)sv.F + sv.front_off[s];
-  load_block_inverse<T, AT>(Ff, f, k, w, U);
-  if (threadIdx.x < w) v[threadIdx.x] = (AT)yz[po + k + threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x < w) {
-    const int i = threadIdx.x;
-    AT acc = v[i];
-    for (int j = i + 1; j < w; ++j) acc += U[j][i] * v[j];
-    x[i] = acc;
-    if (blockIdx.x == 0) {
-      // piv_perm is local to the pivot panel (width nb) holding position k + i
-      const int pos = k + i, pstart = (pos / nb) * nb;
-      sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)acc;
+  const int tid = threadIdx.x, row = tid & (SB - 1), qq = tid >> 7;
+  const int warp = tid >> 5, lane = tid & 31, c0 = 8 * warp;
+  load_block_inverse<T, AT>(sv, s, k, w, U);
+  AT sum[8], comp[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) sum[cc] = comp[cc] = AT(0);
+  for (int j = nbo - 1; j > b; --j) {
+    const int kr = j * SB, wr = min(SB, ns - kr);
+    const T *Fc = F + (int64_t)(k + c0) * f + kr + lane;
+    T q[8][4];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        q[cc][m] = (c0 + cc < w && lane + 32 * m < wr) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
+    AT *x = sm.xs[j & 1];
+    if (!wait_block<T>(sv, po + kr, wr, tag, x, status, &sm.abort)) return;
+    AT xv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xv[m] = x[lane + 32 * m];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      AT a = AT(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
+      kahan_add(sum[cc], comp[cc], a);
     }
   }
-  if (threadIdx.x >= w && threadIdx.x < SB) x[threadIdx.x] = AT(0);
-  __syncthreads();
-  // columns c < k of this CTA (256 of them): each warp takes 4 columns at a
-  // time with its lanes along t (coalesced), partial sums joined by shuffles
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cend = min((int)blockIdx.x * 256 + 256, k);
-  for (int c0 = blockIdx.x * 256 + warp * 4; c0 < cend; c0 += 32) {
-    T q[4][4];
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
+  for (int cc = 0; cc < 8; ++cc) {
+    double t = (double)sum[cc] - (double)comp[cc];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int col = c0 + cc, t = lane + 32 * m;
-        q[cc][m] = (col < cend && t < w) ? Ff[(int64_t)col * f + k + t] : T(0);
-      }
-    AT part[4];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      part[cc] = AT(0);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) part[cc] += (AT)q[cc][m] * x[lane + 32 * m];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part[cc] += __shfl_xor_sync(0xffffffffu, part[cc], o);
-    }
-    if (lane < 4 && c0 + lane < cend) {
-      const AT pv = lane == 0 ? part[0] : lane == 1 ? part[1] : lane == 2 ? part[2] : part[3];
-      yz[po + c0 + lane] -= (double)pv;
-    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sm.dp[0][c0 + cc] = t;
   }
+  __syncthreads();
+  if (tid < SB) sm.rb[tid] = tid < w ? (AT)(sv.yz[po + k + tid] - sm.dp[0][tid]) : AT(0);
+  __syncthreads();
+  {
+    AT a = AT(0);
+    const int j1 = min(32 * qq + 32, w);
+    for (int jj = max(32 * qq, row + 1); jj < j1; ++jj) a += U[jj][row] * sm.rb[jj];
+    sm.ap[qq][row] = a;
+  }
+  __syncthreads();
+  AT x = AT(0);
+  if (tid < w) x = sm.rb[tid] + ((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
+  publish_block<T>(sv, po + k, w, tag, x);
+  if (tid < w) {
+    // piv_perm is local to the pivot panel (width nb) holding position k + tid
+    const int pos = k + tid, pstart = (pos / nb) * nb;
+    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)x;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
+    k_bwd_level(DevSym d, SV sv, const int32_t *__restrict__ lvl_fronts, const SolveItem *__restrict__ items, int nb,
+                unsigned *ctl, int *status, double *__restrict__ sol) {
+  extern __shared__ unsigned char blk_raw[];
+  __shared__ SolveShared<T> sm;
+  if (solve_item_begin(ctl, status, sm)) {
+    const unsigned tag = 2u * *(volatile unsigned *)ctl + 1u;
+    bwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, sol, reinterpret_cast<T(*)[SB + 1]>(blk_raw),
+                sm);
+  }
+  solve_item_end(ctl);
 }
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
@@ -1243,47 +1455,34 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   SV sv = view(st);
   const int nb = c.S.opts.panel;
   const int dpn = st.dpn;
-  const size_t diag_smem = (size_t)SB * (SB + 1) * sizeof(T);
+  const size_t blk_smem = (size_t)SB * (SB + 1) * sizeof(T);
+  k_solve_begin<<<1, 1, 0, c.stream>>>(st.ctl);
+  c.count();
   for (int L = 0; L < c.S.n_levels; ++L) {
-    LevelInfo li = level_info(c, L, dpn);
-    int64_t n = (li.i1 - li.i0) * dpn;
-    k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, li.i0, n, b);
-    c.count();
-    const int32_t *fronts = c.ds.lvl_fronts + li.f0;
-    const int nf = (int)(li.f1 - li.f0);
-    int max_ns = li.ns.empty() ? 0 : li.ns[0];
-    if (max_ns == 0) continue;
-    dim3 gp((max_ns + nb - 1) / nb, nf);
-    k_fwd_permute<<<gp, 64, 0, c.stream>>>(c.ds, sv, fronts, nb);
-    c.count();
-    for (int k = 0; k < max_ns; k += SB) {
-      int na = n_active(li, k);
-      int max_rows = 0;
-      for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - k - std::min(SB, li.ns[q] - k));
-      dim3 g(std::max(1, (max_rows + 255) / 256), na);
-      k_fwd_block<T><<<g, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, st.yz);
+    const int64_t i0 = c.h_item_ptr[L], n = (c.h_item_ptr[L + 1] - i0) * dpn;
+    if (n > 0) {
+      k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, i0, n, b);
       c.count();
     }
-    dim3 gd((max_ns + 255) / 256, nf);
-    k_diag_scale<<<gd, 256, 0, c.stream>>>(c.ds, sv, fronts, st.yz);
+    const int64_t t0 = st.h_fwd_lvl[L], nt = st.h_fwd_lvl[L + 1] - t0;
+    if (nt == 0) continue;
+    k_fwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.fwd_items + t0, nb,
+                                                              st.ctl, c.status);
     c.count();
   }
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
+    const int64_t t0 = st.h_bwd_lvl[L], nt = st.h_bwd_lvl[L + 1] - t0;
+    if (nt == 0) continue;
     LevelInfo li = level_info(c, L, dpn);
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
-    int nf = (int)(li.f1 - li.f0);
-    int max_ns = li.ns.empty() ? 0 : li.ns[0];
-    if (max_ns == 0) continue;
+    const int nf = (int)(li.f1 - li.f0);
+    const int max_ns = li.ns[0];
     dim3 gi((max_ns + 63) / 64, nf);
     k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x, st.yz);
     c.count();
-    int last = ((max_ns - 1) / SB) * SB;
-    for (int k = last; k >= 0; k -= SB) {
-      int na = n_active(li, k);
-      dim3 g(std::max(1, (k + 255) / 256), na);
-      k_bwd_block<T><<<g, 256, diag_smem, c.stream>>>(c.ds, sv, fronts, k, nb, st.yz, x);
-      c.count();
-    }
+    k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb,
+                                                              st.ctl, c.status, x);
+    c.count();
   }
 }
 
@@ -1427,10 +1626,10 @@ void set_kernel_attributes() {
   cudaFuncSetAttribute(k_panel_rows<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((32 * 32 + 32 * 32 + 32 * 129) * sizeof(double)));
   cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
-  cudaFuncSetAttribute(k_fwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_fwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-  cudaFuncSetAttribute(k_bwd_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_bwd_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_fwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_fwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_bwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
+  cudaFuncSetAttribute(k_bwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
   cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
   cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
 }
