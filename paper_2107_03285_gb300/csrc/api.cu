@@ -162,8 +162,9 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   }
   // substitution schedules (one CTA per item): forward items are the
   // front's 128-row bands, own bands (key b) before its struct bands (key
-  // nbo + j); backward items its 128-column blocks, last first (key nbo - 1 -
-  // b).  Sorting a level's items by key puts every dependency first.
+  // nbo + j), except that a front with one own block is a single item;
+  // backward items its 128-column blocks, last first (key nbo - 1 - b).
+  // Sorting a level's items by key puts every dependency first.
   s.h_fwd_items.clear(); s.h_bwd_items.clear();
   s.h_fwd_lvl.assign(1, 0); s.h_bwd_lvl.assign(1, 0);
   int32_t q = 0;
@@ -173,7 +174,9 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
       const int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
       const int32_t nbo = (int32_t)((ns + SBK - 1) / SBK), nbs = (int32_t)((f - ns + SBK - 1) / SBK);
       if (ns > 0) {
-        for (int32_t k = 0; k < nbo + nbs; ++k) s.h_fwd_items.push_back({q, k});
+        // a single-block front is one forward item (it also does its struct rows)
+        const int32_t nfw = nbo > 1 ? nbo + nbs : 1;
+        for (int32_t k = 0; k < nfw; ++k) s.h_fwd_items.push_back({q, k});
         for (int32_t k = 0; k < nbo; ++k) s.h_bwd_items.push_back({q, k});
       }
       ++q;

@@ -962,7 +962,7 @@ __device__ __forceinline__ void kahan_add(AT &sum, AT &comp, AT x) {
 template <typename AT>
 struct SolveShared {
   AT xs[2][SB];       // values of the block being consumed (double-buffered)
-  double dp[4][SB];   // per-quarter partial sums
+  AT dp[4][SB];       // per-quarter (per-column) compensated sums
   AT ap[4][SB];       // per-quarter partial block products
   AT rb[SB];          // right-hand side of the own block
   AT yb[SB];          // the own block's values
@@ -1105,12 +1105,14 @@ __device__ __forceinline__ void fwd_item(const DevSym &d, const SV &sv, const in
     for (int u = 0; u < 32; ++u) a += (AT)v[u] * y[32 * qq + u];
     kahan_add(sum, comp, a);
   }
-  sm.dp[qq][row] = (double)sum - (double)comp;
+  // partial sums are joined in the factor's precision; FP64 (slow on this
+  // part) only for the one subtraction per row from the FP64 right-hand side
+  sm.dp[qq][row] = sum - comp;
   __syncthreads();
   if (!own) {
     if (tid < nr) {
       double *rhs = sv.rhs + sv.rhs_off[s];
-      rhs[r0 + tid] -= (sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid]);
+      rhs[r0 + tid] -= (double)((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid]));
     }
     return;
   }
@@ -1122,7 +1124,7 @@ __device__ __forceinline__ void fwd_item(const DevSym &d, const SV &sv, const in
       // positions inside their panel of nb columns
       const int pos = r0 + tid, pstart = (pos / nb) * nb;
       const double b = sv.rhs[sv.rhs_off[s] + pstart + sv.piv_perm[po + pos]];
-      r = (AT)(b - ((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid])));
+      r = (AT)(b - (double)((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid])));
     }
     sm.rb[tid] = r;
   }
@@ -1154,6 +1156,26 @@ __device__ __forceinline__ void fwd_item(const DevSym &d, const SV &sv, const in
       sv.yz[p + 1] = (d11 * y2 - d21 * y1) / det;
     }
   }
+  if (nbo > 1) return;
+  // a single-block front has no struct-band items: this CTA updates its
+  // struct rows' right-hand side with y_b from shared memory, 128 rows a pass
+  if (tid >= w && tid < SB) sm.yb[tid] = AT(0);
+  __syncthreads();
+  double *rhs = sv.rhs + sv.rhs_off[s];
+  for (int rs = ns; rs < f; rs += SB) {
+    const int nrs = min(SB, f - rs);
+    const T *Fc = F + (int64_t)(32 * qq) * f + rs + row;
+    T v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = (row < nrs && 32 * qq + u < w) ? Fc[(int64_t)u * f] : T(0);
+    AT a = AT(0);
+#pragma unroll
+    for (int u = 0; u < 32; ++u) a += (AT)v[u] * sm.yb[32 * qq + u];
+    sm.ap[qq][row] = a;
+    __syncthreads();
+    if (tid < nrs) rhs[rs + tid] -= (double)((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
+    __syncthreads();
+  }
 }
 
 template <typename T>
@@ -1169,62 +1191,10 @@ __global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
   solve_item_end(ctl);
 }
 
-// v_own = z_own - L21^T x_struct: a CTA owns 64 own columns, 8 per warp.
-// The solution at the front's struct rows is gathered into shared memory in
-// chunks; each warp reads its columns with the lanes along the rows
-// (coalesced) and joins the lanes' partial sums by shuffles.
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_init(DevSym d, SV sv, const int32_t *__restrict__ fronts,
-                                                   const double *__restrict__ sol, double *__restrict__ yz) {
-  using AT = T;
-  constexpr int CB = 64, CPW = 8, CHUNK = 4096;
-  __shared__ AT xsh[CHUNK];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int nown = d.sn_nown[s];
-  const int ns = nown * dpn;
-  const int t0 = blockIdx.x * CB;
-  if (t0 >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int nst = f - ns;
-  if (nst == 0) return;
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cw = t0 + warp * CPW;  // this warp's first column
-  AT acc[CPW];
-#pragma unroll
-  for (int c = 0; c < CPW; ++c) acc[c] = AT(0);
-  for (int r0 = 0; r0 < nst; r0 += CHUNK) {
-    const int nr = min(CHUNK, nst - r0);
-    __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      const int ii = ns + r0 + r;
-      xsh[r] = (AT)sol[(int64_t)sr[ii / dpn - nown] * dpn + ii % dpn];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < CPW; ++c) {
-      if (cw + c >= ns) break;
-      const T *Fc = F + (int64_t)(cw + c) * f + ns + r0;
-      AT a = AT(0);
-#pragma unroll 8
-      for (int r = lane; r < nr; r += 32) a += (AT)Fc[r] * xsh[r];
-      acc[c] += a;
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < CPW; ++c) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (lane == 0 && cw + c < ns) yz[sv.piv_off[s] + cw + c] -= (double)acc[c];
-  }
-}
-
 // Backward item: own block b = [k, k + w) of front s.  Warp wq owns columns
 // k + 8 wq .. + 8 with its lanes along the rows (coalesced) and accumulates
-// sum_j L(block j, column)^T x_j over every later block j; then v_b (z_b less
-// the struct rows' part, formed by k_bwd_init) minus those sums gives
+// L(rows, column)^T x over the struct rows (x there is the ancestors'
+// solution) and over every later own block; v_b = z_b minus those sums gives
 // x_b = X_b^T v_b, which is published for the earlier blocks and written,
 // un-pivoted, into the solution.
 template <typename T>
@@ -1247,7 +1217,43 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   AT sum[8], comp[8];
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) sum[cc] = comp[cc] = AT(0);
-  for (int j = nbo - 1; j > b; --j) {
+  int ph = 0;  // alternates the value buffers across both loops
+  // struct rows: the solution there (the ancestors') is final; gathered 128
+  // rows a pass
+  const int nown = d.sn_nown[s];
+  const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
+  // the struct-rank index of the next pass is read one pass ahead
+  int sidx = (tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
+  for (int rs = ns; rs < f; rs += SB, ++ph) {
+    const int nrs = min(SB, f - rs);
+    const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
+    T q[8][4];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        q[cc][m] = (c0 + cc < w && lane + 32 * m < nrs) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
+    AT *x = sm.xs[ph & 1];
+    if (tid < SB) {
+      const int ii = rs + tid;
+      const int cur = sidx;
+      if (ii + SB < f) sidx = sr[(ii + SB) / dpn - nown];
+      x[tid] = tid < nrs ? (AT)sol[(int64_t)cur * dpn + ii % dpn] : AT(0);
+    }
+    __syncthreads();
+    AT xv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xv[m] = x[lane + 32 * m];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      AT a = AT(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
+      kahan_add(sum[cc], comp[cc], a);
+    }
+  }
+  // later own blocks, as their values are published
+  for (int j = nbo - 1; j > b; --j, ++ph) {
     const int kr = j * SB, wr = min(SB, ns - kr);
     const T *Fc = F + (int64_t)(k + c0) * f + kr + lane;
     T q[8][4];
@@ -1256,7 +1262,7 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
 #pragma unroll
       for (int m = 0; m < 4; ++m)
         q[cc][m] = (c0 + cc < w && lane + 32 * m < wr) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
-    AT *x = sm.xs[j & 1];
+    AT *x = sm.xs[ph & 1];
     if (!wait_block<T>(sv, po + kr, wr, tag, x, status, &sm.abort)) return;
     AT xv[4];
 #pragma unroll
@@ -1271,13 +1277,13 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   }
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) {
-    double t = (double)sum[cc] - (double)comp[cc];
+    AT t = sum[cc] - comp[cc];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) sm.dp[0][c0 + cc] = t;
   }
   __syncthreads();
-  if (tid < SB) sm.rb[tid] = tid < w ? (AT)(sv.yz[po + k + tid] - sm.dp[0][tid]) : AT(0);
+  if (tid < SB) sm.rb[tid] = tid < w ? (AT)(sv.yz[po + k + tid] - (double)sm.dp[0][tid]) : AT(0);
   __syncthreads();
   {
     AT a = AT(0);
@@ -1473,13 +1479,6 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
     const int64_t t0 = st.h_bwd_lvl[L], nt = st.h_bwd_lvl[L + 1] - t0;
     if (nt == 0) continue;
-    LevelInfo li = level_info(c, L, dpn);
-    const int32_t *fronts = c.ds.lvl_fronts + li.f0;
-    const int nf = (int)(li.f1 - li.f0);
-    const int max_ns = li.ns[0];
-    dim3 gi((max_ns + 63) / 64, nf);
-    k_bwd_init<T><<<gi, 256, 0, c.stream>>>(c.ds, sv, fronts, x, st.yz);
-    c.count();
     k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb,
                                                               st.ctl, c.status, x);
     c.count();
