@@ -192,6 +192,13 @@ const char *sgn_strerror(sgn_status s);
 /* Detail of the last failed call on h (which CUDA call or check failed);
  * empty if none.  Owned by h, valid until the next call on h. */
 const char *sgn_last_error(sgn_t h);
+/* Self-test of the bounded device waits (the paper has no counterpart): runs
+ * one substitution wait, on the first bound store, for a block value that
+ * nothing publishes.  Returns SGN_ETIMEOUT after about a second when the
+ * wait gave up and reported as designed (the status word is then cleared
+ * and h stays usable); any other status means the bound or its report
+ * failed.  ESTATE before sgn_bind. */
+sgn_status sgn_selftest_wait_timeout(sgn_t h);
 
 /* ---- hot path ------------------------------------------------------------
  * sgn_assemble: element kernels evaluate, at positions x_d and parameters

@@ -26,7 +26,7 @@ EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_se
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
             "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
-            "sgn_last_error",
+            "sgn_last_error", "sgn_selftest_wait_timeout",
             # learned warm start (include/sgn_learn.h)
             "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
             "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_profile_read": (C.c_int, [VP, P(KernelProfile), C.c_int32]),
         "sgn_launch_count": (C.c_int64, [VP]),
         "sgn_last_error": (C.c_char_p, [VP]),
+        "sgn_selftest_wait_timeout": (C.c_int, [VP]),
         "sgn_learn_create": (C.c_int, [VP, P(LearnOpts), P(VP)]),
         "sgn_learn_device_bytes": (C.c_int, [VP, P(C.c_size_t)]),
         "sgn_learn_bind": (C.c_int, [VP, VP, C.c_size_t]),

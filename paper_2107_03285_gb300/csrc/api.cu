@@ -187,6 +187,20 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
     s.h_fwd_lvl.push_back((int64_t)s.h_fwd_items.size());
     s.h_bwd_lvl.push_back((int64_t)s.h_bwd_items.size());
   }
+  // self-check (the substitutions' waits rely on it): an item of key k waits
+  // only on keys 0 .. k - 1 of its own front, so each front's items must
+  // appear with keys 0, 1, 2, ... in list order within their level
+  s.sched_ok = true;
+  for (const auto *lst : {&s.h_fwd_items, &s.h_bwd_items}) {
+    const auto &lvl = lst == &s.h_fwd_items ? s.h_fwd_lvl : s.h_bwd_lvl;
+    std::vector<int32_t> next(q, 0);
+    for (size_t L = 0; L + 1 < lvl.size(); ++L)
+      for (int64_t t = lvl[L]; t < lvl[L + 1]; ++t) {
+        const SolveItem &it = (*lst)[t];
+        if (it.q < 0 || it.q >= q || it.key != next[it.q]) s.sched_ok = false;
+        else ++next[it.q];
+      }
+  }
   s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po;
   s.cb_elems = plan_cb_arena(c.S, dpn, s.h_cb_off, &s.cb_sum);
 }
@@ -275,6 +289,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     store_offsets(c, s, dpn);
     if (!on) return;
     if (s.cb_elems < 0) { plan_ok = false; s.cb_elems = 0; }
+    if (!s.sched_ok) plan_ok = false;
     size_t es = fp32 ? 4 : 8;
     s.F = cv.take<char>((size_t)s.front_elems * es);
     s.CB = cv.take<char>((size_t)s.cb_elems * es);
@@ -309,7 +324,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   store(c.kkt32, (stores & SGN_STORE_MIXED) != 0, 2 * d, true, true);
   store(c.kf, (stores & SGN_STORE_KFACT) != 0, d, false, false);
   store(c.kf32, (stores & SGN_STORE_KFACT_MIXED) != 0, d, false, true);
-  return plan_ok ? cv.off + 256 : 0;  // 0: the contribution-block plan failed its self-check
+  return plan_ok ? cv.off + 256 : 0;  // 0: a host plan failed its self-check
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -373,6 +388,21 @@ sgn_status launch_check(sgn_ctx *h) {
 extern "C" {
 
 const char *sgn_last_error(sgn_t h) { return h ? h->last_error.c_str() : ""; }
+
+sgn_status sgn_selftest_wait_timeout(sgn_t h) {
+  if (!h) return SGN_EINVAL;
+  if (!h->bound) return SGN_ESTATE;
+  Store *st = nullptr;
+  for (Store *s : {&h->kkt32, &h->kkt64, &h->kf32, &h->kf})
+    if (s->enabled) { st = s; break; }
+  if (!st) return SGN_ESTATE;
+  sgn_status s = check_status(h);  // start from a clean status word
+  if (s != SGN_OK) return s;
+  wait_selftest(*h, *st);
+  s = launch_check(h);
+  if (s != SGN_OK) return s;
+  return check_status(h);  // SGN_ETIMEOUT expected; the word is cleared
+}
 
 const char *sgn_strerror(sgn_status s) {
   switch (s) {
@@ -443,7 +473,7 @@ sgn_status sgn_get_info(sgn_t h, sgn_info *o) {
 sgn_status sgn_device_bytes(sgn_t h, int32_t stores, size_t *bytes) {
   if (!h || !bytes) return SGN_EINVAL;
   *bytes = carve(*h, nullptr, stores, nullptr);
-  if (*bytes == 0) { g_err = "internal: contribution-block arena plan overlaps"; return SGN_EINVAL; }
+  if (*bytes == 0) { g_err = "internal: a host plan (contribution-block arena, substitution schedule) failed its self-check"; return SGN_EINVAL; }
   return SGN_OK;
 }
 
@@ -457,7 +487,7 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   if (!h || !dev_buf) return SGN_EINVAL;
   if (((uintptr_t)dev_buf & 255) != 0) { g_err = "device buffer must be 256-byte aligned"; return SGN_EINVAL; }
   size_t need = carve(*h, nullptr, stores, nullptr);
-  if (need == 0) { g_err = "internal: contribution-block arena plan overlaps"; return SGN_EINVAL; }
+  if (need == 0) { g_err = "internal: a host plan (contribution-block arena, substitution schedule) failed its self-check"; return SGN_EINVAL; }
   if (bytes < need) return SGN_ENOMEM;
   h->stream = (cudaStream_t)stream;
   CUDA_TRY(h, cudaGetDevice(&h->device));

@@ -90,6 +90,7 @@ struct Store {
   const SolveItem *fwd_items = nullptr, *bwd_items = nullptr;
   std::vector<SolveItem> h_fwd_items, h_bwd_items;
   std::vector<int64_t> h_fwd_lvl, h_bwd_lvl;  // per level: range in the item lists
+  bool sched_ok = true;  // every item listed after the items it waits on
   const int64_t *front_off = nullptr, *cb_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
   const int64_t *xinv_off = nullptr;
   std::vector<int64_t> h_front_off, h_cb_off, h_w_off, h_rhs_off, h_piv_off, h_xinv_off;
@@ -247,6 +248,7 @@ void solve_store(Ctx &c, Store &s, const double *b_red, double *x_red);
 void pivot_counts(Ctx &c, Store &s);  // fills c.counters (device)
 void set_kernel_attributes();
 void factor_direct(Ctx &c, Store &s);                                   // no graph
+void wait_selftest(Ctx &c, Store &s);  // one substitution wait that must expire
 cudaGraphExec_t capture_fn(Ctx &c, const std::function<void()> &body, int64_t *launches, int64_t *tc);
 void solve_direct(Ctx &c, Store &s, const double *b_red, double *x_red);  // no graph
 void destroy_graphs(Store &s);

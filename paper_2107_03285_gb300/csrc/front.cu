@@ -1509,6 +1509,23 @@ cudaEvent_t *Ctx::prof_pair(int kind, double flops) {
   return p;
 }
 
+// one bounded wait on a block value that nothing publishes (tag 1 is never
+// used: solves use 2e and 2e + 1, e >= 1): it must give up and record
+// DEV_TIMEOUT in the status word
+template <typename T>
+__global__ void k_wait_selftest(SV sv, int *status) {
+  __shared__ SolveShared<T> sm;
+  if (threadIdx.x == 0) sm.abort = 0;
+  __syncthreads();
+  wait_block<T>(sv, 0, 1, 1u, sm.xs[0], status, &sm.abort);
+}
+
+void wait_selftest(Ctx &c, Store &s) {
+  SV sv = view(s);
+  if (s.fp32) k_wait_selftest<float><<<1, SB, 0, c.stream>>>(sv, c.status);
+  else k_wait_selftest<double><<<1, SB, 0, c.stream>>>(sv, c.status);
+}
+
 void factor_direct(Ctx &c, Store &s) {
   if (s.fp32) factor_impl<float>(c, s);
   else factor_impl<double>(c, s);

@@ -110,8 +110,9 @@ def test_calls_before_bind_are_rejected(B):
 @pytest.mark.parametrize("which", ["kuhn3d_9", "batch2d_12"])
 def test_contribution_block_arena_plan_is_consistent(B, which):
     """sgn_device_bytes replays the contribution-block lifetimes and fails if
-    two live blocks would share memory; the arena must also need less than
-    keeping every front whole."""
+    two live blocks would share memory, and checks that every substitution
+    schedule lists each front's items after the items they wait on; the
+    arena must also need less than keeping every front whole."""
     from sgn_inputs import make_preset
     prob = make_preset(which)
     lib, code, h, keep = _setup(B, prob)

@@ -230,3 +230,20 @@ def test_inverted_element_is_reported(sgnmod):
     with pytest.raises(sgnmod.SGNError) as ei:
         s.factor(sgnmod.FP64, report=True)
     assert ei.value.code == 4  # SGN_EINVERTED
+
+
+def test_bounded_wait_reports_timeout_and_context_stays_usable(sgnmod):
+    """A substitution wait on a block value nothing publishes gives up after
+    its bound (about a second), the host reads SGN_ETIMEOUT, and the same
+    handle then still takes a correct step: the failure is reported, the
+    GPU context is not lost."""
+    import time
+    c = case("kuhn3d_7")
+    s = make(sgnmod, c)
+    t0 = time.perf_counter()
+    code = s.lib.sgn_selftest_wait_timeout(s.h)
+    waited = time.perf_counter() - t0
+    assert code == 10  # SGN_ETIMEOUT
+    assert 0.1 < waited < 30.0
+    _, dp, _, _, _ = s.step(c.x, c.p, sgnmod.MIXED)
+    assert _rel(dp.cpu().numpy(), c.dp_k) < 1e-8
