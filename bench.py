@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -34,7 +35,7 @@ METRIC = "SGN steps/sec (assemble+factor+solve)"
 UNIT = "steps/s"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 / FP64 pipe peaks measured on this machine's GB300 with an FMA-chain
-# kernel (152 SMs; the derivation is in the design doc)
+# kernel (152 SMs)
 FP32_SIMT_TFLOPS = 70.0
 FP64_TFLOPS = 1.20
 
@@ -79,7 +80,7 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sgn_bench_clocks_{os.getpid()}_{gpu_index}.csv")
 
     def __enter__(self):
         try:

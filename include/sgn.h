@@ -99,7 +99,7 @@ typedef struct {
 /* Symbolic-phase options; zero-initialise for defaults. */
 typedef struct {
   int32_t leaf_nodes;        /* nested dissection stops at <= leaf_nodes nodes (0: 16) */
-  int32_t panel;             /* pivot panel width: 8, 16, 32 or 64 (0: 32) */
+  int32_t panel;             /* pivot panel width: 8, 16 or 32 (0: 32) */
 } sgn_setup_opts;
 
 /* Least-squares objective (host arrays, copied by sgn_set_objective). */
@@ -251,20 +251,23 @@ sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows_h, int64_t *cols_
 /* sgn_assemble_static: same result as sgn_assemble (x_d, p_d in; the
  * assembled blocks, right-hand-side terms and dc/dp of the handle out), but
  * the per-element state it passes from the element kernel to the slot
- * gather lives in a fixed 16 MB device array inside the library instead of
- * the caller's bound buffer.  The paper has no counterpart: this exists for
- * callers that cannot allocate, or do not want to size, that part of the
- * workspace (e.g. a frozen allocator in a long-running service); the array
- * is allocated with the library image and every GPU that loads libsgn.so
- * holds it until the process exits.  Allocates nothing (no cudaMalloc,
+ * gather lives in a fixed 16 MB device array inside the library, not in the
+ * caller's bound buffer.  The paper has no counterpart.  It serves callers
+ * that must not allocate device memory, or have the runtime set any up, at
+ * the point where they assemble, e.g. a solver loop inside a memory-capped
+ * service whose allocator is frozen after start-up.  It does not shrink the
+ * bound buffer: sgn_device_bytes still counts the element-state region,
+ * which this entry point leaves unused.  The array belongs to the library's
+ * device image: every GPU that loads libsgn.so holds it until the process
+ * exits.  sgn_bind looks up its device address with the handle's device
+ * current, so under CUDA's lazy module loading the array is set up inside
+ * sgn_bind, never inside this call, which allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  Limit: (3 + (dim+1) dim) *
  * n_elem doubles <= 2^21, i.e. 139,810 tetrahedra or 233,016 triangles;
- * larger meshes get SGN_EINVAL.  The first call on a device looks up the
- * array's device address with that device current, so make that first call
- * before any stream capture.  All calls share the array (it keeps the last
- * call's contents; every entry is rewritten before it is read, so nothing
- * needs clearing): calls whose work overlaps on the GPU, from any handle or
- * stream, race on it. */
+ * larger meshes get SGN_EINVAL (sgn_strerror says why).  All calls share the
+ * array (it keeps the last call's contents; every entry is rewritten before
+ * it is read, so nothing needs clearing): calls whose work overlaps on the
+ * GPU, from any handle or stream, race on it. */
 sgn_status sgn_assemble_static(sgn_t h, const double *x_d, const double *p_d);
 
 /* ---- forward simulation and gradient -------------------------------------

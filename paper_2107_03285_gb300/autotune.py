@@ -27,7 +27,7 @@ import numpy as np
 
 from . import binding as B
 
-PANELS = (16, 32, 64)
+PANELS = (16, 32)
 LEAVES = (8, 16, 32, 64)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sgn_autotune.json")
 # tuned choices for the standard workloads, shipped with the package

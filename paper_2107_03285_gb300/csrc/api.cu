@@ -385,6 +385,13 @@ sgn_status launch_check(sgn_ctx *h) {
 
 }  // namespace
 
+namespace sgn {
+void set_error(Ctx *h, const std::string &msg) {
+  g_err = msg;
+  if (h) h->last_error = msg;
+}
+}  // namespace sgn
+
 extern "C" {
 
 const char *sgn_last_error(sgn_t h) { return h ? h->last_error.c_str() : ""; }
@@ -492,6 +499,9 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   h->stream = (cudaStream_t)stream;
   CUDA_TRY(h, cudaGetDevice(&h->device));
   CUDA_TRY(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  // the fixed element-scratch array of sgn_assemble_static is resolved (and,
+  // under lazy module loading, set up) here, never inside an assembly
+  CUDA_TRY(h, static_scratch_bind(h->device));
   std::vector<Upload> ups;
   h->base = (char *)dev_buf;
   h->bytes = bytes;

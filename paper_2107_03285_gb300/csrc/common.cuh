@@ -253,6 +253,14 @@ cudaGraphExec_t capture_fn(Ctx &c, const std::function<void()> &body, int64_t *l
 void solve_direct(Ctx &c, Store &s, const double *b_red, double *x_red);  // no graph
 void destroy_graphs(Store &s);
 
+// ---- error reporting (api.cu): sets the handle's detail (if h) and the
+// message sgn_strerror returns for the status
+void set_error(Ctx *h, const std::string &msg);
+
+// ---- static_scratch.cu: resolves the address of the library's fixed
+// element-scratch array on `device` (current), once per device
+cudaError_t static_scratch_bind(int device);
+
 }  // namespace sgn
 
 // the opaque handle of the C ABI is the context itself

@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "front_view.cuh"
 #include "tc_update.cuh"
 
 namespace sgn {
@@ -31,61 +32,6 @@ namespace sgn {
 namespace {
 
 constexpr int MAXNB = 64;
-
-struct SV {  // store view passed to kernels
-  void *F;                       // factor columns of every front (f x ns each)
-  void *CB;                      // contribution-block arena
-  void *Xinv;                    // diagonal-block inverses
-  void *W;
-  void *Ldg;                     // staged factored diagonal blocks (panel x panel per panel)
-  float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
-  double *rhs;
-  int32_t *piv_type, *piv_perm;
-  double *D0, *D1;
-  double *yz;                    // y, z = D^{-1} y, v of the substitutions (pivot order)
-  unsigned long long *pub;       // published block values of the substitutions
-  unsigned *pflag;               // their tags (FP64 fronts)
-  const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off, *xinv_off;
-  int dpn;
-  int kkt;
-};
-
-SV view(Store &s) {
-  SV v;
-  v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
-  v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz;
-  v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
-  v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
-  v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
-  return v;
-}
-
-__device__ __forceinline__ int front_order(const DevSym &d, int s, int dpn) {
-  return (d.sn_nown[s] + d.sn_nstruct[s]) * dpn;
-}
-
-// The lower triangle of front s (order f, ns fully-summed columns): columns
-// j < ns live in the front array (f x ns, column-major), the contribution
-// block (rows and columns >= ns) in the arena ((f - ns) x (f - ns)).
-template <typename T>
-struct FrontMat {
-  T *L, *C;
-  int64_t f, ns;
-  // element (i, j) of the lower triangle (i >= j)
-  __device__ __forceinline__ T *at(int64_t i, int64_t j) const {
-    return j < ns ? L + i + j * f : C + (i - ns) + (j - ns) * (f - ns);
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ FrontMat<T> front_mat(const DevSym &d, const SV &sv, int s) {
-  FrontMat<T> m;
-  m.L = (T *)sv.F + sv.front_off[s];
-  m.C = (T *)sv.CB + sv.cb_off[s];
-  m.ns = (int64_t)d.sn_nown[s] * sv.dpn;
-  m.f = m.ns + (int64_t)d.sn_nstruct[s] * sv.dpn;
-  return m;
-}
 
 // ---------------------------------------------------------------- assembly
 // One CTA per (front, node column group P): zero the group's DPN columns,
@@ -819,503 +765,6 @@ __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv,
 }
 
 
-// ------------------------------------------------------------------ solves
-__global__ void k_fwd_gather(DevSym d, SV sv, int64_t item_base, int64_t n, const double *__restrict__ b) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  const int dpn = sv.dpn;
-  const int64_t item = item_base + idx / dpn;
-  const int kd = (int)(idx % dpn);
-  const int s = d.item_sn[item], P = d.item_P[item];
-  const int nown = d.sn_nown[s];
-  double v = P < nown ? b[(int64_t)(d.sn_first[s] + P) * dpn + kd] : 0.0;
-  const int coff = d.sn_child_off[s], nch = d.sn_nchild[s];
-  for (int j = 0; j < nch; ++j) {
-    int c = d.children[coff + j];
-    int q = d.cmap[d.cmap_off[coff + j] + P];
-    if (q >= 0) v += sv.rhs[sv.rhs_off[c] + (int64_t)d.sn_nown[c] * dpn + (int64_t)q * dpn + kd];
-  }
-  sv.rhs[sv.rhs_off[s] + (int64_t)P * dpn + kd] = v;
-}
-
-constexpr int SB = 128;  // solve block width (independent of the pivot panel width)
-
-// Arithmetic of the substitutions is done in the factor's precision (AT = T):
-// with FP32 fronts every solve is the correction solve of mixed-precision
-// iterative refinement, whose residual and update are formed in FP64 outside.
-
-// Inverse X = L_bb^{-1} of every SB x SB unit-lower diagonal block of the
-// factor, stored as a dense row-major w x w block (unit diagonal, zeros
-// above) in the store's inverse array.  One CTA per block, thread c
-// computes column c of X by forward substitution (no cross-thread
-// dependency).  Run once per level after its factorization, so that every
-// later solve replaces the sequential triangular solve of a block by a
-// matrix-vector product read with vector loads.
-template <typename T>
-__global__ void __launch_bounds__(SB) k_diag_inverse(DevSym d, SV sv, const int32_t *__restrict__ fronts) {
-  extern __shared__ unsigned char inv_raw[];
-  T(*A)[SB + 1] = reinterpret_cast<T(*)[SB + 1]>(inv_raw);  // A[t][i] = L(t, i) (i < t), A[c][t] = X(t, c) (t > c)
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  const int k = blockIdx.x * SB;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(SB, ns - k);
-  T *F = (T *)sv.F + sv.front_off[s];
-  const int c = threadIdx.x;
-  for (int i = 0; i < w; ++i)
-    if (c > i && c < w) A[c][i] = F[(int64_t)(k + c) + (int64_t)(k + i) * f];
-  __syncthreads();
-  if (c < w) {
-    for (int t = c + 1; t < w; ++t) {
-      T acc = A[t][c];
-      for (int i = c + 1; i < t; ++i) acc += A[t][i] * A[c][i];
-      A[c][t] = -acc;
-    }
-  }
-  __syncthreads();
-  T *X = (T *)sv.Xinv + sv.xinv_off[s] + (int64_t)blockIdx.x * SB * SB;
-  for (int j = 0; j < w; ++j)  // row j, the threads along its columns c
-    if (c < w) X[(int64_t)j * w + c] = c < j ? A[c][j] : (c == j ? T(1) : T(0));
-}
-
-// loads X = L_bb^{-1} of the block at k (block index k / SB) as U[j][i] =
-// X(j, i): the dense row-major block is read as 16-byte vectors, 8 per thread
-// in flight (one round trip for a 128 x 128 FP32 block and 512 threads)
-template <typename T, typename AT>
-__device__ __forceinline__ void load_block_inverse(const SV &sv, int s, int k, int w, AT (*U)[SB + 1]) {
-  const T *X = (const T *)sv.Xinv + sv.xinv_off[s] + (int64_t)(k / SB) * SB * SB;
-  constexpr int VE = 16 / sizeof(T);  // elements per vector
-  constexpr int NV = 8;               // vectors in flight per thread
-  const int nv = (w * w + VE - 1) / VE;
-  for (int base = threadIdx.x; base < nv; base += NV * blockDim.x) {
-    T v[NV][VE];
-#pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int q = base + u * blockDim.x;
-      if (q < nv) {
-        if constexpr (sizeof(T) == 4) {
-          const float4 t = reinterpret_cast<const float4 *>(X)[q];
-          v[u][0] = t.x; v[u][1] = t.y; v[u][2] = t.z; v[u][3] = t.w;
-        } else {
-          const double2 t = reinterpret_cast<const double2 *>(X)[q];
-          v[u][0] = t.x; v[u][1] = t.y;
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int q = base + u * blockDim.x;
-      if (q >= nv) continue;
-#pragma unroll
-      for (int e = 0; e < VE; ++e) {
-        const int idx = q * VE + e;
-        if (idx < w * w) U[idx / w][idx % w] = (AT)v[u][e];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Dataflow substitutions.  The forward (backward) substitution of a level is
-// one launch with one CTA per item of the level's schedule: a 128-row band of
-// a front (forward) or a 128-column block (backward).  A CTA takes its item by
-// ticket, so every item it depends on belongs to a CTA that started before
-// it; it streams its part of the factor while waiting, bounded, for the
-// values of the blocks it depends on, and publishes its own block's values
-// for the CTAs after it.  The sequential chain of 128-wide blocks thus costs
-// one publish-and-observe latency per block instead of a kernel launch.
-
-constexpr int SBT = 4 * SB;                          // threads of a substitution CTA
-constexpr long long SOLVE_WAIT_CYCLES = 1ll << 31;  // ~1 s at 2 GHz
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ bool timed_out(const int *status) {
-  return (*(volatile const int *)status & DEV_TIMEOUT) != 0;
-}
-
-// compensated (Kahan) running sum in the substitution's precision
-template <typename AT>
-__device__ __forceinline__ void kahan_add(AT &sum, AT &comp, AT x) {
-  const AT y = x - comp;
-  const AT t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
-template <typename AT>
-struct SolveShared {
-  AT xs[2][SB];       // values of the block being consumed (double-buffered)
-  AT dp[4][SB];       // per-quarter (per-column) compensated sums
-  AT ap[4][SB];       // per-quarter partial block products
-  AT rb[SB];          // right-hand side of the own block
-  AT yb[SB];          // the own block's values
-  int item, abort;
-};
-
-// publishes the w values of the block at pivot position p under tag (thread
-// t < w holds value t); every thread calls it
-template <typename T>
-__device__ __forceinline__ void publish_block(const SV &sv, int64_t p, int w, unsigned tag, T val) {
-  const int t = threadIdx.x;
-  if constexpr (sizeof(T) == 4) {
-    if (t < w) st_relaxed_u64(sv.pub + p + t, ((unsigned long long)tag << 32) | __float_as_uint(val));
-  } else {
-    if (t < w) reinterpret_cast<double *>(sv.pub)[p + t] = val;
-    __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      st_release_u32(sv.pflag + p, tag);
-    }
-  }
-}
-
-// waits for the block at pivot position p published under tag and copies its
-// w values to dst[0, w) (zeros up to SB); every thread calls it, and it ends
-// with a barrier.  False (DEV_TIMEOUT recorded) when the wait bound expires
-// or another CTA already gave up.
-template <typename T>
-__device__ __forceinline__ bool wait_block(const SV &sv, int64_t p, int w, unsigned tag, T *dst, int *status,
-                                           int *abort) {
-  const int t = threadIdx.x;
-  if constexpr (sizeof(T) == 4) {
-    if (t < w) {
-      const unsigned long long *a = sv.pub + p + t;
-      unsigned long long v = ld_relaxed_u64(a);
-      if ((unsigned)(v >> 32) != tag) {
-        const long long t0 = clock64();
-        for (int n = 1; (unsigned)((v = ld_relaxed_u64(a)) >> 32) != tag; ++n) {
-          if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
-            atomicOr(status, DEV_TIMEOUT);
-            *abort = 1;
-            break;
-          }
-        }
-      }
-      dst[t] = __uint_as_float((unsigned)v);
-    } else if (t < SB) {
-      dst[t] = 0.f;
-    }
-  } else {
-    if (t == 0 && ld_acquire_u32(sv.pflag + p) != tag) {
-      const long long t0 = clock64();
-      for (int n = 1; ld_acquire_u32(sv.pflag + p) != tag; ++n) {
-        if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
-          atomicOr(status, DEV_TIMEOUT);
-          *abort = 1;
-          break;
-        }
-      }
-    }
-    __syncthreads();
-    if (t < w) dst[t] = __ldcg(reinterpret_cast<const double *>(sv.pub) + p + t);
-    else if (t < SB) dst[t] = 0.0;
-  }
-  __syncthreads();
-  return *abort == 0;
-}
-
-// item ticket and completion: the last CTA of a launch resets the counters
-// for the next launch of the same store
-template <typename AT>
-__device__ __forceinline__ bool solve_item_begin(unsigned *ctl, int *status, SolveShared<AT> &sm) {
-  if (threadIdx.x == 0) {
-    sm.item = (int)atomicAdd(&ctl[1], 1u);
-    sm.abort = 0;
-    if (sm.item >= (int)gridDim.x) {  // counters not reset by the previous launch
-      atomicOr(status, DEV_TIMEOUT);
-      sm.abort = 1;
-    } else if (timed_out(status)) {
-      sm.abort = 1;
-    }
-  }
-  __syncthreads();
-  return sm.abort == 0;
-}
-
-__device__ __forceinline__ void solve_item_end(unsigned *ctl) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&ctl[2], 1u) == gridDim.x - 1) {
-      atomicExch(&ctl[1], 0u);
-      atomicExch(&ctl[2], 0u);
-    }
-  }
-}
-
-// a new solve: new tags (2e forward, 2e + 1 backward), counters cleared
-__global__ void k_solve_begin(unsigned *ctl) {
-  ctl[0] += 1u;
-  ctl[1] = 0u;
-  ctl[2] = 0u;
-}
-
-// Forward item: rows [r0, r0 + nr) of front s.  Thread (row, quarter qq)
-// accumulates sum_j L(row, block j) y_j over its 32 columns of every own
-// block j the band depends on.  A struct band subtracts the sums from its
-// right-hand side (read by the parent's gather); own band b forms r_b =
-// P rhs_b - sums, y_b = X_b r_b with X_b = L_bb^{-1}, publishes y_b and writes
-// z_b = D_b^{-1} y_b.
-template <typename T>
-__device__ __forceinline__ void fwd_item(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
-                                         SolveItem itm, int nb, unsigned tag, int *status, T (*U)[SB + 1],
-                                         SolveShared<T> &sm) {
-  using AT = T;
-  const int s = lvl_fronts[itm.q];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  const int f = front_order(d, s, dpn);
-  const int nbo = (ns + SB - 1) / SB;
-  const bool own = itm.key < nbo;
-  const int r0 = own ? itm.key * SB : ns + (itm.key - nbo) * SB;
-  const int nr = min(SB, (own ? ns : f) - r0);  // an own band ends at the last own row
-  const int ndep = own ? itm.key : nbo;
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const int64_t po = sv.piv_off[s];
-  const int tid = threadIdx.x, row = tid & (SB - 1), qq = tid >> 7;
-  if (own) load_block_inverse<T, AT>(sv, s, r0, nr, U);
-  AT sum = AT(0), comp = AT(0);
-  for (int j = 0; j < ndep; ++j) {
-    const int kc = j * SB, wc = min(SB, ns - kc);
-    const T *Fc = F + (int64_t)(kc + 32 * qq) * f + r0 + row;
-    T v[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) v[u] = (row < nr && 32 * qq + u < wc) ? Fc[(int64_t)u * f] : T(0);
-    AT *y = sm.xs[j & 1];
-    if (!wait_block<T>(sv, po + kc, wc, tag, y, status, &sm.abort)) return;
-    AT a = AT(0);
-#pragma unroll
-    for (int u = 0; u < 32; ++u) a += (AT)v[u] * y[32 * qq + u];
-    kahan_add(sum, comp, a);
-  }
-  // partial sums are joined in the factor's precision; FP64 (slow on this
-  // part) only for the one subtraction per row from the FP64 right-hand side
-  sm.dp[qq][row] = sum - comp;
-  __syncthreads();
-  if (!own) {
-    if (tid < nr) {
-      double *rhs = sv.rhs + sv.rhs_off[s];
-      rhs[r0 + tid] -= (double)((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid]));
-    }
-    return;
-  }
-  const int w = nr;
-  if (tid < SB) {
-    AT r = AT(0);
-    if (tid < w) {
-      // the factor's rows are in final pivoted order; the pivots permute
-      // positions inside their panel of nb columns
-      const int pos = r0 + tid, pstart = (pos / nb) * nb;
-      const double b = sv.rhs[sv.rhs_off[s] + pstart + sv.piv_perm[po + pos]];
-      r = (AT)(b - (double)((sm.dp[0][tid] + sm.dp[1][tid]) + (sm.dp[2][tid] + sm.dp[3][tid])));
-    }
-    sm.rb[tid] = r;
-  }
-  __syncthreads();
-  {
-    AT a = AT(0);
-    const int i1 = min(32 * qq + 32, row);
-    for (int i = 32 * qq; i < i1; ++i) a += U[row][i] * sm.rb[i];
-    sm.ap[qq][row] = a;
-  }
-  __syncthreads();
-  AT y = AT(0);
-  if (tid < w) {
-    y = sm.rb[tid] + ((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
-    sm.yb[tid] = y;
-  }
-  publish_block<T>(sv, po + r0, w, tag, y);
-  __syncthreads();
-  if (tid < w) {
-    const int64_t p = po + r0 + tid;
-    const int ty = sv.piv_type[p];
-    if (ty == 0) {
-      sv.yz[p] = (double)y / sv.D0[p];
-    } else if (ty == 1) {
-      const double d11 = sv.D0[p], d21 = sv.D1[p], d22 = sv.D0[p + 1];
-      const double det = d11 * d22 - d21 * d21;
-      const double y1 = (double)y, y2 = (double)sm.yb[tid + 1];
-      sv.yz[p] = (d22 * y1 - d21 * y2) / det;
-      sv.yz[p + 1] = (d11 * y2 - d21 * y1) / det;
-    }
-  }
-  if (nbo > 1) return;
-  // a single-block front has no struct-band items: this CTA updates its
-  // struct rows' right-hand side with y_b from shared memory, 128 rows a pass
-  if (tid >= w && tid < SB) sm.yb[tid] = AT(0);
-  __syncthreads();
-  double *rhs = sv.rhs + sv.rhs_off[s];
-  for (int rs = ns; rs < f; rs += SB) {
-    const int nrs = min(SB, f - rs);
-    const T *Fc = F + (int64_t)(32 * qq) * f + rs + row;
-    T v[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) v[u] = (row < nrs && 32 * qq + u < w) ? Fc[(int64_t)u * f] : T(0);
-    AT a = AT(0);
-#pragma unroll
-    for (int u = 0; u < 32; ++u) a += (AT)v[u] * sm.yb[32 * qq + u];
-    sm.ap[qq][row] = a;
-    __syncthreads();
-    if (tid < nrs) rhs[rs + tid] -= (double)((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
-    k_fwd_level(DevSym d, SV sv, const int32_t *__restrict__ lvl_fronts, const SolveItem *__restrict__ items, int nb,
-                unsigned *ctl, int *status) {
-  extern __shared__ unsigned char blk_raw[];
-  __shared__ SolveShared<T> sm;
-  if (solve_item_begin(ctl, status, sm)) {
-    const unsigned tag = 2u * *(volatile unsigned *)ctl;
-    fwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, reinterpret_cast<T(*)[SB + 1]>(blk_raw), sm);
-  }
-  solve_item_end(ctl);
-}
-
-// Backward item: own block b = [k, k + w) of front s.  Warp wq owns columns
-// k + 8 wq .. + 8 with its lanes along the rows (coalesced) and accumulates
-// L(rows, column)^T x over the struct rows (x there is the ancestors'
-// solution) and over every later own block; v_b = z_b minus those sums gives
-// x_b = X_b^T v_b, which is published for the earlier blocks and written,
-// un-pivoted, into the solution.
-template <typename T>
-__device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
-                                         SolveItem itm, int nb, unsigned tag, int *status, double *__restrict__ sol,
-                                         T (*U)[SB + 1], SolveShared<T> &sm) {
-  using AT = T;
-  const int s = lvl_fronts[itm.q];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  const int f = front_order(d, s, dpn);
-  const int nbo = (ns + SB - 1) / SB;
-  const int b = nbo - 1 - itm.key;
-  const int k = b * SB, w = min(SB, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const int64_t po = sv.piv_off[s];
-  const int tid = threadIdx.x, row = tid & (SB - 1), qq = tid >> 7;
-  const int warp = tid >> 5, lane = tid & 31, c0 = 8 * warp;
-  load_block_inverse<T, AT>(sv, s, k, w, U);
-  AT sum[8], comp[8];
-#pragma unroll
-  for (int cc = 0; cc < 8; ++cc) sum[cc] = comp[cc] = AT(0);
-  int ph = 0;  // alternates the value buffers across both loops
-  // struct rows: the solution there (the ancestors') is final; gathered 128
-  // rows a pass
-  const int nown = d.sn_nown[s];
-  const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
-  // the struct-rank index of the next pass is read one pass ahead
-  int sidx = (tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
-  for (int rs = ns; rs < f; rs += SB, ++ph) {
-    const int nrs = min(SB, f - rs);
-    const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
-    T q[8][4];
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        q[cc][m] = (c0 + cc < w && lane + 32 * m < nrs) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
-    AT *x = sm.xs[ph & 1];
-    if (tid < SB) {
-      const int ii = rs + tid;
-      const int cur = sidx;
-      if (ii + SB < f) sidx = sr[(ii + SB) / dpn - nown];
-      x[tid] = tid < nrs ? (AT)sol[(int64_t)cur * dpn + ii % dpn] : AT(0);
-    }
-    __syncthreads();
-    AT xv[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) xv[m] = x[lane + 32 * m];
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      AT a = AT(0);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
-      kahan_add(sum[cc], comp[cc], a);
-    }
-  }
-  // later own blocks, as their values are published
-  for (int j = nbo - 1; j > b; --j, ++ph) {
-    const int kr = j * SB, wr = min(SB, ns - kr);
-    const T *Fc = F + (int64_t)(k + c0) * f + kr + lane;
-    T q[8][4];
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        q[cc][m] = (c0 + cc < w && lane + 32 * m < wr) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
-    AT *x = sm.xs[ph & 1];
-    if (!wait_block<T>(sv, po + kr, wr, tag, x, status, &sm.abort)) return;
-    AT xv[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) xv[m] = x[lane + 32 * m];
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      AT a = AT(0);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
-      kahan_add(sum[cc], comp[cc], a);
-    }
-  }
-#pragma unroll
-  for (int cc = 0; cc < 8; ++cc) {
-    AT t = sum[cc] - comp[cc];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sm.dp[0][c0 + cc] = t;
-  }
-  __syncthreads();
-  if (tid < SB) sm.rb[tid] = tid < w ? (AT)(sv.yz[po + k + tid] - (double)sm.dp[0][tid]) : AT(0);
-  __syncthreads();
-  {
-    AT a = AT(0);
-    const int j1 = min(32 * qq + 32, w);
-    for (int jj = max(32 * qq, row + 1); jj < j1; ++jj) a += U[jj][row] * sm.rb[jj];
-    sm.ap[qq][row] = a;
-  }
-  __syncthreads();
-  AT x = AT(0);
-  if (tid < w) x = sm.rb[tid] + ((sm.ap[0][tid] + sm.ap[1][tid]) + (sm.ap[2][tid] + sm.ap[3][tid]));
-  publish_block<T>(sv, po + k, w, tag, x);
-  if (tid < w) {
-    // piv_perm is local to the pivot panel (width nb) holding position k + tid
-    const int pos = k + tid, pstart = (pos / nb) * nb;
-    sol[(int64_t)d.sn_first[s] * dpn + pstart + sv.piv_perm[po + pos]] = (double)x;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
-    k_bwd_level(DevSym d, SV sv, const int32_t *__restrict__ lvl_fronts, const SolveItem *__restrict__ items, int nb,
-                unsigned *ctl, int *status, double *__restrict__ sol) {
-  extern __shared__ unsigned char blk_raw[];
-  __shared__ SolveShared<T> sm;
-  if (solve_item_begin(ctl, status, sm)) {
-    const unsigned tag = 2u * *(volatile unsigned *)ctl + 1u;
-    bwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, sol, reinterpret_cast<T(*)[SB + 1]>(blk_raw),
-                sm);
-  }
-  solve_item_end(ctl);
-}
-
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
                                const double *__restrict__ D1, unsigned long long *counters) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1368,8 +817,8 @@ void factor_impl(Ctx &c, Store &st) {
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
   unsigned long long *ctr = (unsigned long long *)c.counters;
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
-  // panel kernels compiled for 16, 32 and 64 columns
-  const int nbt = nb <= 16 ? 16 : (nb <= 32 ? 32 : 64);
+  // panel kernels compiled for 16 and 32 columns
+  const int nbt = nb <= 16 ? 16 : 32;
   const size_t rows_smem = (size_t)(32 * nbt + nbt * nbt + nbt * 129) * sizeof(T);
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, st.dpn);
@@ -1406,8 +855,7 @@ void factor_impl(Ctx &c, Store &st) {
           ProfScope ps(c, SGN_PROF_TRSM, fl);
           dim3 gp((max_rows + 127) / 128, na);
           if (nbt == 16) k_panel_rows<T, 16><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
-          else if (nbt == 32) k_panel_rows<T, 32><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
-          else k_panel_rows<T, 64><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
+          else k_panel_rows<T, 32><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
           c.count();
         }
       }
@@ -1447,42 +895,10 @@ void factor_impl(Ctx &c, Store &st) {
     }
     if (max_ns > 0) {
       ProfScope ps(c, SGN_PROF_SOLVE);
-      dim3 gi((max_ns + SB - 1) / SB, (unsigned)(li.f1 - li.f0));
-      k_diag_inverse<T><<<gi, SB, (size_t)SB * (SB + 1) * sizeof(T), c.stream>>>(c.ds, sv, fronts);
-      c.count();
+      launch_diag_inverse(c, st, fronts, max_ns, (int)(li.f1 - li.f0));
     }
   }
   st.factored = true;
-}
-
-template <typename T>
-void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
-  ProfScope ps(c, SGN_PROF_SOLVE);
-  SV sv = view(st);
-  const int nb = c.S.opts.panel;
-  const int dpn = st.dpn;
-  const size_t blk_smem = (size_t)SB * (SB + 1) * sizeof(T);
-  k_solve_begin<<<1, 1, 0, c.stream>>>(st.ctl);
-  c.count();
-  for (int L = 0; L < c.S.n_levels; ++L) {
-    const int64_t i0 = c.h_item_ptr[L], n = (c.h_item_ptr[L + 1] - i0) * dpn;
-    if (n > 0) {
-      k_fwd_gather<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.ds, sv, i0, n, b);
-      c.count();
-    }
-    const int64_t t0 = st.h_fwd_lvl[L], nt = st.h_fwd_lvl[L + 1] - t0;
-    if (nt == 0) continue;
-    k_fwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.fwd_items + t0, nb,
-                                                              st.ctl, c.status);
-    c.count();
-  }
-  for (int L = c.S.n_levels - 1; L >= 0; --L) {
-    const int64_t t0 = st.h_bwd_lvl[L], nt = st.h_bwd_lvl[L + 1] - t0;
-    if (nt == 0) continue;
-    k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb,
-                                                              st.ctl, c.status, x);
-    c.count();
-  }
 }
 
 }  // namespace
@@ -1509,32 +925,11 @@ cudaEvent_t *Ctx::prof_pair(int kind, double flops) {
   return p;
 }
 
-// one bounded wait on a block value that nothing publishes (tag 1 is never
-// used: solves use 2e and 2e + 1, e >= 1): it must give up and record
-// DEV_TIMEOUT in the status word
-template <typename T>
-__global__ void k_wait_selftest(SV sv, int *status) {
-  __shared__ SolveShared<T> sm;
-  if (threadIdx.x == 0) sm.abort = 0;
-  __syncthreads();
-  wait_block<T>(sv, 0, 1, 1u, sm.xs[0], status, &sm.abort);
-}
-
-void wait_selftest(Ctx &c, Store &s) {
-  SV sv = view(s);
-  if (s.fp32) k_wait_selftest<float><<<1, SB, 0, c.stream>>>(sv, c.status);
-  else k_wait_selftest<double><<<1, SB, 0, c.stream>>>(sv, c.status);
-}
-
 void factor_direct(Ctx &c, Store &s) {
   if (s.fp32) factor_impl<float>(c, s);
   else factor_impl<double>(c, s);
 }
 
-void solve_direct(Ctx &c, Store &s, const double *b, double *x) {
-  if (s.fp32) solve_impl<float>(c, s, b, x);
-  else solve_impl<double>(c, s, b, x);
-}
 
 void Ctx::harvest_graph_events() {
   if (!pending_events) return;
@@ -1611,43 +1006,15 @@ void factor_store(Ctx &c, Store &s) {
   s.factored = true;
 }
 
-void solve_store(Ctx &c, Store &s, const double *b, double *x) {
-  auto run = [&]() {
-    if (s.fp32) solve_impl<float>(c, s, b, x);
-    else solve_impl<double>(c, s, b, x);
-  };
-  if (!c.use_graphs || !c.cap_stream || c.prof_mask != 0) {
-    run();
-    return;
-  }
-  if (!s.sgraph || s.sgraph_b != b || s.sgraph_x != x) {
-    if (s.sgraph) cudaGraphExecDestroy(s.sgraph);
-    s.sgraph = capture(c, run, &s.sgraph_launches, nullptr);
-    s.sgraph_b = b;
-    s.sgraph_x = x;
-  }
-  if (!s.sgraph) { run(); return; }
-  cudaGraphLaunch(s.sgraph, c.stream);
-  c.launches += s.sgraph_launches;
-}
 
 void set_kernel_attributes() {
   static bool done = false;
   if (done) return;
   done = true;
-  cudaFuncSetAttribute(k_panel_rows<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)((32 * 64 + 64 * 64 + 64 * 129) * sizeof(double)));
-  cudaFuncSetAttribute(k_panel_rows<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)((32 * 64 + 64 * 64 + 64 * 129) * sizeof(float)));
   cudaFuncSetAttribute(k_panel_rows<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((32 * 32 + 32 * 32 + 32 * 129) * sizeof(double)));
   cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
-  cudaFuncSetAttribute(k_fwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_fwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-  cudaFuncSetAttribute(k_bwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_bwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-  cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  set_solve_attributes();
 }
 
 void destroy_graphs(Store &s) {

@@ -1,0 +1,71 @@
+// Internal to the multifrontal factorization (front.cu) and the
+// substitutions (solve.cu): the store view the kernels receive and the
+// addressing of a front's lower triangle.
+#pragma once
+
+#include "common.cuh"
+
+namespace sgn {
+
+struct SV {  // store view passed to kernels
+  void *F;                       // factor columns of every front (f x ns each)
+  void *CB;                      // contribution-block arena
+  void *Xinv;                    // diagonal-block inverses
+  void *W;
+  void *Ldg;                     // staged factored diagonal blocks (panel x panel per panel)
+  float *wk0, *wk1, *wk2, *wk3;  // K-major hi/lo copies (FP32 fronts with tensor cores)
+  double *rhs;
+  int32_t *piv_type, *piv_perm;
+  double *D0, *D1;
+  double *yz;                    // y, z = D^{-1} y, v of the substitutions (pivot order)
+  unsigned long long *pub;       // published block values of the substitutions
+  unsigned *pflag;               // their tags (FP64 fronts)
+  const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off, *xinv_off;
+  int dpn;
+  int kkt;
+};
+
+inline SV view(Store &s) {
+  SV v;
+  v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
+  v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz;
+  v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
+  v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
+  v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
+  return v;
+}
+
+__device__ __forceinline__ int front_order(const DevSym &d, int s, int dpn) {
+  return (d.sn_nown[s] + d.sn_nstruct[s]) * dpn;
+}
+
+// The lower triangle of front s (order f, ns fully-summed columns): columns
+// j < ns live in the front array (f x ns, column-major), the contribution
+// block (rows and columns >= ns) in the arena ((f - ns) x (f - ns)).
+template <typename T>
+struct FrontMat {
+  T *L, *C;
+  int64_t f, ns;
+  // element (i, j) of the lower triangle (i >= j)
+  __device__ __forceinline__ T *at(int64_t i, int64_t j) const {
+    return j < ns ? L + i + j * f : C + (i - ns) + (j - ns) * (f - ns);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ FrontMat<T> front_mat(const DevSym &d, const SV &sv, int s) {
+  FrontMat<T> m;
+  m.L = (T *)sv.F + sv.front_off[s];
+  m.C = (T *)sv.CB + sv.cb_off[s];
+  m.ns = (int64_t)d.sn_nown[s] * sv.dpn;
+  m.f = m.ns + (int64_t)d.sn_nstruct[s] * sv.dpn;
+  return m;
+}
+
+constexpr int SB = 128;  // solve block width (independent of the pivot panel width)
+
+// host-side launchers shared by the two translation units
+void launch_diag_inverse(Ctx &c, Store &st, const int32_t *fronts, int max_ns, int nfronts);
+void set_solve_attributes();
+
+}  // namespace sgn

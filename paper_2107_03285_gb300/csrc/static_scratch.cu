@@ -3,11 +3,13 @@
 //
 // Who needs this: code that may not allocate device memory at the point where
 // it assembles, e.g. a solver loop inside a real-time or memory-capped
-// service whose allocator is frozen, or a host that has handed all device
-// memory to another runtime, and that would rather not size or keep the
-// element-state part of the workspace itself.  The array below is a fixed
-// part of the library image: every GPU that loads libsgn.so holds it (16 MB)
-// until the process exits.
+// service whose allocator is frozen after start-up, or a host that has handed
+// all device memory to another runtime.  The array below is a fixed part of
+// the library's device image: every GPU that loads libsgn.so holds it (16 MB)
+// until the process exits.  Under CUDA's lazy module loading the array's
+// memory is taken when the module is first used; sgn_bind resolves the
+// array's address (static_scratch_bind below), so that happens at bind time,
+// where the caller provides memory anyway, and never inside an assembly.
 #include <cstdio>
 #include <mutex>
 
@@ -25,43 +27,63 @@ double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
+namespace sgn {
+
+// Called by sgn_bind with the handle's device current: looks up (once per
+// device) the device address of the array.  Host code must never use the
+// symbol itself as a pointer: on the host it names a stand-in object.
+cudaError_t static_scratch_bind(int device) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_ptr[device]) return cudaSuccess;
+  void *ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_assemble_scratch);
+  if (e != cudaSuccess) return e;
+  if (!ptr) return cudaErrorInvalidSymbol;
+  g_scratch_ptr[device] = static_cast<double *>(ptr);
+  return cudaSuccess;
+}
+
+}  // namespace sgn
+
 extern "C" sgn_status sgn_assemble_static(sgn_t h, const double *x_d, const double *p_d) {
-  if (!h || !x_d || !p_d) return SGN_EINVAL;
+  if (!h || !x_d || !p_d) {
+    sgn::set_error(nullptr, "sgn_assemble_static: null argument");
+    return SGN_EINVAL;
+  }
   sgn::Ctx &c = *h;
   if (!c.bound || !c.have_objective) return SGN_ESTATE;
   const int64_t need = (int64_t)(3 + (c.S.dim + 1) * c.S.dim) * c.S.n_elem;
   if (need > kStaticScratchDoubles) {
-    c.last_error = "sgn_assemble_static: mesh needs more element scratch than the 16 MB static array";
+    sgn::set_error(&c, "sgn_assemble_static: the mesh needs more element scratch than the 16 MB static array "
+                       "((3 + (dim+1) dim) n_elem must be <= 2^21 doubles)");
     return SGN_EINVAL;
   }
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SGN_ECUDA;
   double *scratch = nullptr;
   {
-    // first call on this device (with it current): resolve the device address
-    // of the array; host code must not use the symbol itself as a pointer
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      void *ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_assemble_scratch);
-      if (e != cudaSuccess || !ptr) {
-        c.last_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-        return SGN_ECUDA;
-      }
-      g_scratch_ptr[dev] = static_cast<double *>(ptr);
-    }
-    scratch = g_scratch_ptr[dev];
+    scratch = (c.device >= 0 && c.device < kMaxDevices) ? g_scratch_ptr[c.device] : nullptr;
+  }
+  if (!scratch) {  // sgn_bind resolves it; without that the handle is not usable here
+    sgn::set_error(&c, "sgn_assemble_static: the static array's address was not resolved at sgn_bind");
+    return SGN_ESTATE;
   }
   // the element state is written for every element before it is read, so
   // nothing in the array needs clearing between calls
-  sgn::launch_elem_state_into(c, x_d, p_d, scratch);
-  sgn::launch_slot_gather_from(c, scratch);
-  sgn::launch_objective_terms(c, x_d, p_d);
+  {
+    sgn::ProfScope ps(c, SGN_PROF_ELEMENTS);
+    sgn::launch_elem_state_into(c, x_d, p_d, scratch);
+    sgn::launch_slot_gather_from(c, scratch);
+  }
+  {
+    sgn::ProfScope ps(c, SGN_PROF_VECTOR);
+    sgn::launch_objective_terms(c, x_d, p_d);
+  }
   c.assembled = true;
   c.kkt64.factored = c.kkt32.factored = c.kf.factored = c.kf32.factored = false;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    c.last_error = std::string("kernel launch: ") + cudaGetErrorString(e);
+    sgn::set_error(&c, std::string("sgn_assemble_static: kernel launch: ") + cudaGetErrorString(e));
     return SGN_ECUDA;
   }
   return SGN_OK;

@@ -150,9 +150,9 @@ std::string analyze(int dim, int n_nodes, int n_elem, const double *X, const int
   SymbolicOptions opts = opts_in;
   if (opts.leaf_nodes <= 0) opts.leaf_nodes = 16;
   if (opts.panel <= 0) opts.panel = 32;
-  // panels tile the 256-column outer blocks exactly: 8, 16, 32 or 64
-  if (opts.panel != 8 && opts.panel != 16 && opts.panel != 32 && opts.panel != 64)
-    return "panel must be 8, 16, 32 or 64";
+  // panels tile the 256-column outer blocks exactly: 8, 16 or 32
+  if (opts.panel != 8 && opts.panel != 16 && opts.panel != 32)
+    return "panel must be 8, 16 or 32";
   const int nv = dim + 1;
   S = Symbolic();
   S.dim = dim; S.n_nodes = n_nodes; S.n_elem = n_elem; S.opts = opts;

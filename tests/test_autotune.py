@@ -17,10 +17,10 @@ def _table(leaf, panel):
 
 def test_candidates_cover_the_grid_and_skip_tiny_leaves():
     c2 = A.candidates(2)
-    assert (16, 32) in c2 and (64, 64) in c2
+    assert (16, 32) in c2 and (64, 32) in c2
     assert all(p in A.PANELS and l in A.LEAVES for l, p in c2)
     # a leaf front of fewer than half a panel of unknowns is not a candidate
-    assert A.candidates(2, panels=(64,), leaves=(4, 8)) == [(8, 64)]
+    assert A.candidates(2, panels=(32,), leaves=(2, 4)) == [(4, 32)]
 
 
 def test_choose_picks_the_fastest_and_breaks_ties_by_order():

@@ -149,7 +149,7 @@ def test_paper_rhs_and_multiplier_shift(sgnmod):
     assert _rel((dlk - dlp).cpu().numpy(), lam) < 1e-9
 
 
-@pytest.mark.parametrize("panel,leaf", [(8, 4), (16, 64), (64, 8)])
+@pytest.mark.parametrize("panel,leaf", [(8, 4), (16, 64), (32, 8)])
 def test_panel_and_leaf_sizes(sgnmod, panel, leaf):
     c = case("kuhn3d_7")
     s = make(sgnmod, c, panel=panel, leaf_nodes=leaf)

@@ -1,7 +1,10 @@
 """sgn_assemble_static: the assembly entry point whose per-element scratch is a
-fixed device array inside the library (for callers that cannot allocate that
-workspace).  Its output must equal sgn_assemble's, call after call, since all
-calls share the array.  Kept in a file that pytest collects last."""
+fixed device array inside the library, for callers that must not allocate
+device memory (or have the runtime set any up) while they assemble, such as
+a service whose allocator is frozen after start-up.  Its output must equal
+sgn_assemble's, call after call, since all calls share the array; and a call
+must leave the device's free memory unchanged (the array is set up at
+sgn_bind).  Kept in a file that pytest collects last."""
 import ctypes as C
 
 import numpy as np
@@ -66,10 +69,29 @@ def test_static_scratch_assembly_matches_sgn_assemble(P, which):
     s.close()
 
 
+def test_static_scratch_call_allocates_nothing(P):
+    """Device free memory (cudaMemGetInfo) is the same before and after two
+    calls: the array was set up when the handle was bound."""
+    prob = problem_3d(9, seed=6, p_sigma=0.1)
+    s = P.SGN.from_problem(prob, stores=P.STORE_FP64)
+    xd = torch.as_tensor(prob.X, device="cuda")
+    pd = torch.as_tensor(prob.p0, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert _static(s, xd, pd) == P.binding.OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    s.close()
+
+
 def test_static_scratch_rejects_meshes_beyond_its_limit(P):
     prob = problem_3d(30)  # 146,334 tets > 139,810
     s = P.SGN.from_problem(prob, stores=0)
     xd = torch.as_tensor(prob.X, device="cuda")
     pd = torch.as_tensor(prob.p0, device="cuda")
-    assert _static(s, xd, pd) == P.binding.EINVAL
+    code = _static(s, xd, pd)
+    assert code == P.binding.EINVAL
+    assert "16 MB" in s.lib.sgn_strerror(code).decode()
     s.close()
