@@ -100,6 +100,9 @@ typedef struct {
 typedef struct {
   int32_t leaf_nodes;        /* nested dissection stops at <= leaf_nodes nodes (0: 16) */
   int32_t panel;             /* pivot panel width: 8, 16 or 32 (0: 32) */
+  int32_t update_ctas;       /* CTAs of one tensor-core trailing-update launch, shared by the
+                                level's active fronts; each CTA loops over its tiles
+                                (0: one per SM) */
 } sgn_setup_opts;
 
 /* Least-squares objective (host arrays, copied by sgn_set_objective). */
@@ -147,9 +150,11 @@ typedef struct {
 
 typedef struct {
   int32_t max_iter;               /* default 0 -> 50 */
-  double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10); a residual a Newton
-                                     step no longer halves also counts once below 1e-7 ||f_ext||
-                                     (the round-off floor of c grows with the mesh) */
+  double tol;                     /* ||c|| <= tol ||f_ext|| (default 0 -> 1e-10).  The iterate is the
+                                     displacement x - X, so the round-off floor of ||c|| does not
+                                     depend on where the body sits (measured: 1.3e-11 ||f_ext|| on a
+                                     60 x 60 grid); for a tol below the floor, a residual a Newton
+                                     step no longer halves also counts once below 1e-10 ||f_ext|| */
   int32_t precision;              /* SGN_FP64 (default): K factored in FP64 (SGN_STORE_KFACT);
                                      SGN_MIXED: K factored with FP32 fronts on the tensor cores
                                      (SGN_STORE_KFACT_MIXED) and every Newton direction refined

@@ -13,6 +13,12 @@ In 2D the same formula with 2x2 F is plane strain with unit thickness.
 
 Element kinematics: D_m = [X_1 - X_0, ..., X_d - X_0] (columns), vol =
 |det D_m| / d!, D_s likewise from the deformed positions, F = D_s D_m^{-1}.
+With displacements u = x - X the same F reads F = I + D_u D_m^{-1}
+(D_s = D_m + D_u); every element function accepts either positions x or,
+through the keyword u, displacements.  The displacement form keeps the
+round-off of F independent of where the body sits: an absolute position
+carries a representation error of about eps |x|, a displacement one of
+eps |u| (the forward simulation iterates on u for that reason).
 Writing F_ij = sum_a x_{a,i} B_{a,j} defines the shape-function gradients
 B (B_a = row a-1 of D_m^{-1} for a >= 1, B_0 = -sum_a B_a).
 
@@ -52,6 +58,17 @@ def deformation_gradient(x, conn, Dminv):
     return Ds @ Dminv
 
 
+def deformation_gradient_disp(u, conn, Dminv):
+    """F = I + D_u D_m^{-1} from node displacements u (x = X + u)."""
+    d = Dminv.shape[1]
+    Du = np.stack([u[conn[:, a]] - u[conn[:, 0]] for a in range(1, d + 1)], axis=2)
+    return np.eye(d)[None] + Du @ Dminv
+
+
+def _F(x, u, conn, Dminv):
+    return deformation_gradient(x, conn, Dminv) if u is None else deformation_gradient_disp(u, conn, Dminv)
+
+
 def energy_density(F, mu, lam):
     d = F.shape[1]
     J = np.linalg.det(F)
@@ -81,36 +98,36 @@ def piola_tangent(F, mu, lam):
     return T
 
 
-def element_energy(x, X, conn, E, nu):
-    """vol_e Psi(F_e) per element."""
+def element_energy(x, X, conn, E, nu, u=None):
+    """vol_e Psi(F_e) per element (positions x, or displacements u)."""
     Dminv, vol, _ = rest_geometry(X, conn)
-    F = deformation_gradient(x, conn, Dminv)
+    F = _F(x, u, conn, Dminv)
     mu, lam = lame(E, nu)
     return vol * energy_density(F, mu, lam)
 
 
-def element_force(x, X, conn, E, nu):
+def element_force(x, X, conn, E, nu, u=None):
     """Gradient of vol Psi w.r.t. the element's node positions,
     (n_e, d+1, d): f_{a,k} = vol sum_j P_kj B_aj."""
     _, vol, B = rest_geometry(X, conn)
     Dminv = B[:, 1:, :]
-    F = deformation_gradient(x, conn, Dminv)
+    F = _F(x, u, conn, Dminv)
     mu, lam = lame(E, nu)
     P = first_piola(F, mu, lam)
     return vol[:, None, None] * np.einsum("ekj,eaj->eak", P, B)
 
 
-def element_hessian(x, X, conn, E, nu):
+def element_hessian(x, X, conn, E, nu, u=None):
     """Hessian of vol Psi w.r.t. the element's node positions,
     (n_e, d+1, d, d+1, d): K[a,m,b,n] = vol sum_jl B_aj dP_mj/dF_nl B_bl."""
     _, vol, B = rest_geometry(X, conn)
     Dminv = B[:, 1:, :]
-    F = deformation_gradient(x, conn, Dminv)
+    F = _F(x, u, conn, Dminv)
     mu, lam = lame(E, nu)
     T = piola_tangent(F, mu, lam)
     return vol[:, None, None, None, None] * np.einsum("eaj,emjnl,ebl->eambn", B, T, B)
 
 
-def element_jacobian_det(x, X, conn):
+def element_jacobian_det(x, X, conn, u=None):
     Dminv, _, _ = rest_geometry(X, conn)
-    return np.linalg.det(deformation_gradient(x, conn, Dminv))
+    return np.linalg.det(_F(x, u, conn, Dminv))

@@ -55,6 +55,15 @@ def positions_from_free(prob, xf):
     return x.reshape(prob.X.shape)
 
 
+def displacements_from_free(prob, uf):
+    """Full node displacements: free DOFs from uf, fixed nodes zero."""
+    g2f = free_dof_map(prob)
+    u = np.zeros(prob.X.size, dtype=uf.dtype)
+    m = g2f >= 0
+    u[m] = uf[g2f[m]]
+    return u.reshape(prob.X.shape)
+
+
 def free_from_positions(prob, x):
     g2f = free_dof_map(prob)
     xf = np.empty(int(np.count_nonzero(g2f >= 0)), dtype=x.dtype)
@@ -75,18 +84,22 @@ def moduli(prob, p):
     return prob.E0 * np.exp(p)
 
 
-def potential(prob, x, p):
+def potential(prob, x, p, u=None):
     """Pi(x; p) = sum_e vol_e Psi(F_e) - f_ext . x (fixed nodes contribute
-    a constant)."""
+    a constant).  Given displacements u (x = X + u) instead, the constant
+    f_ext . X is left out: Pi = sum_e vol_e Psi(F_e) - f_ext . u."""
     E = moduli(prob, p)
+    if u is not None:
+        W = el.element_energy(None, prob.X, prob.conn, E, prob.nu, u=u)
+        return W.sum() - np.sum(prob.fext * u)
     W = el.element_energy(x, prob.X, prob.conn, E, prob.nu)
     return W.sum() - np.sum(prob.fext * x)
 
 
-def internal_force(prob, x, p):
-    """Assembled f_int over free DOFs."""
+def internal_force(prob, x, p, u=None):
+    """Assembled f_int over free DOFs (at positions x, or displacements u)."""
     E = moduli(prob, p)
-    fe = el.element_force(x, prob.X, prob.conn, E, prob.nu).reshape(prob.n_elem, -1)
+    fe = el.element_force(x, prob.X, prob.conn, E, prob.nu, u=u).reshape(prob.n_elem, -1)
     dofs = element_dofs(prob)
     n_x = prob.n_free * prob.dim
     out = np.zeros(n_x, dtype=fe.dtype)
@@ -95,15 +108,15 @@ def internal_force(prob, x, p):
     return out
 
 
-def constraint(prob, x, p):
+def constraint(prob, x, p, u=None):
     """c(x, p) = f_int(x, p) - f_ext on the free DOFs (Eq. optProb)."""
-    return internal_force(prob, x, p) - free_from_positions(prob, prob.fext)
+    return internal_force(prob, x, p, u=u) - free_from_positions(prob, prob.fext)
 
 
-def stiffness(prob, x, p):
+def stiffness(prob, x, p, u=None):
     """K = dc/dx (sparse, free DOFs)."""
     E = moduli(prob, p)
-    He = el.element_hessian(x, prob.X, prob.conn, E, prob.nu)
+    He = el.element_hessian(x, prob.X, prob.conn, E, prob.nu, u=u)
     nd = (prob.dim + 1) * prob.dim
     He = He.reshape(prob.n_elem, nd, nd)
     dofs = element_dofs(prob)

@@ -41,7 +41,7 @@ class Mesh(C.Structure):
 
 
 class SetupOpts(C.Structure):
-    _fields_ = [("leaf_nodes", C.c_int32), ("panel", C.c_int32)]
+    _fields_ = [("leaf_nodes", C.c_int32), ("panel", C.c_int32), ("update_ctas", C.c_int32)]
 
 
 class Objective(C.Structure):

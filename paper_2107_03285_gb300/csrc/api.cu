@@ -21,6 +21,12 @@ namespace {
 
 thread_local std::string g_err;
 
+// Newton equilibrium: a residual that a full-accuracy step no longer halves
+// counts as converged once below this fraction of ||f_ext||.  Measured floors
+// of ||c|| / ||f_ext|| with the displacement iterate: 1.3e-11 (60 x 60 grid),
+// 8.5e-12 (40 x 40), below 1e-13 on the 3D cubes.
+constexpr double kStagnationCap = 1e-10;
+
 #define CUDA_TRY(h, call)                                                   \
   do {                                                                      \
     cudaError_t _e = (call);                                                \
@@ -247,7 +253,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
 #define UP64(field, vec) do { int64_t *p_; st_up(p_, vec); ds.field = p_; } while (0)
   (void)cp; (void)cd; (void)c64;
   UP32(elem_node, S.elem_node); UP32(elem_rank, S.elem_rank);
-  UPD(elem_B, S.elem_B); UPD(elem_vol, S.elem_vol);
+  UPD(elem_B, S.elem_B); UPD(elem_vol, S.elem_vol); UPD(X, S.X);
   UP32(node_rank, S.node_rank); UP32(rank_node, S.rank_node);
   UP32(bsr_ptr, S.bsr_ptr); UP32(bsr_col, S.bsr_col); UP32(bsr_orig_pos, S.bsr_orig_pos);
   UP32(up_slot, S.up_slot); UP32(up_slot_t, S.up_slot_t); UP32(up_ptr, S.up_ptr); UP32(up_contrib, S.up_contrib);
@@ -279,7 +285,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.counters = cv.take<int64_t>(8);
   const size_t nn = (size_t)S.n_nodes * d;
   c.eq = cv.take<double>(4 * nx);
-  c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx);
+  c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx); c.ueq = cv.take<double>(nn);
   c.hx = cv.take<double>(nn); c.hdx = cv.take<double>(nn); c.hdl = cv.take<double>(nn);
   c.hp = cv.take<double>(ne); c.hdp = cv.take<double>(ne);
   bool plan_ok = true;
@@ -435,6 +441,7 @@ sgn_status sgn_setup(const sgn_mesh *mesh, const sgn_setup_opts *opts, sgn_t *ou
   if (!h) return SGN_ENOMEM;
   SymbolicOptions so;
   if (opts) { so.leaf_nodes = opts->leaf_nodes; so.panel = opts->panel; }
+  if (opts && opts->update_ctas < 0) { g_err = "update_ctas must be >= 0"; delete h; return SGN_EINVAL; }
   if (so.leaf_nodes <= 0) so.leaf_nodes = 16;
   if (so.panel <= 0) so.panel = 32;
   if (!(mesh->nu > -1.0 && mesh->nu < 0.5) || !(mesh->E0 > 0.0)) {
@@ -455,6 +462,7 @@ sgn_status sgn_setup(const sgn_mesh *mesh, const sgn_setup_opts *opts, sgn_t *ou
     return SGN_EINVAL;
   }
   h->E0 = mesh->E0; h->nu = mesh->nu;
+  h->update_ctas = opts ? opts->update_ctas : 0;
   *out = h;
   return SGN_OK;
 }
@@ -928,34 +936,40 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
   const int64_t nx = (int64_t)c.S.n_free * d, nn = (int64_t)c.S.n_nodes * d;
   const int max_iter = opts && opts->max_iter > 0 ? opts->max_iter : 50;
   const double tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
+  // The iterate is the displacement u = x - X (node-major, in c.ueq): F is
+  // formed from it, so the round-off floor of ||c|| does not depend on where
+  // the body sits (an absolute position carries eps |x| of representation
+  // error, which alone floors ||c|| at a few 1e-10 ||f_ext|| here).
   double *fr = c.eq, *cr = fr + nx, *dxr = cr + nx, *tmp = dxr + nx;
-  double *xsave = c.xsave, *xr_tmp = c.xrt;
+  double *usave = c.xsave, *ur_tmp = c.xrt, *u = c.ueq;
   launch_from_nodes(c, fext_d, fr);
+  launch_shift_rest(c, x_d, -1.0, u);
   const double fnorm = std::sqrt(device_sumsq3(c, fr, nx, nullptr, 0, nullptr, 0));
   const double scale = fnorm > 0 ? fnorm : 1.0;
-  auto potential = [&](const double *x, bool *valid) -> double {
+  // Pi(u) = sum_e vol_e Psi(F_e) - f_ext . u  (the constant f_ext . X left out)
+  auto potential = [&](const double *uu, bool *valid) -> double {
     int nbk = energy_blocks(c);
-    launch_energy_partials(c, x, p_d, c.partial, nbk);
+    launch_energy_partials(c, uu, p_d, c.partial, nbk, true);
     std::vector<double> hp(nbk);
     cudaMemcpyAsync(hp.data(), c.partial, nbk * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
     cudaStreamSynchronize(c.stream);
     double e = 0.0;
     for (double v : hp) e += v;
     *valid = std::isfinite(e);
-    launch_from_nodes(c, x, xr_tmp);
-    double w = device_dot(c, fr, xr_tmp, nx);
+    launch_from_nodes(c, uu, ur_tmp);
+    double w = device_dot(c, fr, ur_tmp, nx);
     return e - w;
   };
-  auto residual = [&](const double *x) -> double {
-    launch_elem_state(c, x, p_d);
+  auto residual = [&](const double *uu) -> double {
+    launch_elem_state_disp(c, uu, p_d);
     launch_internal_force(c, cr);
     launch_axpy(c, cr, fr, -1.0, nx);
     return std::sqrt(device_sumsq3(c, cr, nx, nullptr, 0, nullptr, 0));
   };
   bool valid = true;
-  double Pi = potential(x_d, &valid);
+  double Pi = potential(u, &valid);
   if (!valid) { c.last_error = "initial guess has an inverted element"; return SGN_EINVERTED; }
-  double cn = residual(x_d);
+  double cn = residual(u);
   double init = cn / scale;
   int it = 0, solves = 0;
   bool conv = false, dir_ok = true;
@@ -963,17 +977,18 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
   double hist[32] = {0}, tstep[32] = {0};
   for (;; ++it) {
     if (it < 32) hist[it] = cn / scale;
-    // converged, or stagnating at the round-off floor of ||c|| (a full-accuracy
-    // Newton step no longer halves it and it is already below 1e-7 ||f_ext||)
-    if (cn <= tol * scale || (dir_ok && cn_prev > 0 && cn > 0.5 * cn_prev && cn <= 1e-7 * scale)) {
+    // converged, or (for a tolerance below the round-off floor) stagnating:
+    // a full-accuracy Newton step no longer halves ||c|| and it is already
+    // below kStagnationCap ||f_ext||
+    if (cn <= tol * scale || (dir_ok && cn_prev > 0 && cn > 0.5 * cn_prev && cn <= kStagnationCap * scale)) {
       conv = true;
       break;
     }
     cn_prev = cn;
     if (it >= max_iter) break;
-    // Newton direction: K dx = -c.  Every solve goes through (c.rx -> c.zx)
+    // Newton direction: K du = -c.  Every solve goes through (c.rx -> c.zx)
     // so that the captured substitution graph is reused; with FP32 fronts the
-    // direction is refined against the FP64 K until ||K dx + c|| <= eta ||c||
+    // direction is refined against the FP64 K until ||K du + c|| <= eta ||c||
     launch_slot_gather(c, false);
     c.assembled = true;
     factor_store(c, kst);
@@ -995,35 +1010,36 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
       }
     }
     double slope = device_dot(c, cr, dxr, nx);
-    CUDA_TRY(h, cudaMemcpyAsync(xsave, x_d, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    CUDA_TRY(h, cudaMemcpyAsync(usave, u, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     double t = 1.0, Pit = 0.0;
     bool acc = false;
     for (int hv = 0; hv < 40; ++hv) {
-      launch_positions_update(c, xsave, dxr, t, x_d);
+      launch_positions_update(c, usave, dxr, t, u);
       bool ok = true;
-      Pit = potential(x_d, &ok);
+      Pit = potential(u, &ok);
       if (ok) {
         if (Pit <= Pi + 1e-4 * t * slope) { acc = true; break; }
         if (std::fabs(t * slope) <= 1e-13 * std::max(std::fabs(Pi), 1e-300)) {
-          double cnt = residual(x_d);
+          double cnt = residual(u);
           if (cnt < cn) { acc = true; break; }
         }
       }
       t *= 0.5;
     }
     if (!acc) {
-      launch_positions_update(c, xsave, dxr, 1.0, x_d);
+      launch_positions_update(c, usave, dxr, 1.0, u);
       bool ok = true;
-      Pit = potential(x_d, &ok);
+      Pit = potential(u, &ok);
       if (!ok) {
-        CUDA_TRY(h, cudaMemcpyAsync(x_d, xsave, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        CUDA_TRY(h, cudaMemcpyAsync(u, usave, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         break;
       }
     }
     if (it < 32) tstep[it] = acc ? t : 1.0;
     Pi = Pit;
-    cn = residual(x_d);
+    cn = residual(u);
   }
+  launch_shift_rest(c, u, 1.0, x_d);  // x = X + u
   c.kf.factored = c.kf32.factored = false;  // K factor belongs to an earlier iterate
   c.assembled = false;
   if (c.active) c.active->factored = false;

@@ -49,16 +49,21 @@ __device__ __forceinline__ double det_inv(const double F[D][D], double Fi[D][D])
   }
 }
 
+// F = I + sum_a u_a B_a^T with u_a = v_a - xs X_a: v holds positions (xs = 1)
+// or displacements (xs = 0).  Summing displacements instead of positions
+// (F = sum_a x_a B_a^T) keeps the round-off of F at eps |u| |B| rather than
+// eps |x| |B|, independent of where the body sits.
 template <int D>
 __device__ __forceinline__ void load_F(int e, int ne, const int32_t *__restrict__ elem_node,
-                                       const double *__restrict__ elem_B, const double *__restrict__ x,
-                                       double B[D + 1][D], double F[D][D]) {
-  double xa[D + 1][D];
+                                       const double *__restrict__ elem_B, const double *__restrict__ v,
+                                       const double *__restrict__ X, double xs, double B[D + 1][D],
+                                       double F[D][D]) {
+  double ua[D + 1][D];
 #pragma unroll
   for (int a = 0; a <= D; ++a) {
     int n = __ldg(elem_node + (int64_t)a * ne + e);
 #pragma unroll
-    for (int i = 0; i < D; ++i) xa[a][i] = __ldg(x + (int64_t)n * D + i);
+    for (int i = 0; i < D; ++i) ua[a][i] = fma(-xs, __ldg(X + (int64_t)n * D + i), __ldg(v + (int64_t)n * D + i));
 #pragma unroll
     for (int j = 0; j < D; ++j) B[a][j] = __ldg(elem_B + (int64_t)(a * D + j) * ne + e);
   }
@@ -66,9 +71,9 @@ __device__ __forceinline__ void load_F(int e, int ne, const int32_t *__restrict_
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      double s = 0.0;
+      double s = i == j ? 1.0 : 0.0;
 #pragma unroll
-      for (int a = 0; a <= D; ++a) s = fma(xa[a][i], B[a][j], s);
+      for (int a = 0; a <= D; ++a) s = fma(ua[a][i], B[a][j], s);
       F[i][j] = s;
     }
 }
@@ -78,13 +83,14 @@ template <int D>
 __global__ void __launch_bounds__(TPB) k_elem_state(int ne, const int32_t *__restrict__ elem_node,
                                                     const double *__restrict__ elem_B,
                                                     const double *__restrict__ elem_vol,
-                                                    const double *__restrict__ x, const double *__restrict__ p,
+                                                    const double *__restrict__ x, const double *__restrict__ X,
+                                                    double xs, const double *__restrict__ p,
                                                     double E0, double nu, double *__restrict__ st,
                                                     double *__restrict__ cpv, int *status) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   double B[D + 1][D], F[D][D], Fi[D][D];
-  load_F<D>(e, ne, elem_node, elem_B, x, B, F);
+  load_F<D>(e, ne, elem_node, elem_B, x, X, xs, B, F);
   double J = det_inv<D>(F, Fi);
   if (!(J > 0.0)) {
     atomicOr(status, DEV_INVERTED);
@@ -426,13 +432,14 @@ template <int D>
 __global__ void __launch_bounds__(TPB) k_energy(int ne, const int32_t *__restrict__ elem_node,
                                                 const double *__restrict__ elem_B,
                                                 const double *__restrict__ elem_vol,
-                                                const double *__restrict__ x, const double *__restrict__ p,
-                                                double E0, double nu, double *__restrict__ partial) {
+                                                const double *__restrict__ x, const double *__restrict__ X, double xs,
+                                                const double *__restrict__ p, double E0, double nu,
+                                                double *__restrict__ partial) {
   __shared__ double sh[TPB];
   double s = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
     double B[D + 1][D], F[D][D], Fi[D][D];
-    load_F<D>(e, ne, elem_node, elem_B, x, B, F);
+    load_F<D>(e, ne, elem_node, elem_B, x, X, xs, B, F);
     double J = det_inv<D>(F, Fi);
     if (!(J > 0.0)) { s = INFINITY; continue; }
     double lnJ = log(J);
@@ -453,6 +460,14 @@ __global__ void __launch_bounds__(TPB) k_energy(int ne, const int32_t *__restric
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// out = v + s X over all node coordinates (s = -1: displacements of
+// positions v; s = +1: positions of displacements v)
+__global__ void k_shift_rest(int64_t n, const double *__restrict__ v, const double *__restrict__ X, double s,
+                             double *__restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fma(s, X[i], v[i]);
 }
 
 template <int D>
@@ -476,15 +491,21 @@ __global__ void k_positions(int n_free, const int32_t *__restrict__ rank_node, c
 
 void launch_elem_state(Ctx &c, const double *x, const double *p) {
   const DevSym &d = c.ds;
-  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, p,
-                 c.E0, c.nu, c.st, c.cpv, c.status);
+  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, d.X,
+                 1.0, p, c.E0, c.nu, c.st, c.cpv, c.status);
+}
+
+void launch_elem_state_disp(Ctx &c, const double *u, const double *p) {
+  const DevSym &d = c.ds;
+  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, u, d.X,
+                 0.0, p, c.E0, c.nu, c.st, c.cpv, c.status);
 }
 
 // same two kernels with the element state in caller-chosen scratch memory
 void launch_elem_state_into(Ctx &c, const double *x, const double *p, double *st) {
   const DevSym &d = c.ds;
-  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, p,
-                 c.E0, c.nu, st, c.cpv, c.status);
+  SGN_DISPATCH_D(c, k_elem_state, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, d.X,
+                 1.0, p, c.E0, c.nu, st, c.cpv, c.status);
 }
 
 void launch_slot_gather_from(Ctx &c, const double *st) {
@@ -591,15 +612,21 @@ void launch_internal_force(Ctx &c, double *fr) {
 
 int energy_blocks(Ctx &c) { return c.n_partial; }
 
-void launch_energy_partials(Ctx &c, const double *x, const double *p, double *partials, int nblocks) {
+void launch_energy_partials(Ctx &c, const double *x, const double *p, double *partials, int nblocks, bool disp) {
   const DevSym &d = c.ds;
-  SGN_DISPATCH_D(c, k_energy, nblocks, TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, p, c.E0, c.nu,
-                 partials);
+  SGN_DISPATCH_D(c, k_energy, nblocks, TPB, 0, d.n_elem, d.elem_node, d.elem_B, d.elem_vol, x, d.X,
+                 disp ? 0.0 : 1.0, p, c.E0, c.nu, partials);
 }
 
 void launch_positions_update(Ctx &c, const double *x0, const double *dxr, double t, double *x) {
   const DevSym &d = c.ds;
   SGN_DISPATCH_D(c, k_positions, nblk((int64_t)d.n_free * d.dim), TPB, 0, d.n_free, d.rank_node, x0, dxr, t, x);
+}
+
+void launch_shift_rest(Ctx &c, const double *v, double s, double *out) {
+  const int64_t n = (int64_t)c.ds.n_nodes * c.ds.dim;
+  k_shift_rest<<<nblk(n), TPB, 0, c.stream>>>(n, v, c.ds.X, s, out);
+  c.count();
 }
 
 void launch_gradient_finish(Ctx &c, const double *lam_r, double *g) {

@@ -31,6 +31,7 @@ struct DevSym {
   int dim = 0, n_nodes = 0, n_elem = 0, n_free = 0, n_sn = 0, panel = 32;
   const int32_t *elem_node = nullptr, *elem_rank = nullptr;
   const double *elem_B = nullptr, *elem_vol = nullptr;
+  const double *X = nullptr;               // rest positions [n_nodes][dim]
   const int32_t *node_rank = nullptr, *rank_node = nullptr;
   const int32_t *bsr_ptr = nullptr, *bsr_col = nullptr, *bsr_orig_pos = nullptr;
   const int32_t *up_slot = nullptr, *up_slot_t = nullptr, *up_ptr = nullptr, *up_contrib = nullptr;
@@ -122,6 +123,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   int device = -1;
   int num_sms = 152;
+  int update_ctas = 0;              // CTAs per tensor-core trailing update (0: num_sms)
   bool bound = false;
 
   // carving
@@ -157,6 +159,7 @@ struct Ctx {
   int64_t *counters = nullptr;      // pivot counters (perturbed, 2x2, pos, neg, zero)
   double *eq = nullptr;             // equilibrium scratch: [4][n_x]
   double *xsave = nullptr, *xrt = nullptr;   // [n_nodes*d], [n_x]
+  double *ueq = nullptr;            // Newton iterate u = x - X [n_nodes*d]
   double *hx = nullptr, *hdx = nullptr, *hdl = nullptr;  // host-call staging [n_nodes*d]
   double *hp = nullptr, *hdp = nullptr;                  // host-call staging [n_elem]
 
@@ -214,7 +217,8 @@ struct ProfScope {
 };
 
 // ---- launchers (assemble.cu)
-void launch_elem_state(Ctx &c, const double *x, const double *p);
+void launch_elem_state(Ctx &c, const double *x, const double *p);       // at positions x
+void launch_elem_state_disp(Ctx &c, const double *u, const double *p);  // at displacements u = x - X
 void launch_slot_gather(Ctx &c, bool with_G);
 void launch_elem_state_into(Ctx &c, const double *x, const double *p, double *st);
 void launch_slot_gather_from(Ctx &c, const double *st);
@@ -237,7 +241,11 @@ void launch_to_nodes_plain(Ctx &c, const double *vr, double *out_nodes);
 void launch_from_nodes(Ctx &c, const double *nodes, double *vr);
 // equilibrium helpers
 void launch_internal_force(Ctx &c, double *fr);      // f_int in rank-DOF layout from cpv
-void launch_energy_partials(Ctx &c, const double *x, const double *p, double *partials, int nblocks);
+// disp: x holds displacements u = x - X (else positions)
+void launch_energy_partials(Ctx &c, const double *x, const double *p, double *partials, int nblocks,
+                            bool disp = false);
+// out = v + s X over all node coordinates (node-major)
+void launch_shift_rest(Ctx &c, const double *v, double s, double *out);
 void launch_positions_update(Ctx &c, const double *x0, const double *dxr, double t, double *x);
 int energy_blocks(Ctx &c);
 void launch_gradient_finish(Ctx &c, const double *lam_r, double *g);

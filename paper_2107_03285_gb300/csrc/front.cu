@@ -876,7 +876,8 @@ void factor_impl(Ctx &c, Store &st) {
           // active fronts and let every CTA loop over its front's tiles
           int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
           int tiles = nt128 * (nt128 + 1) / 2;
-          int g = std::max(1, std::min(tiles, (c.num_sms + na - 1) / na));
+          const int ctas = c.update_ctas > 0 ? c.update_ctas : c.num_sms;
+          int g = std::max(1, std::min(tiles, (ctas + na - 1) / na));
           dim3 gtc(g, na);
           k_update_tcp<<<gtc, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK,
                                                                           (const tc::Maps *)st.maps, c.status);

@@ -22,7 +22,7 @@ class SGN:
     """Sparse Gauss-Newton context for one mesh (Sec. 4, Eq. sparseSystemGN)."""
 
     def __init__(self, dim, X, conn, fixed_node, E0, nu, stores=B.STORE_FP64 | B.STORE_KFACT,
-                 leaf_nodes=0, panel=0, device="cuda", stream=None):
+                 leaf_nodes=0, panel=0, update_ctas=0, device="cuda", stream=None):
         import torch
         self._torch = torch
         self.lib = B.lib()
@@ -33,7 +33,7 @@ class SGN:
         self.n_nodes, self.n_elem = self.X.shape[0], self.conn.shape[0]
         mesh = B.Mesh(self.dim, self.n_nodes, self.n_elem, B._dptr(self.X, C.c_double),
                       B._dptr(self.conn, C.c_int32), B._dptr(self.fixed, C.c_uint8), float(E0), float(nu))
-        opts = B.SetupOpts(int(leaf_nodes), int(panel))
+        opts = B.SetupOpts(int(leaf_nodes), int(panel), int(update_ctas))
         h = C.c_void_p()
         B._check(self.lib.sgn_setup(C.byref(mesh), C.byref(opts), C.byref(h)), "sgn_setup")
         self.h = h

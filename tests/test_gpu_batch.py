@@ -137,7 +137,7 @@ def test_autotuned_setup_keeps_parity(P, tmp_path):
     batch = problem_batch2d(12, seed=7, side_lo=5, side_hi=24)
     subs = _instances(batch)
     x, refs = _batch_state(batch, subs)
-    cands = [(8, 16), (16, 32), (32, 64)]
+    cands = [(8, 16), (16, 32), (32, 32)]
     path = str(tmp_path / "tune.json")
     best = A.tune(P, batch, P.MIXED, cache_path=path, x=x, cands=cands, reps=3, warmup=1)
     assert (best.leaf_nodes, best.panel) in cands and best.ms > 0

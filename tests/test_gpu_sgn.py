@@ -247,3 +247,59 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable(sgnmod):
     assert 0.1 < waited < 30.0
     _, dp, _, _, _ = s.step(c.x, c.p, sgnmod.MIXED)
     assert _rel(dp.cpu().numpy(), c.dp_k) < 1e-8
+
+
+@pytest.mark.parametrize("ctas", [1, 3])
+def test_tensor_core_update_ctas_loop_over_tiles(sgnmod, ctas):
+    """Capping the tensor-core update at a few CTAs makes every CTA walk
+    several 128 x 128 tiles of its front, alternating its two TMEM
+    accumulators (the persistent loop's buffer hand-off); the step still
+    matches the FP64 oracle."""
+    c = case("kuhn3d_11")
+    s = make(sgnmod, c, update_ctas=ctas)
+    _, dp, _, frep, srep = s.step(c.x, c.p, sgnmod.MIXED)
+    assert frep.tensor_core_updates > 0
+    assert _rel(dp.cpu().numpy(), c.dp_k) < 1e-8
+    n_x = c.prob.n_free * c.prob.dim
+    assert (frep.n_pos, frep.n_neg, frep.n_zero) == (n_x + c.prob.n_elem, n_x, 0)
+
+
+def test_mixed_step_error_certificate_kuhn3d_24(sgnmod):
+    """A posteriori bound on the mixed GPU step of a 24^3-node cube (N =
+    192,490), where dense Gauss-Newton is out of reach: H >= alpha I gives
+    ||dp - dp*|| <= ||H dp + g|| / alpha, with H dp and g applied by the
+    oracle through two sparse K solves (SuperLU on the CPU).  At this size
+    the root front has 27 blocks of 128 columns in each substitution chain
+    and every tensor-core CTA loops over several tiles."""
+    prob = problem_3d(24, seed=2, p_sigma=0.1)
+    s = sgnmod.SGN.from_problem(prob, stores=sgnmod.STORE_MIXED | sgnmod.STORE_KFACT_MIXED)
+    x, rep = s.equilibrium(prob.p0, prob.fext, precision=sgnmod.MIXED)
+    assert rep.converged and rep.residual <= 1e-10
+    x = x.cpu().numpy()
+    _, dp, _, frep, srep = s.step(x, prob.p0, sgnmod.MIXED)
+    dp = dp.cpu().numpy()
+    b = S.blocks(prob, x, prob.p0)
+    bound, _ = S.step_error_bound(b, dp)
+    assert bound <= 1e-8 * np.linalg.norm(dp), bound / np.linalg.norm(dp)
+    n_x = prob.n_free * prob.dim
+    assert (frep.n_pos, frep.n_neg, frep.n_zero) == (n_x + prob.n_elem, n_x, 0)
+
+
+def test_equilibrium_is_translation_invariant(sgnmod):
+    """The Newton iterate is the displacement: the same problem moved by 32
+    (grid spacing 1/16, so the moved rest shape is exact) takes the same
+    iterations to the same residual, below 1e-10, and the same
+    displacements."""
+    a = problem_2d(17, seed=5)
+    b = problem_2d(17, seed=5)
+    b.X = b.X + 32.0
+    b.target = b.target + 32.0
+    out = []
+    for prob in (a, b):
+        s = sgnmod.SGN.from_problem(prob, stores=sgnmod.STORE_KFACT)
+        x, rep = s.equilibrium(prob.p0, prob.fext)
+        assert rep.converged and rep.residual <= 1e-10
+        out.append(((x.cpu().numpy() - prob.X), list(rep.history)[:rep.iters + 1]))
+        s.close()
+    assert out[0][1] == out[1][1]
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=0, atol=1e-13)

@@ -170,3 +170,23 @@ def test_planted_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(el, "piola_tangent", broken)
     with pytest.raises(AssertionError):
         test_hessian_is_complex_step_jacobian_of_force(3)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_displacement_form_equals_position_form(d):
+    """F = I + D_u D_m^{-1} (u = x - X) is D_s D_m^{-1} rewritten: the two
+    agree to rounding, and at u = 0 the displacement form is I exactly, so
+    the energy and the force vanish exactly at rest."""
+    X, conn, x, E = _disconnected(d, 64, seed=10 + d)
+    u = x - X
+    f_pos = el.element_force(x, X, conn, E, 0.3)
+    f_dis = el.element_force(None, X, conn, E, 0.3, u=u)
+    np.testing.assert_allclose(f_dis, f_pos, rtol=0, atol=1e-10 * np.abs(f_pos).max())
+    H_pos = el.element_hessian(x, X, conn, E, 0.3)
+    H_dis = el.element_hessian(None, X, conn, E, 0.3, u=u)
+    np.testing.assert_allclose(H_dis, H_pos, rtol=0, atol=1e-10 * np.abs(H_pos).max())
+    z = np.zeros_like(X)
+    assert np.all(el.element_energy(None, X, conn, E, 0.3, u=z) == 0.0)
+    assert np.all(el.element_force(None, X, conn, E, 0.3, u=z) == 0.0)
+    Dminv, _, _ = el.rest_geometry(X, conn)
+    assert np.all(el.deformation_gradient_disp(z, conn, Dminv) == np.eye(d)[None])

@@ -147,3 +147,24 @@ def test_planted_sign_error_in_cp_is_caught(tiny, monkeypatch):
     monkeypatch.setattr(S, "param_jacobian", lambda *a: -orig(*a))
     with pytest.raises(AssertionError):
         test_sensitivity_matches_finite_differences((prob, p, x))
+
+
+def test_newton_iterate_is_translation_invariant():
+    """The Newton iterate is the displacement, so moving the whole problem
+    (rest shape and targets) changes nothing: the same displacements, the
+    same residual history, and the 1e-10 tolerance is met although the body
+    sits far from the origin (from absolute positions the round-off floor
+    there is about 2e-8 ||f_ext||).  The unmoved problem pins the moved one."""
+    from sgn_inputs import problem_2d
+    # grid spacing 1/16 and an offset of 32: the moved rest shape is exact,
+    # so the rest geometry (D_m) is bit for bit the same
+    a = problem_2d(17, seed=5)
+    b = problem_2d(17, seed=5)
+    b.X = b.X + 32.0
+    b.target = b.target + 32.0
+    xa, ia = EQ.newton(a, a.p0)
+    xb, ib = EQ.newton(b, b.p0)
+    assert ia["converged"] and ib["converged"]
+    assert ia["residual"] <= 1e-10 and ib["residual"] <= 1e-10
+    np.testing.assert_array_equal(ia["u"], ib["u"])
+    assert ia["history"] == ib["history"]
