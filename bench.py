@@ -198,25 +198,39 @@ def _timed(torch, fn):
     return r, time.perf_counter() - t0
 
 
+def _batch_instances(args):
+    """The batched workload's instances (batch2d_<n>: n plane-strain grids,
+    sides U{10..60})."""
+    from sgn_inputs import batch2d_instances
+    kind, _, n = args.batch_workload.rpartition("_")
+    if kind != "batch2d":
+        raise ValueError(f"batched workload must be batch2d_<n>, not {args.batch_workload}")
+    return batch2d_instances(int(n), seed=args.seed)
+
+
 def form_batched(P, torch, args):
-    """Many uneven plane-strain instances (one disjoint mesh, one elimination
-    forest): the mixed step as one CUDA-graph launch (assemble, factor, solve,
-    4 refinement solves) against the stepwise plain FP64 path on the same
-    batch."""
-    from sgn_inputs import make_preset
-    prob = make_preset(args.batch_workload, seed=args.seed)
+    """Many uneven plane-strain instances behind one handle (sgn_batch_setup:
+    one elimination forest): the mixed step as one CUDA-graph launch
+    (assemble, factor, solve, 4 refinement solves) against the stepwise plain
+    FP64 path on the same batch; per-instance residuals from the library."""
+    subs = _batch_instances(args)
     from paper_2107_03285_gb300 import autotune
-    tuned = autotune.lookup(prob, P.MIXED)
+    tuned = autotune.lookup(subs, P.MIXED)
     leaf, panel = tuned if tuned else (0, 0)
-    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED,
-                           leaf_nodes=leaf, panel=panel)
+    s = P.SGN.from_batch(subs, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED,
+                         leaf_nodes=leaf, panel=panel)
     try:
-        (x64, r64), t64e = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.FP64))
-        (x, rep), t_eq = _timed(torch, lambda: s.equilibrium(prob.p0, prob.fext, precision=P.MIXED))
-        eq64 = {"iters": r64.iters, "residual": r64.residual, "seconds": t64e,
-                "history": list(r64.history)[:r64.iters + 1], "max_abs_dx_vs_mixed": float((x64 - x).abs().max())}
+        p0 = np.concatenate([sub.p0 for sub in subs])
+        fext = np.concatenate([sub.fext for sub in subs])
+        (x64, r64), t64e = _timed(torch, lambda: s.equilibrium(p0, fext, precision=P.FP64))
+        res64 = s.batch_residuals(P.binding.BATCH_EQUILIBRIUM)
+        (x, rep), t_eq = _timed(torch, lambda: s.equilibrium(p0, fext, precision=P.MIXED))
+        resm = s.batch_residuals(P.binding.BATCH_EQUILIBRIUM)
+        eq64 = {"iters": r64.iters, "residual": r64.residual, "max_instance_residual": float(res64.max()),
+                "seconds": t64e, "history": list(r64.history)[:r64.iters + 1],
+                "max_abs_dx_vs_mixed": float((x64 - x).abs().max())}
         del x64
-        p = torch.as_tensor(prob.p0, device=x.device)
+        p = torch.as_tensor(p0, device=x.device)
         out = (torch.empty_like(x), torch.empty_like(p), torch.empty_like(x))
         s.step(x, p, P.FP64)
         (_, dp64, _, _, _), t64 = _timed(torch, lambda: s.step(x, p, P.FP64))
@@ -234,17 +248,20 @@ def form_batched(P, torch, args):
         ms = e0.elapsed_time(e1) / n
         launches = (s.launch_count() - l0) / n
         _, dpg, _, res = s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=True)
+        kkt_inst = s.batch_residuals(P.binding.BATCH_KKT)
         err = float(torch.linalg.norm(dpg - dp64) / torch.linalg.norm(dp64))
-        k = len(prob.meta["sides"])
-        return {"workload": f"{args.batch_workload}: {k} instances, sides {min(prob.meta['sides'])}.."
-                            f"{max(prob.meta['sides'])}, {prob.n_nodes} nodes, {prob.n_elem} triangles, "
-                            f"N={int(s.info.n_kkt)}",
+        k = len(subs)
+        sides = [int(round(np.sqrt(sub.n_nodes))) for sub in subs]
+        return {"workload": f"{args.batch_workload}: {k} instances (sgn_batch_setup), sides {min(sides)}.."
+                            f"{max(sides)}, {s.n_nodes} nodes, {s.n_elem} triangles, N={int(s.info.n_kkt)}",
                 "graph_mixed": {"steps_per_s": 1e3 / ms, "instance_steps_per_s": k * 1e3 / ms, "ms_per_step": ms,
                                 "launches_per_graph": launches, "kkt_residual": res,
+                                "max_instance_kkt_residual": float(kkt_inst.max()),
                                 "dp_rel_err_vs_fp64_gpu": err},
                 "stepwise_fp64": {"steps_per_s": 1.0 / t64, "ms_per_step": 1e3 * t64},
                 "speedup_vs_fp64": (1e3 / ms) * t64,
                 "equilibrium_mixed": {"iters": rep.iters, "solves": rep.solves, "residual": rep.residual,
+                                      "max_instance_residual": float(resm.max()),
                                       "seconds": t_eq, "history": list(rep.history)[:rep.iters + 1]},
                 "equilibrium_fp64": eq64,
                 "levels": int(s.info.n_levels), "supernodes": int(s.info.n_supernodes),
@@ -260,14 +277,16 @@ def form_batched_sharded(P, torch, args, ws, rank):
     exchange): every rank builds and times its own share as one graph step;
     the batch's rate is set by the slowest rank."""
     from paper_2107_03285_gb300 import shard
-    from sgn_inputs import make_preset, select_instances
-    batch = make_preset(args.batch_workload, seed=args.seed)
-    parts = shard.partition(shard.instance_costs(batch.meta["sides"]), ws)
-    prob = select_instances(batch, parts[rank])
-    s = P.SGN.from_problem(prob, stores=P.STORE_MIXED | P.STORE_KFACT_MIXED)
+    subs = _batch_instances(args)
+    sides = [int(round(np.sqrt(sub.n_nodes))) for sub in subs]
+    parts = shard.partition(shard.instance_costs(sides), ws)
+    mine = [subs[i] for i in parts[rank]]
+    s = P.SGN.from_batch(mine, stores=P.STORE_MIXED | P.STORE_KFACT_MIXED)
     try:
-        x, rep = s.equilibrium(prob.p0, prob.fext, precision=P.MIXED)
-        p = torch.as_tensor(prob.p0, device=x.device)
+        p0 = np.concatenate([sub.p0 for sub in mine])
+        fext = np.concatenate([sub.fext for sub in mine])
+        x, rep = s.equilibrium(p0, fext, precision=P.MIXED)
+        p = torch.as_tensor(p0, device=x.device)
         out = (torch.empty_like(x), torch.empty_like(p), torch.empty_like(x))
         for _ in range(3):
             s.step_graph(x, p, P.MIXED, refine_steps=4, out=out, residual=False)
@@ -281,7 +300,7 @@ def form_batched_sharded(P, torch, args, ws, rank):
         e1.record(s.stream)
         e1.synchronize()
         ms = shard.max_over_ranks(e0.elapsed_time(e1) / n, device=x.device)
-        k = len(batch.meta["sides"])
+        k = len(subs)
         return {"workload": f"{args.batch_workload} over {ws} ranks (cost-balanced, no collective on the data path)",
                 "instances_per_rank": [int(len(q)) for q in parts], "ms_per_step_slowest_rank": ms,
                 "steps_per_s": 1e3 / ms, "instance_steps_per_s": k * 1e3 / ms, "scaling": "strong"}

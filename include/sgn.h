@@ -275,6 +275,35 @@ sgn_status sgn_export_kkt(sgn_t h, int64_t *nnz, int64_t *rows_h, int64_t *cols_
  * GPU, from any handle or stream, race on it. */
 sgn_status sgn_assemble_static(sgn_t h, const double *x_d, const double *p_d);
 
+/* ---- batched instances ----------------------------------------------------
+ * The paper solves one design instance at a time (Sec. 5); these calls put n
+ * independent instances behind one handle.  sgn_batch_setup joins the meshes
+ * (node ids of instance i shifted by the nodes of instances 0..i-1, elements
+ * likewise) and their objectives (tracked DOF ids shifted the same way) into
+ * one disjoint system: its matrix is block diagonal by instance, so every
+ * instance's (dx, dp, dlambda) is exactly its own SGN step (Eq.
+ * sparseSystemGN), while the symbolic phase splits the node graph into its
+ * connected components first (one subtree of one elimination forest per
+ * instance) and every level's fronts of all instances share the launches.
+ * Instances keep their own coordinates and may overlap in space.  All meshes
+ * need the same dim, E0 and nu, all objectives the same alpha (EINVAL
+ * otherwise); objectives may be NULL (then call sgn_set_objective with joined
+ * DOF ids).  The objective given here is applied by sgn_bind.  Every other
+ * call then works on the joined arrays: positions [sum n_nodes][dim], p
+ * [sum n_elem], in instance order. */
+sgn_status sgn_batch_setup(int32_t n, const sgn_mesh *meshes, const sgn_objective *objectives,
+                           const sgn_setup_opts *opts, sgn_t *out);
+/* Number of instances in *n (0: not a batched handle) and, if the arrays are
+ * non-NULL, the n + 1 node and element offsets of the instances. */
+sgn_status sgn_batch_info(sgn_t h, int32_t *n, int64_t *node_off_h, int64_t *elem_off_h);
+enum {
+  SGN_BATCH_EQUILIBRIUM = 0,  /* ||c_i|| / ||f_ext,i|| at the last sgn_equilibrium's iterate */
+  SGN_BATCH_KKT = 1           /* ||b_i - M_i z_i|| / ||b_i|| of the last sgn_solve / sgn_step_graph */
+};
+/* Per-instance relative residuals (res_h: n doubles, FP64), synchronises.
+ * ESTATE if no such call has run since sgn_bind. */
+sgn_status sgn_batch_residuals(sgn_t h, int32_t kind, double *res_h);
+
 /* ---- forward simulation and gradient -------------------------------------
  * sgn_equilibrium: Newton's method on Pi(x; p) with a backtracking line
  * search that keeps Pi monotone and rejects inverted elements (Sec. 5,

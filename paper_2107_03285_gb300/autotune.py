@@ -52,13 +52,29 @@ class Choice:
     ms: float
 
 
+def _pattern(prob):
+    """(dim, n_nodes, n_elem, conn, fixed) of a problem or of a list of
+    batched instances joined in order (node ids shifted as sgn_batch_setup
+    shifts them)."""
+    if isinstance(prob, (list, tuple)):
+        off, conns = 0, []
+        for pr in prob:
+            conns.append(np.asarray(pr.conn, dtype=np.int64) + off)
+            off += pr.n_nodes
+        conn = np.concatenate(conns).astype(np.int32)
+        fixed = np.concatenate([np.asarray(pr.fixed_node, dtype=np.uint8) for pr in prob])
+        return prob[0].dim, off, conn.shape[0], conn, fixed
+    return prob.dim, prob.n_nodes, prob.n_elem, prob.conn, prob.fixed_node
+
+
 def pattern_key(prob, precision) -> str:
     """Hash of what the symbolic phase sees: dimension, connectivity, fixed
     nodes (and the precision the step runs in)."""
+    dim, n_nodes, n_elem, conn, fixed = _pattern(prob)
     h = hashlib.sha256()
-    h.update(np.int64([prob.dim, prob.n_nodes, prob.n_elem, int(precision)]).tobytes())
-    h.update(np.ascontiguousarray(prob.conn, dtype=np.int32).tobytes())
-    h.update(np.ascontiguousarray(prob.fixed_node, dtype=np.uint8).tobytes())
+    h.update(np.int64([dim, n_nodes, n_elem, int(precision)]).tobytes())
+    h.update(np.ascontiguousarray(conn, dtype=np.int32).tobytes())
+    h.update(np.ascontiguousarray(fixed, dtype=np.uint8).tobytes())
     return h.hexdigest()[:32]
 
 
@@ -111,11 +127,17 @@ def measure_step(P, prob, precision, leaf, panel, x=None, reps=5, warmup=2, refi
     (CUDA events on the step's stream, after warm-up launches)."""
     import torch
     stores = B.STORE_MIXED if precision == B.MIXED else B.STORE_FP64
-    s = P.SGN.from_problem(prob, stores=stores, leaf_nodes=leaf, panel=panel)
+    batched = isinstance(prob, (list, tuple))
+    if batched:
+        s = P.SGN.from_batch(prob, stores=stores, leaf_nodes=leaf, panel=panel)
+        p0 = np.concatenate([pr.p0 for pr in prob])
+    else:
+        s = P.SGN.from_problem(prob, stores=stores, leaf_nodes=leaf, panel=panel)
+        p0 = prob.p0
     try:
-        xs = prob.X if x is None else x
+        xs = s.X if x is None else x
         xd = torch.as_tensor(np.ascontiguousarray(xs, dtype=np.float64), device=s.device)
-        pd = torch.as_tensor(np.ascontiguousarray(prob.p0, dtype=np.float64), device=s.device)
+        pd = torch.as_tensor(np.ascontiguousarray(p0, dtype=np.float64), device=s.device)
         out = (torch.empty_like(xd), torch.empty_like(pd), torch.empty_like(xd))
         for _ in range(warmup):
             s.step_graph(xd, pd, precision, refine_steps=refine_steps, out=out, residual=False)
@@ -146,12 +168,14 @@ def tune(P, prob, precision=B.MIXED, cache_path: str | None = DEFAULT_CACHE, x=N
             return Choice(int(e["leaf_nodes"]), int(e["panel"]), float(e["ms"]))
     measure = measure or measure_step
     timings = {}
-    for leaf, panel in (cands or candidates(prob.dim)):
+    dim = prob[0].dim if isinstance(prob, (list, tuple)) else prob.dim
+    for leaf, panel in (cands or candidates(dim)):
         timings[(leaf, panel)] = float(measure(P, prob, precision, leaf, panel, x=x, **measure_kw))
     best = choose(timings)
     if cache_path:
         cache = load_cache(cache_path)
-        cache[key] = {"leaf_nodes": best.leaf_nodes, "panel": best.panel, "ms": best.ms, "name": prob.name,
+        name = f"{len(prob)} instances" if isinstance(prob, (list, tuple)) else prob.name
+        cache[key] = {"leaf_nodes": best.leaf_nodes, "panel": best.panel, "ms": best.ms, "name": name,
                       "timings": {f"{l}/{p}": t for (l, p), t in timings.items()}}
         store_cache(cache_path, cache)
     return best

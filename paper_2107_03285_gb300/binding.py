@@ -20,13 +20,14 @@ OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINI
 FP64, MIXED = 0, 1
 RHS_KKT, RHS_PAPER = 0, 1
 STORE_FP64, STORE_MIXED, STORE_KFACT, STORE_KFACT_MIXED = 1, 2, 4, 8
+BATCH_EQUILIBRIUM, BATCH_KKT = 0, 1
 PROF_KINDS = ["update", "panel_update", "pivot", "trsm", "front_assembly", "elements", "solve", "vector"]
 
 EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_set_stream",
             "sgn_set_objective", "sgn_destroy", "sgn_strerror", "sgn_assemble", "sgn_factor",
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
             "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
-            "sgn_last_error", "sgn_selftest_wait_timeout",
+            "sgn_last_error", "sgn_selftest_wait_timeout", "sgn_batch_setup", "sgn_batch_info", "sgn_batch_residuals",
             # learned warm start (include/sgn_learn.h)
             "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
             "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
@@ -122,6 +123,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_launch_count": (C.c_int64, [VP]),
         "sgn_last_error": (C.c_char_p, [VP]),
         "sgn_selftest_wait_timeout": (C.c_int, [VP]),
+        "sgn_batch_setup": (C.c_int, [C.c_int32, P(Mesh), P(Objective), P(SetupOpts), P(VP)]),
+        "sgn_batch_info": (C.c_int, [VP, P(C.c_int32), P(C.c_int64), P(C.c_int64)]),
+        "sgn_batch_residuals": (C.c_int, [VP, C.c_int32, dp]),
         "sgn_learn_create": (C.c_int, [VP, P(LearnOpts), P(VP)]),
         "sgn_learn_device_bytes": (C.c_int, [VP, P(C.c_size_t)]),
         "sgn_learn_bind": (C.c_int, [VP, VP, C.c_size_t]),

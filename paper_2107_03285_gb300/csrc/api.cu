@@ -288,6 +288,12 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx); c.ueq = cv.take<double>(nn);
   c.hx = cv.take<double>(nn); c.hdx = cv.take<double>(nn); c.hdl = cv.take<double>(nn);
   c.hp = cv.take<double>(ne); c.hdp = cv.take<double>(ne);
+  if (c.n_inst > 0) {
+    int32_t *p_;
+    st_up(p_, c.h_rank_inst); c.rank_inst = p_;
+    st_up(p_, c.h_elem_inst); c.elem_inst = p_;
+    c.inst_acc = cv.take<double>(4 * (size_t)c.n_inst);
+  }
   bool plan_ok = true;
   auto store = [&](Store &s, bool on, int dpn, bool kkt, bool fp32) {
     s.enabled = on;
@@ -548,7 +554,14 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   if (h->step_graph) { cudaGraphExecDestroy(h->step_graph); h->step_graph = nullptr; }
   h->bound = true;
   h->assembled = false;
+  h->inst_have_eq = h->inst_have_kkt = false;
   h->kkt64.factored = h->kkt32.factored = h->kf.factored = h->kf32.factored = false;
+  if (h->pending_obj) {  // the joined objective of sgn_batch_setup
+    sgn_objective o{(int32_t)h->pobj_track.size(), h->pobj_track.data(), h->pobj_target.data(),
+                    h->pobj_weight.data(), h->pobj_alpha};
+    sgn_status s = sgn_set_objective(h, &o);
+    if (s != SGN_OK) return s;
+  }
   return SGN_OK;
 }
 
@@ -696,6 +709,8 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     launch_axpy(c, c.zl, c.rl, 1.0, nx);
     ++steps;
   }
+  batch_record_solve(c);
+  c.inst_have_kkt = c.n_inst > 0;
   if (dx_d) launch_to_nodes_plain(c, c.zx, dx_d);
   if (dl_d) launch_to_nodes_plain(c, c.zl, dl_d);
   CUDA_TRY(h, cudaMemcpyAsync(dp_d, c.zp, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
@@ -865,6 +880,7 @@ sgn_status sgn_step_graph(sgn_t h, sgn_precision prec, int32_t refine_steps, con
       launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
       launch_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx, c.partial2);
       launch_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx, c.partial2 + c.n_partial);
+      batch_record_solve(c);
       if (dx_d) launch_to_nodes_plain(c, c.zx, dx_d);
       if (dl_d) launch_to_nodes_plain(c, c.zl, dl_d);
       cudaMemcpyAsync(dp_d, c.zp, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
@@ -879,6 +895,7 @@ sgn_status sgn_step_graph(sgn_t h, sgn_precision prec, int32_t refine_steps, con
     h->step_refine = refine_steps;
   }
   CUDA_TRY(h, cudaGraphLaunch(h->step_graph, c.stream));
+  c.inst_have_kkt = c.n_inst > 0;
   c.launches += h->step_launches;
   c.tc_launches += h->step_tc;
   c.assembled = true;
@@ -1040,6 +1057,8 @@ sgn_status sgn_equilibrium(sgn_t h, const double *p_d, const double *fext_d, dou
     cn = residual(u);
   }
   launch_shift_rest(c, u, 1.0, x_d);  // x = X + u
+  batch_record_equilibrium(c, cr, fr);
+  c.inst_have_eq = c.n_inst > 0;
   c.kf.factored = c.kf32.factored = false;  // K factor belongs to an earlier iterate
   c.assembled = false;
   if (c.active) c.active->factored = false;

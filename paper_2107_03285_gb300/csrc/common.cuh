@@ -163,6 +163,19 @@ struct Ctx {
   double *hx = nullptr, *hdx = nullptr, *hdl = nullptr;  // host-call staging [n_nodes*d]
   double *hp = nullptr, *hdp = nullptr;                  // host-call staging [n_elem]
 
+  // batched instances (sgn_batch_setup): instance i owns nodes
+  // [inst_node_off[i], inst_node_off[i+1]) and elements likewise
+  int n_inst = 0;
+  std::vector<int64_t> inst_node_off, inst_elem_off;
+  std::vector<int32_t> h_rank_inst, h_elem_inst;
+  const int32_t *rank_inst = nullptr, *elem_inst = nullptr;  // device copies
+  double *inst_acc = nullptr;       // [4][n_inst]: ||c||^2, ||f_ext||^2, ||r||^2, ||b||^2
+  bool inst_have_eq = false, inst_have_kkt = false;
+  bool pending_obj = false;         // objective given at set-up, applied at bind
+  std::vector<int64_t> pobj_track;
+  std::vector<double> pobj_target, pobj_weight;
+  double pobj_alpha = 0.0;
+
   Store kkt64, kkt32, kf, kf32;
   Store *active = nullptr;          // saddle-point factor of the last sgn_factor
 
@@ -260,6 +273,10 @@ void wait_selftest(Ctx &c, Store &s);  // one substitution wait that must expire
 cudaGraphExec_t capture_fn(Ctx &c, const std::function<void()> &body, int64_t *launches, int64_t *tc);
 void solve_direct(Ctx &c, Store &s, const double *b_red, double *x_red);  // no graph
 void destroy_graphs(Store &s);
+
+// ---- batch.cu: per-instance norms of a batched handle (no-ops otherwise)
+void batch_record_equilibrium(Ctx &c, const double *cr, const double *fr);
+void batch_record_solve(Ctx &c);
 
 // ---- error reporting (api.cu): sets the handle's detail (if h) and the
 // message sgn_strerror returns for the status

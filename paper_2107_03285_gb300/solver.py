@@ -37,6 +37,45 @@ class SGN:
         h = C.c_void_p()
         B._check(self.lib.sgn_setup(C.byref(mesh), C.byref(opts), C.byref(h)), "sgn_setup")
         self.h = h
+        self._bind(stores, device, stream)
+
+    @classmethod
+    def from_batch(cls, probs, stores=B.STORE_FP64 | B.STORE_KFACT, leaf_nodes=0, panel=0, update_ctas=0,
+                   device="cuda", stream=None):
+        """One handle for many independent instances (sgn_batch_setup): the
+        meshes and objectives of `probs` joined in order; x, p, fext and the
+        step's outputs are the instances' arrays concatenated."""
+        self = cls.__new__(cls)
+        import torch
+        self._torch = torch
+        self.lib = B.lib()
+        probs = list(probs)
+        self.dim = int(probs[0].dim)
+        keep = []
+        meshes = (B.Mesh * len(probs))()
+        objs = (B.Objective * len(probs))()
+        for i, pr in enumerate(probs):
+            X = _f64(pr.X).reshape(-1, self.dim)
+            conn = np.ascontiguousarray(pr.conn, dtype=np.int32)
+            fixed = np.ascontiguousarray(pr.fixed_node, dtype=np.uint8)
+            tr = np.ascontiguousarray(pr.track_dof, dtype=np.int64)
+            tg, wt = _f64(pr.target), _f64(pr.weight)
+            keep += [X, conn, fixed, tr, tg, wt]
+            meshes[i] = B.Mesh(self.dim, X.shape[0], conn.shape[0], B._dptr(X, C.c_double),
+                               B._dptr(conn, C.c_int32), B._dptr(fixed, C.c_uint8), float(pr.E0), float(pr.nu))
+            objs[i] = B.Objective(tr.shape[0], B._dptr(tr, C.c_int64), B._dptr(tg, C.c_double),
+                                  B._dptr(wt, C.c_double), float(pr.alpha))
+        opts = B.SetupOpts(int(leaf_nodes), int(panel), int(update_ctas))
+        h = C.c_void_p()
+        B._check(self.lib.sgn_batch_setup(len(probs), meshes, objs, C.byref(opts), C.byref(h)), "sgn_batch_setup")
+        self.h = h
+        self.X = np.concatenate([_f64(pr.X).reshape(-1, self.dim) for pr in probs])
+        self.n_nodes, self.n_elem = self.X.shape[0], sum(int(pr.n_elem) for pr in probs)
+        self._bind(stores, device, stream)
+        return self
+
+    def _bind(self, stores, device, stream):
+        import torch
         self.info = B.Info()
         B._check(self.lib.sgn_get_info(self.h, C.byref(self.info)), "sgn_get_info", self.h)
         self.stores = int(stores)
@@ -47,6 +86,25 @@ class SGN:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         B._check(self.lib.sgn_bind(self.h, C.c_void_p(self.buf.data_ptr()), int(nbytes.value), self.stores,
                                    C.c_void_p(self.stream.cuda_stream)), "sgn_bind", self.h)
+
+    def batch_offsets(self):
+        """(node offsets, element offsets), n + 1 each, of a batched handle."""
+        n = C.c_int32()
+        B._check(self.lib.sgn_batch_info(self.h, C.byref(n), None, None), "sgn_batch_info", self.h)
+        no = np.empty(n.value + 1, dtype=np.int64)
+        eo = np.empty(n.value + 1, dtype=np.int64)
+        B._check(self.lib.sgn_batch_info(self.h, C.byref(n), B._dptr(no, C.c_int64), B._dptr(eo, C.c_int64)),
+                 "sgn_batch_info", self.h)
+        return no, eo
+
+    def batch_residuals(self, kind=B.BATCH_EQUILIBRIUM):
+        """Per-instance relative residuals of the last equilibrium (kind 0)
+        or saddle-point solve (kind 1)."""
+        no, _ = self.batch_offsets()
+        out = np.empty(no.shape[0] - 1)
+        B._check(self.lib.sgn_batch_residuals(self.h, int(kind), B._dptr(out, C.c_double)), "sgn_batch_residuals",
+                 self.h)
+        return out
 
     @classmethod
     def from_problem(cls, prob, **kw):

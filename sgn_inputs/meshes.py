@@ -195,27 +195,38 @@ def problem_tiny_3d(n: int = 3, seed: int = 1, p_sigma: float = 0.2) -> Problem:
     return problem_3d(n=n, seed=seed, p_sigma=p_sigma, name=f"tiny3d_{n}")
 
 
-def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, side_hi: int = 60,
-                    shift_sigma: float = 0.03, p_sigma: float = 0.1, gap: float = 0.5) -> Problem:
-    """Many independent plane-strain design instances in one disjoint mesh.
+def batch2d_instances(n_instances: int = 256, seed: int = 0, side_lo: int = 10, side_hi: int = 60,
+                      shift_sigma: float = 0.03, p_sigma: float = 0.1) -> list:
+    """Many independent plane-strain design instances of uneven size.
 
-    Instance i is a side_i x side_i grid (side_i ~ U{side_lo..side_hi}),
-    clamped on its left edge, body-loaded, with its right edge tracked towards
-    rest + (0, -0.05) + s_i where s_i ~ N(0, shift_sigma^2) (one 2-vector per
-    instance); p ~ N(0, p_sigma^2).  Instances sit on a square grid of cells
-    (1 + gap) apart, so they never share nodes and the coordinates stay small
-    (positions far from the origin would raise the round-off floor of the
-    equilibrium residual); meta["node_offsets"] and meta["elem_offsets"]
-    delimit them, meta["origins"] holds each instance's translation."""
+    Instance i is a side_i x side_i grid on the unit square (side_i ~
+    U{side_lo..side_hi}), clamped on its left edge, body-loaded, with its right
+    edge tracked towards rest + (0, -0.05) + s_i where s_i ~ N(0, shift_sigma^2)
+    (one 2-vector per instance); p ~ N(0, p_sigma^2).  Every instance keeps its
+    own coordinates."""
     rng = np.random.default_rng(seed)
     sides = rng.integers(side_lo, side_hi + 1, size=n_instances)
+    out = []
+    for n in sides:
+        shift = (0.0, -0.05) + rng.normal(0.0, shift_sigma, size=2)
+        sub = problem_2d(int(n), seed=int(rng.integers(0, 2**31 - 1)), shift=tuple(shift), p_sigma=p_sigma)
+        out.append(sub)
+    return out
+
+
+def problem_batch2d(n_instances: int = 256, seed: int = 0, side_lo: int = 10, side_hi: int = 60,
+                    shift_sigma: float = 0.03, p_sigma: float = 0.1, gap: float = 0.5) -> Problem:
+    """The instances of batch2d_instances joined into one disjoint mesh by
+    hand: they sit on a square grid of cells (1 + gap) apart, so they never
+    share nodes; meta["node_offsets"] and meta["elem_offsets"] delimit them,
+    meta["origins"] holds each instance's translation."""
+    subs = batch2d_instances(n_instances, seed, side_lo, side_hi, shift_sigma, p_sigma)
+    sides = np.array([int(round(np.sqrt(sub.n_nodes))) for sub in subs])
     Xs, conns, fixeds, fexts, tracks, targets, weights, ps = [], [], [], [], [], [], [], []
     node_off, elem_off = [0], [0]
     per_row = int(np.ceil(np.sqrt(n_instances)))
     origins = np.array([((i % per_row) * (1.0 + gap), (i // per_row) * (1.0 + gap)) for i in range(n_instances)])
-    for i, n in enumerate(sides):
-        shift = (0.0, -0.05) + rng.normal(0.0, shift_sigma, size=2)
-        sub = problem_2d(int(n), seed=int(rng.integers(0, 2**31 - 1)), shift=tuple(shift), p_sigma=p_sigma)
+    for i, sub in enumerate(subs):
         X = sub.X + origins[i]
         tgt = sub.target.reshape(-1, 2) + origins[i]
         Xs.append(X)

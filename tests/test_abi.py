@@ -124,3 +124,79 @@ def test_contribution_block_arena_plan_is_consistent(B, which):
         sizes[m] = n.value
     assert sizes[15] < sizes[B.STORE_FP64] + sizes[B.STORE_MIXED] + sizes[B.STORE_KFACT] + sizes[B.STORE_KFACT_MIXED]
     lib.sgn_destroy(h)
+
+
+def _batch_setup(B, probs, alphas=None):
+    lib = B.load_library()
+    keep = []
+    meshes = (B.Mesh * len(probs))()
+    objs = (B.Objective * len(probs))()
+    for i, pr in enumerate(probs):
+        X = np.ascontiguousarray(pr.X, dtype=np.float64)
+        conn = np.ascontiguousarray(pr.conn, dtype=np.int32)
+        fixed = np.ascontiguousarray(pr.fixed_node, dtype=np.uint8)
+        tr = np.ascontiguousarray(pr.track_dof, dtype=np.int64)
+        tg = np.ascontiguousarray(pr.target, dtype=np.float64)
+        wt = np.ascontiguousarray(pr.weight, dtype=np.float64)
+        keep += [X, conn, fixed, tr, tg, wt]
+        meshes[i] = B.Mesh(pr.dim, X.shape[0], conn.shape[0], B._dptr(X, C.c_double), B._dptr(conn, C.c_int32),
+                           B._dptr(fixed, C.c_uint8), pr.E0, pr.nu)
+        a = pr.alpha if alphas is None else alphas[i]
+        objs[i] = B.Objective(tr.shape[0], B._dptr(tr, C.c_int64), B._dptr(tg, C.c_double),
+                              B._dptr(wt, C.c_double), a)
+    h = C.c_void_p()
+    code = lib.sgn_batch_setup(len(probs), meshes, objs, C.byref(B.SetupOpts(0, 0, 0)), C.byref(h))
+    return lib, code, h, keep
+
+
+def test_batch_setup_joins_instances(B):
+    """sgn_batch_setup: offsets of the joined arrays, sizes equal to the sum
+    of the instances' own set-ups, overlapping coordinates allowed."""
+    from sgn_inputs import batch2d_instances
+    probs = batch2d_instances(5, seed=3, side_lo=4, side_hi=9)
+    lib, code, h, keep = _batch_setup(B, probs)
+    assert code == B.OK
+    n = C.c_int32()
+    no = np.zeros(6, dtype=np.int64)
+    eo = np.zeros(6, dtype=np.int64)
+    assert lib.sgn_batch_info(h, C.byref(n), B._dptr(no, C.c_int64), B._dptr(eo, C.c_int64)) == B.OK
+    assert n.value == 5
+    np.testing.assert_array_equal(no, np.cumsum([0] + [p.n_nodes for p in probs]))
+    np.testing.assert_array_equal(eo, np.cumsum([0] + [p.n_elem for p in probs]))
+    info = B.Info()
+    assert lib.sgn_get_info(h, C.byref(info)) == B.OK
+    tot = {"n_x": 0, "nnz_kkt": 0, "nnz_factor": 0}
+    for pr in probs:
+        l1, c1, h1, k1 = _setup(B, pr)
+        assert c1 == B.OK
+        i1 = B.Info()
+        l1.sgn_get_info(h1, C.byref(i1))
+        for k in tot:
+            tot[k] += getattr(i1, k)
+        l1.sgn_destroy(h1)
+    assert info.n_x == tot["n_x"] and info.nnz_kkt == tot["nnz_kkt"]
+    # one elimination forest: the factor of the block-diagonal matrix is the
+    # union of the instances' factors when every instance keeps its own ordering
+    assert info.nnz_factor == tot["nnz_factor"]
+    # residuals before any solve: out of order
+    out = np.zeros(5)
+    assert lib.sgn_batch_residuals(h, 0, B._dptr(out, C.c_double)) == B.ESTATE
+    lib.sgn_destroy(h)
+    # a plain handle is not a batch
+    l2, c2, h2, k2 = _setup(B, probs[0])
+    assert l2.sgn_batch_info(h2, C.byref(n), None, None) == B.OK and n.value == 0
+    l2.sgn_destroy(h2)
+
+
+def test_batch_setup_rejects_mismatched_instances(B):
+    from sgn_inputs import batch2d_instances, problem_tiny_3d
+    probs = batch2d_instances(3, seed=4, side_lo=4, side_hi=6)
+    lib, code, h, _ = _batch_setup(B, probs, alphas=[1e-4, 2e-4, 1e-4])
+    assert code == B.EINVAL and "alpha" in lib.sgn_strerror(code).decode()
+    probs2 = probs[:2] + [problem_tiny_3d()]
+    lib, code, h, _ = _batch_setup(B, probs2)
+    assert code == B.EINVAL and "dim" in lib.sgn_strerror(code).decode()
+    probs[1].E0 = 2e4
+    lib, code, h, _ = _batch_setup(B, probs)
+    assert code == B.EINVAL
+    assert lib.sgn_batch_setup(0, None, None, None, C.byref(C.c_void_p())) == B.EINVAL
