@@ -135,10 +135,26 @@ typedef struct {
   int64_t tensor_core_updates;    /* trailing-update launches on the tcgen05 tensor cores */
 } sgn_factor_report;
 
+/* How sgn_solve reaches its tolerance with the factor as preconditioner.
+ * Sec. 5 ("Solving the saddle point problem") falls back to BiCGSTAB
+ * preconditioned by an LDL^T factor when the direct solve is not accurate
+ * enough; here stationary FP64 refinement comes first and BiCGSTAB (FP64,
+ * right-preconditioned by the factor, on the unstabilized matrix) takes over
+ * when refinement stops contracting. */
+typedef enum {
+  SGN_SOLVE_AUTO = 0,      /* refinement; BiCGSTAB from its last iterate once a refinement step
+                              shrinks the residual by less than half above 1e-11 ||b||, or
+                              max_refine steps did not reach tol */
+  SGN_SOLVE_REFINE = 1,    /* refinement only (SGN_EREFINE if it ends above 1e-8 ||b||) */
+  SGN_SOLVE_BICGSTAB = 2   /* BiCGSTAB from the first preconditioned solve */
+} sgn_solve_method;
+
 typedef struct {
   int32_t max_refine;             /* FP64 refinement steps (default 0 -> 2 FP64 / 30 mixed) */
   double tol;                     /* stop at ||b - M z|| <= tol ||b|| (default 0 -> 1e-12, just above
                                      the FP64 round-off floor of the 40^3 system, ~1.4e-13) */
+  int32_t method;                 /* sgn_solve_method (0: SGN_SOLVE_AUTO) */
+  int32_t max_krylov;             /* BiCGSTAB iterations (default 0 -> 200) */
 } sgn_solve_opts;
 
 typedef struct {
@@ -146,7 +162,16 @@ typedef struct {
   double residual;                /* final ||b - M z|| / ||b|| in FP64 */
   double seconds;
   double history[32];             /* ||b - M z|| / ||b|| after each of the first 32 solves */
+  int32_t krylov_iters;           /* BiCGSTAB iterations taken (0: refinement sufficed) */
 } sgn_solve_report;
+
+/* Stabilization of the factored matrix (sgn_factor_ex): the factor is taken
+ * of M + diag(eps_x 1, 0, -eps_lambda 1) (x, p, lambda blocks), as Sec. 5
+ * does for the LDL^T that preconditions BiCGSTAB; residuals, refinement and
+ * BiCGSTAB still use M itself, so the solution is that of M. */
+typedef struct {
+  double eps_x, eps_lambda;       /* >= 0; both 0: the factor of M (sgn_factor) */
+} sgn_factor_opts;
 
 typedef struct {
   int32_t max_iter;               /* default 0 -> 50 */
@@ -219,6 +244,9 @@ sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d);
  * Bunch-Kaufman 1x1/2x2 pivots restricted to each panel of the fully-summed
  * block.  report may be NULL (no synchronisation). */
 sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *report);
+/* sgn_factor_ex: sgn_factor of the stabilized matrix of sgn_factor_opts
+ * (opts NULL: as sgn_factor).  EINVAL for a negative eps. */
+sgn_status sgn_factor_ex(sgn_t h, sgn_precision prec, const sgn_factor_opts *opts, sgn_factor_report *report);
 /* sgn_solve: (dx, dp, dl) of Eq. sparseSystemGN by forward, diagonal and
  * backward substitution with the factor, followed by FP64 iterative
  * refinement against the assembled matrix.  g_d = df/dp for SGN_RHS_PAPER

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsgn.so")
 # status codes (sgn_status)
 OK, EINVAL, ECUDA, ENOMEM, EINVERTED, ENEWTON, EPIVOT, EREFINE, ESTATE, ENONFINITE, ETIMEOUT = range(11)
 FP64, MIXED = 0, 1
+SOLVE_AUTO, SOLVE_REFINE, SOLVE_BICGSTAB = 0, 1, 2
 RHS_KKT, RHS_PAPER = 0, 1
 STORE_FP64, STORE_MIXED, STORE_KFACT, STORE_KFACT_MIXED = 1, 2, 4, 8
 BATCH_EQUILIBRIUM, BATCH_KKT = 0, 1
@@ -28,6 +29,7 @@ EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_se
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
             "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
             "sgn_last_error", "sgn_selftest_wait_timeout", "sgn_batch_setup", "sgn_batch_info", "sgn_batch_residuals",
+            "sgn_factor_ex",
             # learned warm start (include/sgn_learn.h)
             "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
             "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
@@ -66,12 +68,16 @@ class FactorReport(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("max_refine", C.c_int32), ("tol", C.c_double)]
+    _fields_ = [("max_refine", C.c_int32), ("tol", C.c_double), ("method", C.c_int32), ("max_krylov", C.c_int32)]
 
 
 class SolveReport(C.Structure):
     _fields_ = [("refine_steps", C.c_int32), ("residual", C.c_double), ("seconds", C.c_double),
-                ("history", C.c_double * 32)]
+                ("history", C.c_double * 32), ("krylov_iters", C.c_int32)]
+
+
+class FactorOpts(C.Structure):
+    _fields_ = [("eps_x", C.c_double), ("eps_lambda", C.c_double)]
 
 
 class KernelProfile(C.Structure):
@@ -112,6 +118,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_assemble_static": (C.c_int, [VP, VP, VP]),
         "sgn_step_graph": (C.c_int, [VP, C.c_int, C.c_int32, VP, VP, VP, VP, VP, dp]),
         "sgn_factor": (C.c_int, [VP, C.c_int, P(FactorReport)]),
+        "sgn_factor_ex": (C.c_int, [VP, C.c_int, P(FactorOpts), P(FactorReport)]),
         "sgn_solve": (C.c_int, [VP, C.c_int, VP, VP, VP, VP, P(SolveOpts), P(SolveReport)]),
         "sgn_step_host": (C.c_int, [VP, C.c_int, dp, dp, dp, dp, dp, P(SolveReport)]),
         "sgn_equilibrium": (C.c_int, [VP, VP, VP, VP, P(NewtonOpts), P(NewtonReport)]),

@@ -36,6 +36,10 @@ constexpr double kStagnationCap = 1e-10;
     }                                                                       \
   } while (0)
 
+struct V3 {  // a vector of the full saddle-point system: x, p, lambda parts
+  double *x, *p, *l;
+};
+
 struct Carver {
   char *base;
   size_t off = 0;
@@ -278,6 +282,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.zx = cv.take<double>(nx); c.zp = cv.take<double>(ne); c.zl = cv.take<double>(nx);
   c.rx = cv.take<double>(nx); c.rp = cv.take<double>(ne); c.rl = cv.take<double>(nx);
   c.red = cv.take<double>(2 * nx * 2);  // reduced rhs and solution
+  c.kry = cv.take<double>((size_t)Ctx::KRY_VECS * (2 * nx + ne));  // BiCGSTAB vectors
   c.n_partial = 1024;
   c.partial = cv.take<double>(c.n_partial);
   c.partial2 = cv.take<double>(2 * c.n_partial);
@@ -620,10 +625,21 @@ sgn_status sgn_assemble(sgn_t h, const double *x_d, const double *p_d) {
 }
 
 sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *rep) {
+  return sgn_factor_ex(h, prec, nullptr, rep);
+}
+
+sgn_status sgn_factor_ex(sgn_t h, sgn_precision prec, const sgn_factor_opts *opts, sgn_factor_report *rep) {
   if (!h) return SGN_EINVAL;
+  const double ex = opts ? opts->eps_x : 0.0, el = opts ? opts->eps_lambda : 0.0;
+  if (!(ex >= 0.0) || !(el >= 0.0)) { g_err = "stabilization must be >= 0"; return SGN_EINVAL; }
   if (!h->assembled) return SGN_ESTATE;
   Store &st = prec == SGN_MIXED ? h->kkt32 : h->kkt64;
   if (!st.enabled) { g_err = "store for this precision was not bound"; return SGN_ESTATE; }
+  if (st.eps_x != ex || st.eps_l != el) {  // the captured factor graphs bake the old values in
+    destroy_graphs(st);
+    st.eps_x = ex;
+    st.eps_l = el;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (rep) {
     CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
@@ -665,6 +681,8 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   const int64_t nx = (int64_t)c.S.n_free * c.S.dim, ne = c.S.n_elem;
   int max_refine = opts && opts->max_refine > 0 ? opts->max_refine : (st.fp32 ? 30 : 2);
   double tol = opts && opts->tol > 0 ? opts->tol : 1e-12;
+  const int method = opts ? opts->method : SGN_SOLVE_AUTO;
+  if (method < SGN_SOLVE_AUTO || method > SGN_SOLVE_BICGSTAB) return SGN_EINVAL;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (rep) {
     CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));
@@ -689,16 +707,25 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   launch_recover(c, red_x, c.bp, c.zx, c.zp, c.zl);
   double bn = std::sqrt(device_sumsq3(c, c.bx, nx, c.bp, ne, c.bl, nx));
   double rn = 0.0, rn_prev = 0.0;
-  int steps = 0;
+  int steps = 0, kits = 0;
   double hist[32];
+  bool krylov = false;
   for (;;) {
     launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
     rn = std::sqrt(device_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx));
     if (steps < 32) hist[steps] = bn > 0 ? rn / bn : rn;
     if (!(rn == rn)) { h->last_error = "non-finite residual"; return SGN_ENONFINITE; }
-    if (rn <= tol * bn || steps >= max_refine) break;
+    if (rn <= tol * bn) break;
     // stagnation at round-off level: the FP64 residual cannot fall further
     if (steps > 0 && rn > 0.5 * rn_prev && rn <= 1e-11 * bn) break;
+    if (method == SGN_SOLVE_BICGSTAB || (method == SGN_SOLVE_AUTO && steps > 0 && rn > 0.5 * rn_prev)) {
+      krylov = true;  // refinement no longer contracts: Krylov takes over from z
+      break;
+    }
+    if (steps >= max_refine) {
+      krylov = method == SGN_SOLVE_AUTO;
+      break;
+    }
     rn_prev = rn;
     launch_reduce_rhs(c, c.rx, c.rp, c.rl, red_b, 2 * c.S.dim);
     solve_store(c, st, red_b, red_x);
@@ -708,6 +735,81 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     launch_axpy(c, c.zp, c.rp, 1.0, ne);
     launch_axpy(c, c.zl, c.rl, 1.0, nx);
     ++steps;
+  }
+  if (krylov) {
+    // BiCGSTAB (van der Vorst 1992), right-preconditioned by the factor, on
+    // M z = b from the current z; r = b - M z is in (rx, rp, rl).  Matrix
+    // products go through the FP64 residual kernel with b = 0, which returns
+    // -M v; the signs below account for it.
+    const int max_k = opts && opts->max_krylov > 0 ? opts->max_krylov : 200;
+    const int64_t n3 = 2 * nx + ne;
+    auto vec = [&](int i) { return V3{c.kry + (size_t)i * n3, c.kry + (size_t)i * n3 + nx, c.kry + (size_t)i * n3 + nx + ne}; };
+    const V3 R{c.rx, c.rp, c.rl}, Z{c.zx, c.zp, c.zl};
+    const V3 Rh = vec(0), Pv = vec(1), Vn = vec(2), Y = vec(3), Sv = vec(4), Zt = vec(5), Tn = vec(6), O = vec(7);
+    CUDA_TRY(h, cudaMemsetAsync(c.kry, 0, (size_t)Ctx::KRY_VECS * n3 * sizeof(double), c.stream));
+    auto copy3 = [&](const V3 &d, const V3 &a) {
+      cudaMemcpyAsync(d.x, a.x, nx * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+      cudaMemcpyAsync(d.p, a.p, ne * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+      cudaMemcpyAsync(d.l, a.l, nx * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    };
+    auto axpy3 = [&](const V3 &y, const V3 &x, double a) {
+      launch_axpy(c, y.x, x.x, a, nx); launch_axpy(c, y.p, x.p, a, ne); launch_axpy(c, y.l, x.l, a, nx);
+    };
+    auto dot3 = [&](const V3 &a, const V3 &b) {
+      return device_dot(c, a.x, b.x, nx) + device_dot(c, a.p, b.p, ne) + device_dot(c, a.l, b.l, nx);
+    };
+    auto neg_matvec = [&](const V3 &out, const V3 &in) {  // out = -M in
+      launch_residual(c, O.x, O.p, O.l, in.x, in.p, in.l, out.x, out.p, out.l);
+    };
+    auto precond = [&](const V3 &out, const V3 &in) {  // out = (factor)^{-1} in
+      launch_reduce_rhs(c, in.x, in.p, in.l, red_b, 2 * c.S.dim);
+      solve_store(c, st, red_b, red_x);
+      launch_recover(c, red_x, in.p, out.x, out.p, out.l);
+    };
+    copy3(Rh, R);
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (kits = 0; kits < max_k;) {
+      const double rho1 = dot3(Rh, R);
+      if (rho1 == 0.0 || !std::isfinite(rho1)) break;  // breakdown
+      const double beta = (rho1 / rho) * (alpha / omega);
+      // p = r + beta (p - omega v), v = -Vn
+      axpy3(Pv, Vn, beta == 0.0 ? 0.0 : omega);
+      if (beta != 1.0) {  // p *= beta, then p += r
+        V3 tmp = Pv;
+        cudaMemsetAsync(Y.x, 0, nx * sizeof(double), c.stream);
+        cudaMemsetAsync(Y.p, 0, ne * sizeof(double), c.stream);
+        cudaMemsetAsync(Y.l, 0, nx * sizeof(double), c.stream);
+        axpy3(Y, tmp, beta);
+        copy3(Pv, Y);
+      }
+      axpy3(Pv, R, 1.0);
+      precond(Y, Pv);
+      neg_matvec(Vn, Y);
+      const double rv = dot3(Rh, Vn);  // = -(rh . v)
+      if (rv == 0.0 || !std::isfinite(rv)) break;
+      alpha = -rho1 / rv;
+      copy3(Sv, R);
+      axpy3(Sv, Vn, alpha);  // s = r - alpha v
+      axpy3(Z, Y, alpha);
+      ++kits;
+      const double sn = std::sqrt(dot3(Sv, Sv));
+      if (sn <= tol * bn) { copy3(R, Sv); break; }
+      precond(Zt, Sv);
+      neg_matvec(Tn, Zt);
+      const double tt = dot3(Tn, Tn);
+      if (tt == 0.0 || !std::isfinite(tt)) { copy3(R, Sv); break; }
+      omega = -dot3(Tn, Sv) / tt;  // (t . s) / (t . t)
+      axpy3(Z, Zt, omega);
+      copy3(R, Sv);
+      axpy3(R, Tn, omega);  // r = s - omega t
+      const double rk = std::sqrt(dot3(R, R));
+      if (rk <= tol * bn || omega == 0.0) break;
+      rho = rho1;
+    }
+    // the true FP64 residual of the final iterate
+    launch_residual(c, c.bx, c.bp, c.bl, c.zx, c.zp, c.zl, c.rx, c.rp, c.rl);
+    rn = std::sqrt(device_sumsq3(c, c.rx, nx, c.rp, ne, c.rl, nx));
+    if (!(rn == rn)) { h->last_error = "non-finite residual"; return SGN_ENONFINITE; }
   }
   batch_record_solve(c);
   c.inst_have_kkt = c.n_inst > 0;
@@ -725,6 +827,7 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     rep->refine_steps = steps;
+    rep->krylov_iters = kits;
     rep->residual = bn > 0 ? rn / bn : rn;
     for (int i = 0; i < 32; ++i) rep->history[i] = i <= steps ? hist[i] : 0.0;
     rep->seconds = ms * 1e-3;
@@ -847,6 +950,11 @@ sgn_status sgn_step_graph(sgn_t h, sgn_precision prec, int32_t refine_steps, con
   Store &st = prec == SGN_MIXED ? h->kkt32 : h->kkt64;
   if (!st.enabled) return SGN_ESTATE;
   if (!h->cap_stream) return SGN_ECUDA;
+  if (st.eps_x != 0.0 || st.eps_l != 0.0) {  // the step graph factors M itself
+    destroy_graphs(st);
+    st.eps_x = st.eps_l = 0.0;
+    if (h->step_graph) { cudaGraphExecDestroy(h->step_graph); h->step_graph = nullptr; }
+  }
   Ctx &c = *h;
   const int64_t nx = (int64_t)c.S.n_free * c.S.dim, ne = c.S.n_elem;
   const void *key[6] = {x_d, p_d, dx_d, dp_d, dl_d, &st};

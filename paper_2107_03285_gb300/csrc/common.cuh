@@ -98,6 +98,9 @@ struct Store {
   int64_t front_elems = 0, cb_elems = 0, w_elems = 0, rhs_elems = 0, piv_elems = 0, xinv_elems = 0;
   int64_t cb_sum = 0;  // sum of all contribution blocks (what the arena saves against)
   bool factored = false;
+  // stabilization of the saddle-point fronts (eps_x on the x diagonal,
+  // -eps_l on the lambda diagonal): 0 for the factor of the matrix itself
+  double eps_x = 0.0, eps_l = 0.0;
   // CUDA graphs of the static launch sequences (captured once, replayed)
   cudaGraphExec_t fgraph = nullptr;        // factorization
   cudaGraphExec_t fgraph_prof = nullptr;   // factorization with events around the trailing updates
@@ -152,6 +155,8 @@ struct Ctx {
   double *zx = nullptr, *zp = nullptr, *zl = nullptr;
   double *rx = nullptr, *rp = nullptr, *rl = nullptr;
   double *red = nullptr;            // reduced rhs / solution [n_free * 2d]
+  static constexpr int KRY_VECS = 8;  // BiCGSTAB: r^, p, -v, y, s, z~, -t, zero
+  double *kry = nullptr;            // [KRY_VECS][2 n_x + n_p]
   double *partial = nullptr;        // reduction scratch
   double *partial2 = nullptr;       // [2][n_partial]: ||r||^2, ||b||^2 partial sums of a graph step
   int n_partial = 0;

@@ -43,7 +43,8 @@ template <typename T, int D, int DPN>
 __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t item_base,
                                                         const double *__restrict__ Kv,
                                                         const double *__restrict__ Gv,
-                                                        const double *__restrict__ wA) {
+                                                        const double *__restrict__ wA, double eps_x,
+                                                        double eps_l) {
   const int64_t item = item_base + blockIdx.x;
   const int s = d.item_sn[item], P = d.item_P[item];
   const int nown = d.sn_nown[s];
@@ -76,7 +77,12 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
         if (rx >= cx + 1) *F.at(rx, cx + 1) += T(kv);        // (x row, lambda col)
         if (rx + 1 >= cx) *F.at(rx + 1, cx) += T(kv);        // (lambda row, x col)
         if (rx + 1 >= cx + 1) *F.at(rx + 1, cx + 1) += T(-gv);
-        if (Q == P && a == b) *F.at(rx, cx) += T(wA[(int64_t)r * D + a]);
+        // A on the x diagonal; the optional stabilization eps_x (x) and
+        // -eps_l (lambda) of a preconditioning factor
+        if (Q == P && a == b) {
+          *F.at(rx, cx) += T(wA[(int64_t)r * D + a] + eps_x);
+          if (eps_l != 0.0) *F.at(rx + 1, cx + 1) += T(-eps_l);
+        }
       } else {
         int ri = Q * D + a, ci = P * D + b;
         if (ri >= ci) *F.at(ri, ci) += T(kv);
@@ -826,10 +832,11 @@ void factor_impl(Ctx &c, Store &st) {
     {
       ProfScope ps(c, SGN_PROF_FRONT_ASSEMBLY);
       const dim3 ga((unsigned)nitems);
-      if (D == 2 && st.dpn == 4) k_front_assemble<T, 2, 4><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-      else if (D == 2) k_front_assemble<T, 2, 2><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-      else if (st.dpn == 6) k_front_assemble<T, 3, 6><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
-      else k_front_assemble<T, 3, 3><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA);
+      const double ex = st.kkt ? st.eps_x : 0.0, el = st.kkt ? st.eps_l : 0.0;
+      if (D == 2 && st.dpn == 4) k_front_assemble<T, 2, 4><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else if (D == 2) k_front_assemble<T, 2, 2><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else if (st.dpn == 6) k_front_assemble<T, 3, 6><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else k_front_assemble<T, 3, 3><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
       c.count();
     }
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;

@@ -155,16 +155,22 @@ class SGN:
         self._pv = self._dev(p, (self.n_elem,))
         B._check(self.lib.sgn_assemble(self.h, self._p(self._x), self._p(self._pv)), "sgn_assemble", self.h)
 
-    def factor(self, precision=B.FP64, report=True):
+    def factor(self, precision=B.FP64, report=True, eps_x=0.0, eps_lambda=0.0):
+        """LDL^T of the assembled matrix, or (eps_x, eps_lambda > 0) of its
+        stabilized form (sgn_factor_ex), which the solves use as a
+        preconditioner."""
         rep = B.FactorReport() if report else None
-        B._check(self.lib.sgn_factor(self.h, int(precision), C.byref(rep) if report else None), "sgn_factor", self.h)
+        opts = B.FactorOpts(float(eps_x), float(eps_lambda))
+        B._check(self.lib.sgn_factor_ex(self.h, int(precision), C.byref(opts), C.byref(rep) if report else None),
+                 "sgn_factor_ex", self.h)
         return rep
 
-    def solve(self, mode=B.RHS_KKT, g=None, max_refine=0, tol=0.0, report=True, out=None):
+    def solve(self, mode=B.RHS_KKT, g=None, max_refine=0, tol=0.0, report=True, out=None, method=B.SOLVE_AUTO,
+              max_krylov=0):
         dx, dp, dl = out if out is not None else (self._empty(self.n_nodes, self.dim), self._empty(self.n_elem),
                                                    self._empty(self.n_nodes, self.dim))
         gd = self._dev(g, (self.n_elem,)) if g is not None else None
-        opts = B.SolveOpts(int(max_refine), float(tol))
+        opts = B.SolveOpts(int(max_refine), float(tol), int(method), int(max_krylov))
         rep = B.SolveReport() if report else None
         B._check(self.lib.sgn_solve(self.h, int(mode), self._p(gd), self._p(dx), self._p(dp), self._p(dl),
                                     C.byref(opts), C.byref(rep) if report else None), "sgn_solve", self.h)
