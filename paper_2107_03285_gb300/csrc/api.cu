@@ -197,6 +197,30 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
     s.h_fwd_lvl.push_back((int64_t)s.h_fwd_items.size());
     s.h_bwd_lvl.push_back((int64_t)s.h_bwd_items.size());
   }
+  // panel-kernel items per (level, outer block): band-major, so that the
+  // owners of the block's panels (bands 0 and 1 of every front) come first
+  s.h_blk_items.clear();
+  s.h_blk_off.assign(1, 0);
+  for (const auto &lv : c.S.level_fronts) {
+    int64_t max_ns = 0;
+    for (int i : lv) max_ns = std::max<int64_t>(max_ns, (int64_t)c.S.sn[i].nown * dpn);
+    for (int64_t K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
+      for (int32_t b = 0;; ++b) {
+        bool any = false;
+        int32_t q = 0;
+        for (int i : lv) {
+          const int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
+          if (ns > K0 && f - K0 > (int64_t)128 * b) {
+            s.h_blk_items.push_back({q, b});
+            any = true;
+          }
+          ++q;
+        }
+        if (!any) break;
+      }
+      s.h_blk_off.push_back((int64_t)s.h_blk_items.size());
+    }
+  }
   // self-check (the substitutions' waits rely on it): an item of key k waits
   // only on keys 0 .. k - 1 of its own front, so each front's items must
   // appear with keys 0, 1, 2, ... in list order within their level
@@ -319,11 +343,14 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     s.yz = cv.take<double>(s.piv_elems);
     s.pub = cv.take<unsigned long long>(s.piv_elems);
     s.pflag = fp32 ? nullptr : cv.take<unsigned>(s.piv_elems);
+    s.fflag = cv.take<unsigned>(s.piv_elems);
     s.ctl = cv.take<unsigned>(16);
     {
       SolveItem *it;
       st_up(it, s.h_fwd_items); s.fwd_items = it;
       st_up(it, s.h_bwd_items); s.bwd_items = it;
+      BandItem *bi;
+      st_up(bi, s.h_blk_items); s.blk_items = bi;
     }
     if (fp32) {
       for (int q = 0; q < 4; ++q) s.wk[q] = cv.take<float>(s.w_elems);
@@ -543,6 +570,7 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
     if (!st->enabled) continue;
     CUDA_TRY(h, cudaMemsetAsync(st->pub, 0, (size_t)st->piv_elems * sizeof(unsigned long long), h->stream));
     if (st->pflag) CUDA_TRY(h, cudaMemsetAsync(st->pflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(st->fflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(st->ctl, 0, 16 * sizeof(unsigned), h->stream));
   }
   // uploads read host vectors owned by h->S or by the carve's thread-local

@@ -52,6 +52,12 @@ struct SolveItem {
   int32_t q, key;
 };
 
+// one CTA of an outer block's panel kernel: a 128-row band of front q (q
+// indexes the level-ordered front list)
+struct BandItem {
+  int32_t q, band;
+};
+
 // one multifrontal store: fronts + pivots + solve buffers of one kind
 struct Store {
   bool enabled = false;
@@ -92,6 +98,13 @@ struct Store {
   std::vector<SolveItem> h_fwd_items, h_bwd_items;
   std::vector<int64_t> h_fwd_lvl, h_bwd_lvl;  // per level: range in the item lists
   bool sched_ok = true;  // every item listed after the items it waits on
+  // panel kernel of each (level, outer block): its bands, every front's
+  // bands 0 and 1 (the panels' owners) first; fflag: one flag per panel,
+  // set to the factorization's epoch (ctl[4]) once the panel is factored
+  const BandItem *blk_items = nullptr;
+  std::vector<BandItem> h_blk_items;
+  std::vector<int64_t> h_blk_off;
+  unsigned *fflag = nullptr;
   const int64_t *front_off = nullptr, *cb_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
   const int64_t *xinv_off = nullptr;
   std::vector<int64_t> h_front_off, h_cb_off, h_w_off, h_rhs_off, h_piv_off, h_xinv_off;

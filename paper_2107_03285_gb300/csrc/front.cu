@@ -131,57 +131,73 @@ __global__ void __launch_bounds__(256) k_front_assemble(DevSym d, SV sv, int64_t
   }
 }
 
-// ------------------------------------------------------- Bunch-Kaufman panel
-// Bunch-Kaufman LDL^T of the w x w block a (lower triangle, a[j][i] = A(i, j))
-// by the whole CTA: 1x1 / 2x2 pivots, alpha = (1 + sqrt 17) / 8, pivot search
-// restricted to the block, eliminations in CT.  Magnitudes are compared
-// exactly (max of |CT| values); every pivot test is taken in FP64.
-// Deterministic: every warp, and every CTA that runs it on the same block,
-// takes the same decisions.
-// On return column j of a holds W(:, j) = L(:, j) D_j, unscaled (the caller
-// forms L from it and D: bk_unit_lower), sD0 / sD1 the 1x1 and 2x2 pivots
-// (a 1x1 pivot below the static-pivot threshold already replaced), stype
-// their kinds and sperm the block's permutation (position -> original index).
-// Run by all NT threads (NT a multiple of 32, w <= 64).  Every warp searches
-// the pivot column itself (no barrier for the decision), holds the pivot
-// column(s) in registers (rows lane and lane + 32 below the pivot) and
-// broadcasts the entries it needs by shuffles, and owns the columns warp,
-// warp + NT/32, ... of the update: one barrier per step unless rows swap.
-template <typename CT, int NT>
-__device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double eps_rel, int *sperm, int *stype,
-                                double *sD0, double *sD1, unsigned long long *counters, const bool count) {
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// ------------------------------------------------- outer-block panel kernel
+// One launch factors the pivot panels of one 256-column outer block [K0,
+// kend) of every active front of a level.  Each CTA owns a band of 128 rows
+// of one front (rows K0 + 128 b ...).  For every panel [k, k + w) in turn:
+//   * the band holding the panel's diagonal rows (the owner) forms the
+//     panel's diagonal block left-looking from the rows it factored itself
+//     (A11 = F11 - W[k:k+w, K0:k] L[k:k+w, K0:k]^T), factors it with
+//     Bunch-Kaufman in one warp, stages L11 / D / the permutation and
+//     publishes the panel (a release store of the factorization's epoch);
+//   * every band with rows below the panel waits (bounded) for that
+//     publication, then updates its rows left-looking by the block's earlier
+//     panels, permutes and solves them against L11 (W = L21 D and L21), and
+//     writes the K-major hi / lo copies the tensor-core update reads.
+// A CTA takes its (front, band) item by ticket; the items list every front's
+// bands 0 and 1 (the only owners) before all other bands, so every CTA a
+// band waits for has started before it.  A wait that expires records
+// DEV_TIMEOUT and the CTA gives up.
+
+constexpr int BAND = 128;                           // rows per CTA
+constexpr long long PANEL_WAIT_CYCLES = 1ll << 31;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned ld_acquire_flag(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_flag(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bunch-Kaufman LDL^T of the w x w block a (w <= 32; a[j][i] = A(i, j), lower
+// triangle) by one warp, lane i holding row i: 1x1 / 2x2 pivots, alpha =
+// (1 + sqrt 17) / 8, pivot search restricted to the block, eliminations in
+// CT; magnitudes compared exactly (max of |CT| values), every pivot test
+// taken in FP64 in lane 0.  On return column j of a holds W(:, j) =
+// L(:, j) D_j unscaled, sD0 / sD1 the 1x1 and 2x2 pivots (a 1x1 pivot below
+// the static-pivot threshold replaced), stype their kinds (0: 1x1, 1 / 2:
+// first / second of a pair) and sperm the block's permutation (position ->
+// original index).
+template <typename CT, int PITCH>
+__device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel, int *sperm, int *stype,
+                               double *sD0, double *sD1, unsigned long long *counters) {
+  const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
-  for (int t = tid; t < w; t += NT) { sperm[t] = t; stype[t] = 0; sD1[t] = 0.0; sD0[t] = 0.0; }
+  sperm[lane] = lane; stype[lane] = 0; sD0[lane] = 0.0; sD1[lane] = 0.0;
   CT bm = CT(0);
   for (int jj = 0; jj < w; ++jj)
-    for (int i = jj + lane; i < w; i += 32) bm = max(bm, (CT)fabs(a[jj][i]));
+    if (lane >= jj && lane < w) bm = max(bm, (CT)fabs(a[jj][lane]));
   for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(FULL, bm, o));
   const double thresh = eps_rel * fmax((double)bm, 1e-300);
-  // the largest CT not above thresh: |x| > thresh  <=>  |x| > thresh_c for
-  // every CT value x, so the static-pivot test needs no FP64 arithmetic
+  // the largest CT not above thresh: |x| > thresh  <=>  |x| > thresh_c
   CT thresh_c = (CT)thresh;
   if ((double)thresh_c > thresh) thresh_c = nextafter(thresh_c, CT(0));
-  __syncthreads();
+  __syncwarp();
   int j = 0;
   while (j < w) {
-    // ---- pivot search (every warp; the column max is exact in CT)
+    // ---- pivot search: largest |A(i, j)|, i > j (ties to the lowest index)
     CT cm = CT(-1);
     int ci = w;
-    for (int i = j + 1 + lane; i < w; i += 32) {
-      const CT v = (CT)fabs(a[j][i]);
-      if (v > cm) { cm = v; ci = i; }
-    }
+    if (lane > j && lane < w) { cm = (CT)fabs(a[j][lane]); ci = lane; }
     for (int o = 16; o > 0; o >>= 1) {
       const CT ov = __shfl_xor_sync(FULL, cm, o);
       const int oi = __shfl_xor_sync(FULL, ci, o);
       if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
     }
     const int imax = ci;
-    // the FP64 tests run in lane 0 only (FP64 issue is scarce); the
-    // decision reaches the other lanes by shuffles
     const CT akk = a[j][j];
     int code = 0;  // 0: 1x1 at j, 1: needs the row of imax
     if (lane == 0) {
@@ -190,13 +206,10 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
     }
     code = __shfl_sync(FULL, code, 0);
     int kstep = 1, kp = j;
-    const bool read_row = code == 1;
-    if (read_row) {
+    if (code == 1) {
+      // largest off-diagonal |A(imax, t)|, t in [j, w), t != imax
       CT rm = CT(0);
-      for (int t = j + lane; t < w; t += 32) {
-        if (t == imax) continue;
-        rm = max(rm, (CT)(t < imax ? fabs(a[t][imax]) : fabs(a[imax][t])));
-      }
+      if (lane >= j && lane < w && lane != imax) rm = (CT)(lane < imax ? fabs(a[lane][imax]) : fabs(a[imax][lane]));
       for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL, rm, o));
       const CT aii = a[imax][imax];
       int dec = 0;  // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
@@ -211,13 +224,12 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
       else if (dec == 2) { kstep = 2; kp = imax; }
     }
     const int kk = j + kstep - 1;
-    // the search read entries the update (or the swap) writes: wait for all warps
-    if (read_row || kp != kk) __syncthreads();
+    __syncwarp();
     if (kp != kk) {
-      // symmetric interchange of kk and kp in the trailing lower triangle and
-      // of the already eliminated part of both rows
+      // symmetric interchange of kk and kp (> kk) in the trailing lower
+      // triangle and in the already eliminated part of both rows
       const int n1 = w - kp - 1, n2 = kp - kk - 1, n3 = kk;
-      for (int idx = tid; idx < 1 + n1 + n2 + n3; idx += NT) {
+      for (int idx = lane; idx < 1 + n1 + n2 + n3; idx += 32) {
         if (idx == 0) {
           CT t0 = a[kk][kk]; a[kk][kk] = a[kp][kp]; a[kp][kp] = t0;
           int tp = sperm[kk]; sperm[kk] = sperm[kp]; sperm[kp] = tp;
@@ -232,58 +244,50 @@ __device__ void bk_factor_block(CT (*a)[MAXNB + 1], const int w, const double ep
           CT t0 = a[cc][kk]; a[cc][kk] = a[cc][kp]; a[cc][kp] = t0;
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
     if (kstep == 1) {
       CT dj = a[j][j];
       const bool perturb = !(fabs(dj) > thresh_c);
       if (perturb) dj = (dj >= CT(0)) ? (CT)thresh : (CT)-thresh;
-      if (tid == 0) {
+      if (lane == 0) {
         sD0[j] = (double)dj; stype[j] = 0;
-        if (perturb && count) atomicAdd(counters + 0, 1ull);
+        if (perturb) atomicAdd(counters + 0, 1ull);
       }
       const CT rd = CT(1) / dj;
-      const int i0 = j + 1 + lane, i1 = i0 + 32;
-      const CT l0 = i0 < w ? a[j][i0] : CT(0), l1 = i1 < w ? a[j][i1] : CT(0);
-      for (int cc = j + 1 + warp; cc < w; cc += NW) {
-        const int src = cc - j - 1;  // lane holding row cc of the pivot column
-        const CT fc = __shfl_sync(FULL, src < 32 ? l0 : l1, src & 31) * rd;
-        if (i0 < w && i0 >= cc) a[cc][i0] -= l0 * fc;
-        if (i1 < w && i1 >= cc) a[cc][i1] -= l1 * fc;
+      const CT l = (lane > j && lane < w) ? a[j][lane] : CT(0);
+      for (int cc = j + 1; cc < w; ++cc) {
+        const CT fc = __shfl_sync(FULL, l, cc) * rd;
+        if (lane >= cc && lane < w) a[cc][lane] -= l * fc;
       }
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
       const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
-      if (tid == 0) {
+      if (lane == 0) {
         sD0[j] = (double)d11; sD1[j] = (double)d21; sD0[j + 1] = (double)d22;
         stype[j] = 1; stype[j + 1] = 2;
-        if (count) atomicAdd(counters + 1, 1ull);
+        atomicAdd(counters + 1, 1ull);
       }
-      const int i0 = j + 2 + lane, i1 = i0 + 32;
-      const CT u0 = i0 < w ? a[j][i0] : CT(0), v0 = i0 < w ? a[j + 1][i0] : CT(0);
-      const CT u1 = i1 < w ? a[j][i1] : CT(0), v1 = i1 < w ? a[j + 1][i1] : CT(0);
-      const CT p0 = u0 * i11 + v0 * i21, q0 = u0 * i21 + v0 * i22;  // (L1, L2) of row i0
-      const CT p1 = u1 * i11 + v1 * i21, q1 = u1 * i21 + v1 * i22;
-      for (int cc = j + 2 + warp; cc < w; cc += NW) {
-        const int src = cc - j - 2;
-        const CT w1 = __shfl_sync(FULL, src < 32 ? u0 : u1, src & 31);
-        const CT w2 = __shfl_sync(FULL, src < 32 ? v0 : v1, src & 31);
-        if (i0 < w && i0 >= cc) a[cc][i0] -= p0 * w1 + q0 * w2;
-        if (i1 < w && i1 >= cc) a[cc][i1] -= p1 * w1 + q1 * w2;
+      const bool in = lane > j + 1 && lane < w;
+      const CT u = in ? a[j][lane] : CT(0), v = in ? a[j + 1][lane] : CT(0);
+      const CT p = u * i11 + v * i21, q = u * i21 + v * i22;  // (L1, L2) of row lane
+      for (int cc = j + 2; cc < w; ++cc) {
+        const CT w1 = __shfl_sync(FULL, u, cc), w2 = __shfl_sync(FULL, v, cc);
+        if (lane >= cc && lane < w) a[cc][lane] -= p * w1 + q * w2;
       }
     }
-    __syncthreads();
+    __syncwarp();
     j += kstep;
   }
 }
 
-// L(i, j) (i > j) of a block factored by bk_factor_block, from its unscaled
+// L(i, j) (i > j) of a block factored by bk_factor_warp, from its unscaled
 // columns and pivots: a 1x1 column is divided by its pivot, a 2x2 pair is
 // multiplied by the pair's inverse; L is zero inside a 2x2 pivot
-template <typename CT>
-__device__ __forceinline__ CT bk_unit_lower(const CT (*a)[MAXNB + 1], int i, int j, const int *stype,
-                                            const double *sD0, const double *sD1) {
+template <typename CT, int PITCH>
+__device__ __forceinline__ CT bk_unit_lower(const CT (*a)[PITCH], int i, int j, const int *stype, const double *sD0,
+                                            const double *sD1) {
   const int ty = stype[j];
   if (ty == 0) return a[j][i] * (CT(1) / (CT)sD0[j]);
   const int j0 = ty == 1 ? j : j - 1;  // first column of the pair
@@ -293,59 +297,6 @@ __device__ __forceinline__ CT bk_unit_lower(const CT (*a)[MAXNB + 1], int i, int
   const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
   const CT u = a[j0][i], v = a[j0 + 1][i];
   return ty == 1 ? u * i11 + v * i21 : u * i21 + v * i22;
-}
-
-// Pivot panel [k, k + w), diagonal block (one CTA per active front):
-// Bunch-Kaufman of the block, which already holds every update (the
-// trailing updates of earlier outer blocks and, through k_panel_rows, those
-// of the earlier panels of this block).  L11 (D on its diagonal) is staged,
-// D and the permutation go to the pivot arrays; the front's diagonal block
-// itself is rewritten by the end-of-block kernel.
-template <typename T>
-__global__ void __launch_bounds__(128) k_panel_diag(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int nb, double eps_rel, unsigned long long *counters) {
-  using CT = T;
-  __shared__ CT a[MAXNB][MAXNB + 1];
-  __shared__ double sD0[MAXNB], sD1[MAXNB];
-  __shared__ int sperm[MAXNB], stype[MAXNB];
-  const int s = fronts[blockIdx.x];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const T *F = (const T *)sv.F + sv.front_off[s];
-  const int tid = threadIdx.x;
-  for (int base = tid; base < w * w; base += 8 * blockDim.x) {
-    CT v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int jj = idx / w, ii = idx - jj * w;
-      v[u] = (idx < w * w && ii >= jj) ? (CT)F[(int64_t)(k + ii) + (int64_t)(k + jj) * f] : CT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < w * w) a[idx / w][idx % w] = v[u];
-    }
-  }
-  __syncthreads();
-  bk_factor_block<CT, 128>(a, w, eps_rel, sperm, stype, sD0, sD1, counters, true);
-  __syncthreads();
-  T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    const int jj = idx / w, ii = idx - jj * w;
-    if (ii >= jj)
-      stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : T(bk_unit_lower<CT>(a, ii, jj, stype, sD0, sD1));
-  }
-  const int64_t po = sv.piv_off[s] + k;
-  if (tid < w) {
-    sv.piv_type[po + tid] = stype[tid];
-    sv.piv_perm[po + tid] = sperm[tid];
-    sv.D0[po + tid] = sD0[tid];
-    sv.D1[po + tid] = sD1[tid];
-  }
 }
 
 // four consecutive shared-memory values as one vector load (16-byte aligned)
@@ -358,66 +309,104 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-// Pivot panel [k, k + w), rows below it (128 rows per CTA, one row per
-// thread, NBT >= w the panel width it is compiled for):
-//   left-looking update of the rows by the earlier panels of the outer block,
-//   F21 -= W[rows, K0:k] L[k:k+w, K0:k]^T (the next chunk of W prefetched into
-//   registers while the current one is applied; L chunks read as vectors);
-//   permutation and forward substitution with L11 in registers (x = F21 P^T
-//   L11^{-T} = L21 D); L21 = x D^{-1}.  Writes L21 to the front, x to the outer
-//   block's W and (FP32 fronts with tensor cores) both as K-major hi / lo
-//   operand copies.  The CTAs whose rows belong to the later panels of the
-//   same outer block also apply this panel's contribution to those panels'
-//   diagonal blocks (right-looking), so that k_panel_diag finds them ready.
+// the panel's diagonal block, formed left-looking by its owner band:
+// a[jj][ii] = F(k + ii, k + jj) - sum_{t in [K0, k)} W(k + ii, t) L(k + jj, t)
+// (ii >= jj, zero elsewhere), then factored by warp 0; stage (L11 with D on
+// its diagonal) and the pivot arrays are written for the bands
 template <typename T, int NBT>
-__global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32_t *__restrict__ fronts, int k,
-                                                     int K0, int nb) {
+__device__ void owner_panel(const DevSym &d, const SV &sv, int s, int f, int ns, int K0, int k, int w, int nb,
+                            double eps_rel, unsigned long long *counters, T (*a)[NBT + 1], T (*Wc)[33],
+                            T (*Lc)[33], double *sD0, double *sD1, int *sperm, int *stype) {
+  const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  const T *W = (const T *)sv.W + sv.w_off[s];
+  const int64_t ldw = f - K0;
+  T acc[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) acc[r] = T(0);
+  for (int t0 = K0; t0 < k; t0 += 32) {
+    const int kc = min(32, k - t0);
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+      const int u = idx >> 5, r = idx & 31;  // column t0 + u, row k + r
+      const bool ok = u < kc && r < w;
+      Wc[r][u] = ok ? __ldcg(W + (int64_t)(k + r - K0) + (int64_t)(t0 - K0 + u) * ldw) : T(0);
+      Lc[r][u] = ok ? __ldcg(F + (int64_t)(k + r) + (int64_t)(t0 + u) * f) : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int u = 0; u < 32; ++u) {
+      const T lv = Lc[lane][u];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) acc[r] += Wc[grp + 4 * r][u] * lv;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int ii = grp + 4 * r, jj = lane;
+    if (ii < NBT && jj < NBT)
+      a[jj][ii] = (ii >= jj && ii < w) ? __ldcg(F + (int64_t)(k + ii) + (int64_t)(k + jj) * f) - acc[r] : T(0);
+  }
+  __syncthreads();
+  if (grp == 0) bk_factor_warp<T, NBT + 1>(a, w, eps_rel, sperm, stype, sD0, sD1, counters);
+  __syncthreads();
+  T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int jj = idx / w, ii = idx - jj * w;
+    if (ii >= jj)
+      stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : bk_unit_lower<T, NBT + 1>(a, ii, jj, stype, sD0, sD1);
+  }
+  const int64_t po = sv.piv_off[s] + k;
+  if (tid < w) {
+    sv.piv_type[po + tid] = stype[tid];
+    sv.piv_perm[po + tid] = sperm[tid];
+    sv.D0[po + tid] = sD0[tid];
+    sv.D1[po + tid] = sD1[tid];
+  }
+}
+
+// one panel [k, k + w) of the band's rows i in [max(rb0, k + w), rb1), one
+// row per thread (row rb0 + tid): left-looking update by the earlier panels
+// of the block, F21 -= W[rows, K0:k] L[k:k+w, K0:k]^T (the next chunk of W
+// prefetched while the current one is applied); permutation and forward
+// substitution with L11 (x = F21 P^T L11^{-T} = L21 D); L21 = x D^{-1}.
+// Writes L21 to the front, x to the block's W and (FP32 fronts with tensor
+// cores) both as K-major hi / lo operand copies.  Reads of data other CTAs
+// wrote go through L2 (ld.global.cg).
+template <typename T, int NBT>
+__device__ void band_panel_rows(const DevSym &d, const SV &sv, int s, int f, int ns, int K0, int k, int w, int nb,
+                                int rb0, int rb1, T *Lp, T *L11T, T *xs, T *sD0, T *sD1, T *sI0, T *sI1,
+                                int *sperm, int *stype) {
   using CT = T;
-  constexpr int RB = 128, KC = 32, XS = RB + 1;
-  extern __shared__ __align__(16) unsigned char rows_raw[];
-  CT *Lp = reinterpret_cast<CT *>(rows_raw);  // [KC][NBT]: L(k + t, K0 + cu + u)
-  CT *L11T = Lp + KC * NBT;                   // [NBT][NBT]: L11T[c][t] = L(t, c) for t > c, else 0
-  CT *xs = L11T + NBT * NBT;                  // [NBT][XS]: this CTA's rows, column t
-  __shared__ CT sD0[NBT], sD1[NBT], sI0[NBT], sI1[NBT];
-  __shared__ int sperm[NBT], stype[NBT];
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (k >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int w = min(nb, ns - k);
-  const int r0 = k + w;
-  const int nrows = f - r0;
-  if ((int)blockIdx.x * RB >= nrows) return;
+  constexpr int RB = BAND, KC = 32, XS = RB + 1;
   T *F = (T *)sv.F + sv.front_off[s];
   T *W = (T *)sv.W + sv.w_off[s];
   const int64_t ldw = f - K0;
   const int tid = threadIdx.x;
-  const int il = blockIdx.x * RB + tid;
-  const bool row_ok = il < nrows;
-  const int64_t i = r0 + il;
+  const int64_t i = (int64_t)rb0 + tid;
+  const bool row_ok = i >= k + w && i < rb1;
   const int kp_in = k - K0;
   const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
-  // every operand in one round trip: the row's panel entries, L11, pivots
+  __syncthreads();  // the shared buffers may still be read by the previous panel
   {
     CT v[NBT];
 #pragma unroll
-    for (int t = 0; t < NBT; ++t) v[t] = (row_ok && t < w) ? (CT)F[i + (int64_t)(k + t) * f] : CT(0);
+    for (int t = 0; t < NBT; ++t) v[t] = (row_ok && t < w) ? (CT)__ldcg(F + i + (int64_t)(k + t) * f) : CT(0);
     constexpr int PER = (NBT * NBT + 127) / 128;
     CT lt[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int idx = tid + q * 128;
       const int c = idx / NBT, t = idx - c * NBT;
-      lt[q] = (idx < NBT * NBT && c < t && t < w) ? (CT)stage[(int64_t)t * nb + c] : CT(0);
+      lt[q] = (idx < NBT * NBT && c < t && t < w) ? (CT)__ldcg(stage + (int64_t)t * nb + c) : CT(0);
     }
     const int64_t po = sv.piv_off[s] + k;
     if (tid < NBT) {
       const bool in = tid < w;
-      sD0[tid] = in ? (CT)sv.D0[po + tid] : CT(1);
-      sD1[tid] = in ? (CT)sv.D1[po + tid] : CT(0);
-      sperm[tid] = in ? sv.piv_perm[po + tid] : tid;
-      stype[tid] = in ? sv.piv_type[po + tid] : 0;
+      sD0[tid] = in ? (CT)__ldcg(sv.D0 + po + tid) : CT(1);
+      sD1[tid] = in ? (CT)__ldcg(sv.D1 + po + tid) : CT(0);
+      sperm[tid] = in ? __ldcg(sv.piv_perm + po + tid) : tid;
+      stype[tid] = in ? __ldcg(sv.piv_type + po + tid) : 0;
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q)
@@ -446,20 +435,20 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
   // left-looking update
   CT wr[KC];
 #pragma unroll
-  for (int u = 0; u < KC; ++u) wr[u] = (row_ok && u < kp_in) ? (CT)W[(i - K0) + (int64_t)u * ldw] : CT(0);
+  for (int u = 0; u < KC; ++u) wr[u] = (row_ok && u < kp_in) ? (CT)__ldcg(W + (i - K0) + (int64_t)u * ldw) : CT(0);
   for (int cu = 0; cu < kp_in; cu += KC) {
     const int kc = min(KC, kp_in - cu);
     __syncthreads();
     for (int idx = tid; idx < KC * NBT; idx += blockDim.x) {
       const int u = idx / NBT, t = idx - u * NBT;
-      Lp[idx] = (u < kc && t < w) ? (CT)F[(int64_t)(k + t) + (int64_t)(K0 + cu + u) * f] : CT(0);
+      Lp[idx] = (u < kc && t < w) ? (CT)__ldcg(F + (int64_t)(k + t) + (int64_t)(K0 + cu + u) * f) : CT(0);
     }
     __syncthreads();
     CT wn[KC];
     const int nx = cu + KC;
 #pragma unroll
     for (int u = 0; u < KC; ++u)
-      wn[u] = (row_ok && nx + u < kp_in) ? (CT)W[(i - K0) + (int64_t)(nx + u) * ldw] : CT(0);
+      wn[u] = (row_ok && nx + u < kp_in) ? (CT)__ldcg(W + (i - K0) + (int64_t)(nx + u) * ldw) : CT(0);
     if (row_ok) {
 #pragma unroll 4
       for (int t0 = 0; t0 < NBT; t0 += 4) {
@@ -514,61 +503,32 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
       xs[t * XS + tid] = l;  // own column of xs: no other thread reads it before the barrier
     }
   }
-  __syncthreads();
-  {
-    // later panels of this outer block: A(i, j) -= sum_t W(i, t) L(j, t) for
-    // rows i >= j of one panel; both rows belong to this CTA (panels are
-    // w-aligned from r0 and w divides the CTA's 128 rows)
-    const int kend_blk = min(K0 + FACTOR_BLOCK, ns);
-    const int rowbase = r0 + blockIdx.x * RB;
-    if (row_ok && i < kend_blk) {
-      const int pa = r0 + ((int)(i - r0) / w) * w;
-      const int pl = pa - rowbase;  // first local row of the panel
-      const int ni = (int)i - pa;   // columns pa .. i: ni + 1 of them
-      // all of this row's entries of the block loaded at once, then updated
-      CT cur[NBT];
-#pragma unroll
-      for (int q = 0; q < NBT; ++q) cur[q] = q <= ni ? (CT)F[i + (int64_t)(pa + q) * f] : CT(0);
-#pragma unroll
-      for (int t = 0; t < NBT; ++t) {
-        if (t >= w) break;
-        const CT xt = x[t];
-#pragma unroll
-        for (int q = 0; q < NBT; ++q) cur[q] -= xt * xs[t * XS + min(pl + q, RB - 1)];
-      }
-#pragma unroll
-      for (int q = 0; q < NBT; ++q)
-        if (q <= ni) F[i + (int64_t)(pa + q) * f] = T(cur[q]);
-    }
-  }
   if (sv.wk0) {
     // K-major hi / lo copies, written warp-cooperatively (lanes along t):
     // first L (already in xs), then W
     const int warp = tid >> 5, lane = tid & 31;
     const int wpad = (k + w == ns) ? ((k - K0 + w + 31) / 32) * 32 - (k - K0) : w;
     for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1) {
-        __syncthreads();
-        if (row_ok) {
+      __syncthreads();
+      if (pass == 1 && row_ok) {
 #pragma unroll
-          for (int t = 0; t < NBT; ++t) {
-            if (t >= w) break;
-            xs[t * XS + tid] = x[t];
-          }
+        for (int t = 0; t < NBT; ++t) {
+          if (t >= w) break;
+          xs[t * XS + tid] = x[t];
         }
-        __syncthreads();
       }
+      __syncthreads();
       float *hi = pass == 1 ? sv.wk0 : sv.wk2, *lo = pass == 1 ? sv.wk1 : sv.wk3;
       // rows are FACTOR_BLOCK floats apart and k - K0, wpad are multiples of 4:
       // every lane stores 4 consecutive entries as one 16-byte vector
-      const int q4 = wpad / 4;                 // vectors per row
+      const int q4 = wpad / 4;  // vectors per row
       const int rows_per_it = 32 / q4 > 0 ? 32 / q4 : 1;
       const int sub = lane / q4, t4 = (lane % q4) * 4;
       for (int rr = 0; rr < 32; rr += rows_per_it) {
         const int rloc = warp * 32 + rr + sub;
-        const int ilr = blockIdx.x * RB + rloc;
-        if (sub >= rows_per_it || rr + sub >= 32 || ilr >= nrows) continue;
-        const int64_t base = sv.w_off[s] + (int64_t)(r0 + ilr) * FACTOR_BLOCK + (k - K0);
+        const int64_t ig = (int64_t)rb0 + rloc;
+        if (sub >= rows_per_it || rr + sub >= 32 || ig < k + w || ig >= rb1) continue;
+        const int64_t base = sv.w_off[s] + ig * FACTOR_BLOCK + (k - K0);
         for (int t = t4; t < wpad; t += 4 * q4) {
           float v[4], h[4], l[4];
 #pragma unroll
@@ -583,6 +543,93 @@ __global__ void __launch_bounds__(128) k_panel_rows(DevSym d, SV sv, const int32
       }
     }
   }
+}
+
+template <typename T, int NBT>
+__global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int32_t *__restrict__ fronts,
+                                                      const BandItem *__restrict__ items, int K0, int nb,
+                                                      double eps_rel, unsigned long long *counters, unsigned *ctl,
+                                                      int *status) {
+  extern __shared__ __align__(16) unsigned char rows_raw[];
+  T *Lp = reinterpret_cast<T *>(rows_raw);  // [32][NBT]
+  T *L11T = Lp + 32 * NBT;                   // [NBT][NBT]
+  T *xs = L11T + NBT * NBT;                  // [NBT][129]
+  __shared__ T a[NBT][NBT + 1];
+  __shared__ T Wc[32][33], Lc[32][33];
+  __shared__ double bD0[NBT], bD1[NBT];
+  __shared__ int bperm[NBT], btype[NBT];
+  __shared__ T sD0[NBT], sD1[NBT], sI0[NBT], sI1[NBT];
+  __shared__ int sperm[NBT], stype[NBT];
+  __shared__ int s_item, s_abort;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_item = (int)atomicAdd(&ctl[5], 1u);
+    s_abort = 0;
+    if (s_item >= (int)gridDim.x) {  // counters not reset by the previous launch
+      atomicOr(status, DEV_TIMEOUT);
+      s_abort = 1;
+    } else if (*(volatile const int *)status & DEV_TIMEOUT) {
+      s_abort = 1;
+    }
+  }
+  __syncthreads();
+  if (!s_abort) {
+    const unsigned epoch = *(volatile const unsigned *)&ctl[4];
+    const BandItem it = items[s_item];
+    const int s = fronts[it.q];
+    const int dpn = sv.dpn;
+    const int ns = d.sn_nown[s] * dpn;
+    const int f = front_order(d, s, dpn);
+    const int kend = min(K0 + FACTOR_BLOCK, ns);
+    const int rb0 = K0 + BAND * it.band, rb1 = min(rb0 + BAND, f);
+    unsigned *flag = sv.fflag + sv.piv_off[s];
+    for (int k = K0; k < kend; k += nb) {
+      const int w = min(nb, ns - k);
+      const bool owner = (k - K0) / BAND == it.band;
+      if (!owner && rb1 <= k + w) break;  // no rows below this panel (nor below later ones)
+      if (owner) {
+        owner_panel<T, NBT>(d, sv, s, f, ns, K0, k, w, nb, eps_rel, counters, a, Wc, Lc, bD0, bD1, bperm, btype);
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_release_flag(flag + k, epoch);
+        }
+      } else {
+        if (tid == 0 && ld_acquire_flag(flag + k) != epoch) {
+          const long long t0 = clock64();
+          for (int n = 1; ld_acquire_flag(flag + k) != epoch; ++n) {
+            if ((n & 255) == 0 &&
+                ((*(volatile const int *)status & DEV_TIMEOUT) || clock64() - t0 > PANEL_WAIT_CYCLES)) {
+              atomicOr(status, DEV_TIMEOUT);
+              s_abort = 1;
+              break;
+            }
+          }
+        }
+        __syncthreads();
+        if (s_abort) break;
+      }
+      if (rb1 > k + w)
+        band_panel_rows<T, NBT>(d, sv, s, f, ns, K0, k, w, nb, rb0, rb1, Lp, L11T, xs, sD0, sD1, sI0, sI1, sperm,
+                                stype);
+    }
+  }
+  // the last CTA to finish resets the ticket counters for the next launch
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[6], 1u) == gridDim.x - 1) {
+      atomicExch(&ctl[5], 0u);
+      atomicExch(&ctl[6], 0u);
+    }
+  }
+}
+
+// a new factorization: a new epoch for the panel flags, ticket counters cleared
+__global__ void k_factor_begin(unsigned *ctl) {
+  ctl[4] += 1u;
+  ctl[5] = 0u;
+  ctl[6] = 0u;
 }
 
 // applies the pivot permutations of the panels of the outer block [K0, kend)
@@ -825,7 +872,10 @@ void factor_impl(Ctx &c, Store &st) {
   cudaMemsetAsync(c.counters, 0, 8 * sizeof(int64_t), c.stream);
   // panel kernels compiled for 16 and 32 columns
   const int nbt = nb <= 16 ? 16 : 32;
-  const size_t rows_smem = (size_t)(32 * nbt + nbt * nbt + nbt * 129) * sizeof(T);
+  const size_t panels_smem = (size_t)(32 * nbt + nbt * nbt + nbt * 129) * sizeof(T);
+  k_factor_begin<<<1, 1, 0, c.stream>>>(st.ctl);
+  c.count();
+  int64_t blk = 0;  // index into the store's per-(level, outer block) item ranges
   for (int L = 0; L < c.S.n_levels; ++L) {
     LevelInfo li = level_info(c, L, st.dpn);
     int64_t nitems = li.i1 - li.i0;
@@ -843,28 +893,25 @@ void factor_impl(Ctx &c, Store &st) {
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
     for (int K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
       const int kstop = std::min(K0 + FACTOR_BLOCK, max_ns);
-      for (int k = K0; k < kstop; k += nb) {
-        int na = n_active(li, k);
-        int max_rows = 0;
+      {
+        // every panel of the block in one launch (one CTA per 128-row band)
+        int na = n_active(li, K0);
         double fl = 0.0;
-        for (int q = 0; q < na; ++q) {
-          int w = std::min(nb, li.ns[q] - k);
-          max_rows = std::max(max_rows, li.f[q] - k - w);
-          double nr = li.f[q] - k;
-          fl += 2.0 * (nr * w - w * (w - 1) / 2.0) * (k - K0);  // left-looking panel update
-        }
-        {
-          ProfScope ps(c, SGN_PROF_PIVOT);
-          k_panel_diag<T><<<na, 128, 0, c.stream>>>(c.ds, sv, fronts, k, nb, eps_rel, ctr);
-          c.count();
-        }
-        if (max_rows > 0) {
-          ProfScope ps(c, SGN_PROF_TRSM, fl);
-          dim3 gp((max_rows + 127) / 128, na);
-          if (nbt == 16) k_panel_rows<T, 16><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
-          else k_panel_rows<T, 32><<<gp, 128, rows_smem, c.stream>>>(c.ds, sv, fronts, k, K0, nb);
-          c.count();
-        }
+        for (int q = 0; q < na; ++q)
+          for (int k = K0; k < std::min(K0 + FACTOR_BLOCK, li.ns[q]); k += nb) {
+            const double w = std::min(nb, li.ns[q] - k), nr = li.f[q] - k;
+            fl += 2.0 * (nr * w - w * (w - 1) / 2.0) * (k - K0);  // left-looking panel updates
+          }
+        const int64_t b0 = st.h_blk_off[blk], b1 = st.h_blk_off[blk + 1];
+        ++blk;
+        ProfScope ps(c, SGN_PROF_TRSM, fl);
+        if (nbt == 16)
+          k_block_panels<T, 16><<<(unsigned)(b1 - b0), 128, panels_smem, c.stream>>>(
+              c.ds, sv, fronts, st.blk_items + b0, K0, nb, eps_rel, ctr, st.ctl, c.status);
+        else
+          k_block_panels<T, 32><<<(unsigned)(b1 - b0), 128, panels_smem, c.stream>>>(
+              c.ds, sv, fronts, st.blk_items + b0, K0, nb, eps_rel, ctr, st.ctl, c.status);
+        c.count();
       }
       int na = n_active(li, K0);
       int max_rows = 0;
@@ -1019,7 +1066,7 @@ void set_kernel_attributes() {
   static bool done = false;
   if (done) return;
   done = true;
-  cudaFuncSetAttribute(k_panel_rows<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_block_panels<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((32 * 32 + 32 * 32 + 32 * 129) * sizeof(double)));
   cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
   set_solve_attributes();

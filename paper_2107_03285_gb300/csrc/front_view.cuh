@@ -20,6 +20,7 @@ struct SV {  // store view passed to kernels
   double *yz;                    // y, z = D^{-1} y, v of the substitutions (pivot order)
   unsigned long long *pub;       // published block values of the substitutions
   unsigned *pflag;               // their tags (FP64 fronts)
+  unsigned *fflag;               // panel-published flags of the factorization (epoch tags)
   const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off, *xinv_off;
   int dpn;
   int kkt;
@@ -28,7 +29,7 @@ struct SV {  // store view passed to kernels
 inline SV view(Store &s) {
   SV v;
   v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
-  v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz;
+  v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz; v.fflag = s.fflag;
   v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
