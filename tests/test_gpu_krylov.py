@@ -73,15 +73,21 @@ def test_bicgstab_recovers_the_solution(P, case, prec_name, tol):
 
 
 def test_bicgstab_from_the_start_and_paper_stabilization(P, case):
-    """SGN_SOLVE_BICGSTAB with the factor of M converges in a few iterations;
-    with the paper's stabilization (eps_x = eps_lambda = 1e-6) the default
-    path needs no Krylov iterations at all."""
+    """SGN_SOLVE_BICGSTAB with the FP32 factor of M (whose first solve is
+    only FP32-accurate) converges in a few iterations; with the FP64 factor
+    the first solve already meets the tolerance and no iteration runs; with
+    the paper's stabilization (eps_x = eps_lambda = 1e-6) the default path
+    needs no Krylov iterations at all."""
     prob, x, dp_ref, eps = case
-    s = P.SGN.from_problem(prob, stores=P.STORE_FP64)
+    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED)
     s.assemble(x, prob.p0)
+    s.factor(P.MIXED)
+    _, dp, _, rep = s.solve(P.RHS_KKT, method=P.binding.SOLVE_BICGSTAB)
+    assert rep.refine_steps == 0 and 1 <= rep.krylov_iters <= 10 and rep.residual <= 1e-12
+    assert _rel(dp.cpu().numpy(), dp_ref) < 1e-8
     s.factor(P.FP64)
     _, dp, _, rep = s.solve(P.RHS_KKT, method=P.binding.SOLVE_BICGSTAB)
-    assert 1 <= rep.krylov_iters <= 5 and rep.residual <= 1e-12
+    assert rep.krylov_iters == 0 and rep.residual <= 1e-12
     assert _rel(dp.cpu().numpy(), dp_ref) < 1e-9
     s.factor(P.FP64, eps_x=1e-6, eps_lambda=1e-6)
     _, dp, _, rep = s.solve(P.RHS_KKT)
