@@ -161,22 +161,45 @@ __device__ __forceinline__ void st_release_flag(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// The Bunch-Kaufman pivot tests, decided exactly as their FP64 evaluation:
+//   ge_alpha(a, c):      a >= alpha * c                 (FP64 product)
+//   ge_alpha_sq(a, r, c): a * r >= alpha * (c * c)       (FP64 products)
+// with a, r, c values of the front's type.  For FP32 fronts the comparison is
+// first made in FP32; the FP32 operands differ from the FP64 ones by less
+// than 2^-22 relative, so a gap larger than 2^-20 of the larger side decides
+// it, and only a near tie runs the FP64 arithmetic (the FP64 pipe of this
+// part issues a warp instruction every ~64 cycles).
+constexpr double BK_ALPHA = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+__device__ __forceinline__ bool ge_alpha(float a, float c) {
+  const float r = 0.64038820f * c;
+  const float g = a - r;
+  if (fabsf(g) > 0x1p-20f * fmaxf(a, r)) return g > 0.f;
+  return (double)a >= BK_ALPHA * (double)c;
+}
+__device__ __forceinline__ bool ge_alpha(double a, double c) { return a >= BK_ALPHA * c; }
+__device__ __forceinline__ bool ge_alpha_sq(float a, float r, float c) {
+  const float lhs = a * r, rhs = (0.64038820f * c) * c;
+  const float g = lhs - rhs;
+  if (fabsf(g) > 0x1p-20f * fmaxf(lhs, rhs)) return g > 0.f;
+  return (double)a * (double)r >= BK_ALPHA * ((double)c * (double)c);
+}
+__device__ __forceinline__ bool ge_alpha_sq(double a, double r, double c) { return a * r >= BK_ALPHA * (c * c); }
+
 // Bunch-Kaufman LDL^T of the w x w block a (w <= 32; a[j][i] = A(i, j), lower
 // triangle) by one warp, lane i holding row i: 1x1 / 2x2 pivots, alpha =
 // (1 + sqrt 17) / 8, pivot search restricted to the block, eliminations in
-// CT; magnitudes compared exactly (max of |CT| values), every pivot test
-// taken in FP64 in lane 0.  On return column j of a holds W(:, j) =
-// L(:, j) D_j unscaled, sD0 / sD1 the 1x1 and 2x2 pivots (a 1x1 pivot below
-// the static-pivot threshold replaced), stype their kinds (0: 1x1, 1 / 2:
-// first / second of a pair) and sperm the block's permutation (position ->
-// original index).
+// CT, magnitudes compared exactly (max of |CT| values), pivot tests decided
+// as in FP64 (ge_alpha, ge_alpha_sq) in lane 0.  On return column j of a
+// holds W(:, j) = L(:, j) D_j unscaled, sD0 / sD1 (32 entries) the 1x1 and
+// 2x2 pivots (a 1x1 pivot below the static-pivot threshold replaced), stype
+// their kinds (0: 1x1, 1 / 2: first / second of a pair) and sperm the
+// block's permutation (position -> original index).
 template <typename CT, int PITCH>
 __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel, int *sperm, int *stype,
-                               double *sD0, double *sD1, unsigned long long *counters) {
+                               CT *sD0, CT *sD1, unsigned long long *counters) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
-  sperm[lane] = lane; stype[lane] = 0; sD0[lane] = 0.0; sD1[lane] = 0.0;
+  sperm[lane] = lane; stype[lane] = 0; sD0[lane] = CT(0); sD1[lane] = CT(0);
   CT bm = CT(0);
   for (int jj = 0; jj < w; ++jj)
     if (lane >= jj && lane < w) bm = max(bm, (CT)fabs(a[jj][lane]));
@@ -185,6 +208,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
   // the largest CT not above thresh: |x| > thresh  <=>  |x| > thresh_c
   CT thresh_c = (CT)thresh;
   if ((double)thresh_c > thresh) thresh_c = nextafter(thresh_c, CT(0));
+  const CT thresh_v = (CT)thresh;  // the static pivot's magnitude
   __syncwarp();
   int j = 0;
   while (j < w) {
@@ -199,11 +223,10 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
     }
     const int imax = ci;
     const CT akk = a[j][j];
-    int code = 0;  // 0: 1x1 at j, 1: needs the row of imax
-    if (lane == 0) {
-      const double colmax = fmax((double)cm, 0.0), absakk = fabs((double)akk);
-      code = (!(fmax(absakk, colmax) > thresh) || absakk >= alpha * colmax) ? 0 : 1;
-    }
+    const CT colmax = max(cm, CT(0)), absakk = (CT)fabs(akk);
+    // 0: 1x1 at j (every lane evaluates the same tests on the same values)
+    int code = 0;
+    if (lane == 0) code = (!(max(absakk, colmax) > thresh_c) || ge_alpha(absakk, colmax)) ? 0 : 1;
     code = __shfl_sync(FULL, code, 0);
     int kstep = 1, kp = j;
     if (code == 1) {
@@ -211,12 +234,11 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       CT rm = CT(0);
       if (lane >= j && lane < w && lane != imax) rm = (CT)(lane < imax ? fabs(a[lane][imax]) : fabs(a[imax][lane]));
       for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL, rm, o));
-      const CT aii = a[imax][imax];
+      const CT aii = (CT)fabs(a[imax][imax]);
       int dec = 0;  // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
       if (lane == 0) {
-        const double colmax = fmax((double)cm, 0.0), absakk = fabs((double)akk), rowmax = (double)rm;
-        if (absakk >= alpha * colmax * (colmax / rowmax)) dec = 0;
-        else if (fabs((double)aii) >= alpha * rowmax) dec = 1;
+        if (ge_alpha_sq(absakk, rm, colmax)) dec = 0;
+        else if (ge_alpha(aii, rm)) dec = 1;
         else dec = 2;
       }
       dec = __shfl_sync(FULL, dec, 0);
@@ -249,9 +271,9 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
     if (kstep == 1) {
       CT dj = a[j][j];
       const bool perturb = !(fabs(dj) > thresh_c);
-      if (perturb) dj = (dj >= CT(0)) ? (CT)thresh : (CT)-thresh;
+      if (perturb) dj = (dj >= CT(0)) ? thresh_v : -thresh_v;
       if (lane == 0) {
-        sD0[j] = (double)dj; stype[j] = 0;
+        sD0[j] = dj; stype[j] = 0;
         if (perturb) atomicAdd(counters + 0, 1ull);
       }
       const CT rd = CT(1) / dj;
@@ -263,9 +285,10 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
-      const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
+      const CT rdet = CT(1) / det;
+      const CT i11 = d22 * rdet, i21 = -d21 * rdet, i22 = d11 * rdet;
       if (lane == 0) {
-        sD0[j] = (double)d11; sD1[j] = (double)d21; sD0[j + 1] = (double)d22;
+        sD0[j] = d11; sD1[j] = d21; sD0[j + 1] = d22;
         stype[j] = 1; stype[j + 1] = 2;
         atomicAdd(counters + 1, 1ull);
       }
@@ -286,13 +309,13 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
 // columns and pivots: a 1x1 column is divided by its pivot, a 2x2 pair is
 // multiplied by the pair's inverse; L is zero inside a 2x2 pivot
 template <typename CT, int PITCH>
-__device__ __forceinline__ CT bk_unit_lower(const CT (*a)[PITCH], int i, int j, const int *stype, const double *sD0,
-                                            const double *sD1) {
+__device__ __forceinline__ CT bk_unit_lower(const CT (*a)[PITCH], int i, int j, const int *stype, const CT *sD0,
+                                            const CT *sD1) {
   const int ty = stype[j];
-  if (ty == 0) return a[j][i] * (CT(1) / (CT)sD0[j]);
+  if (ty == 0) return a[j][i] * (CT(1) / sD0[j]);
   const int j0 = ty == 1 ? j : j - 1;  // first column of the pair
   if (i == j0 + 1) return CT(0);
-  const CT d11 = (CT)sD0[j0], d21 = (CT)sD1[j0], d22 = (CT)sD0[j0 + 1];
+  const CT d11 = sD0[j0], d21 = sD1[j0], d22 = sD0[j0 + 1];
   const CT det = d11 * d22 - d21 * d21;
   const CT i11 = d22 / det, i21 = -d21 / det, i22 = d11 / det;
   const CT u = a[j0][i], v = a[j0 + 1][i];
@@ -309,59 +332,34 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-// the panel's diagonal block, formed left-looking by its owner band:
-// a[jj][ii] = F(k + ii, k + jj) - sum_{t in [K0, k)} W(k + ii, t) L(k + jj, t)
-// (ii >= jj, zero elsewhere), then factored by warp 0; stage (L11 with D on
-// its diagonal) and the pivot arrays are written for the bands
+// the panel's diagonal block, already updated by every earlier panel (the
+// band holding it applied those updates right-looking, band_panel_rows),
+// factored by warp 0; stage (L11 with D on its diagonal) and the pivot
+// arrays are written for the bands
 template <typename T, int NBT>
-__device__ void owner_panel(const DevSym &d, const SV &sv, int s, int f, int ns, int K0, int k, int w, int nb,
-                            double eps_rel, unsigned long long *counters, T (*a)[NBT + 1], T (*Wc)[33],
-                            T (*Lc)[33], double *sD0, double *sD1, int *sperm, int *stype) {
-  const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+__device__ void owner_panel(const DevSym &d, const SV &sv, int s, int f, int k, int w, int nb, double eps_rel,
+                            unsigned long long *counters, T (*a)[NBT + 1], T *sD0, T *sD1, int *sperm, int *stype) {
+  const int tid = threadIdx.x;
   const T *F = (const T *)sv.F + sv.front_off[s];
-  const T *W = (const T *)sv.W + sv.w_off[s];
-  const int64_t ldw = f - K0;
-  T acc[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) acc[r] = T(0);
-  for (int t0 = K0; t0 < k; t0 += 32) {
-    const int kc = min(32, k - t0);
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int u = idx >> 5, r = idx & 31;  // column t0 + u, row k + r
-      const bool ok = u < kc && r < w;
-      Wc[r][u] = ok ? __ldcg(W + (int64_t)(k + r - K0) + (int64_t)(t0 - K0 + u) * ldw) : T(0);
-      Lc[r][u] = ok ? __ldcg(F + (int64_t)(k + r) + (int64_t)(t0 + u) * f) : T(0);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int u = 0; u < 32; ++u) {
-      const T lv = Lc[lane][u];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r] += Wc[grp + 4 * r][u] * lv;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int ii = grp + 4 * r, jj = lane;
-    if (ii < NBT && jj < NBT)
-      a[jj][ii] = (ii >= jj && ii < w) ? __ldcg(F + (int64_t)(k + ii) + (int64_t)(k + jj) * f) - acc[r] : T(0);
+  for (int idx = tid; idx < NBT * NBT; idx += blockDim.x) {
+    const int jj = idx / NBT, ii = idx - jj * NBT;
+    a[jj][ii] = (ii >= jj && ii < w) ? __ldcg(F + (int64_t)(k + ii) + (int64_t)(k + jj) * f) : T(0);
   }
   __syncthreads();
-  if (grp == 0) bk_factor_warp<T, NBT + 1>(a, w, eps_rel, sperm, stype, sD0, sD1, counters);
+  if (tid < 32) bk_factor_warp<T, NBT + 1>(a, w, eps_rel, sperm, stype, sD0, sD1, counters);
   __syncthreads();
   T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
     const int jj = idx / w, ii = idx - jj * w;
     if (ii >= jj)
-      stage[(int64_t)ii * nb + jj] = (ii == jj) ? T(sD0[jj]) : bk_unit_lower<T, NBT + 1>(a, ii, jj, stype, sD0, sD1);
+      stage[(int64_t)ii * nb + jj] = (ii == jj) ? sD0[jj] : bk_unit_lower<T, NBT + 1>(a, ii, jj, stype, sD0, sD1);
   }
   const int64_t po = sv.piv_off[s] + k;
   if (tid < w) {
     sv.piv_type[po + tid] = stype[tid];
     sv.piv_perm[po + tid] = sperm[tid];
-    sv.D0[po + tid] = sD0[tid];
-    sv.D1[po + tid] = sD1[tid];
+    sv.D0[po + tid] = (double)sD0[tid];
+    sv.D1[po + tid] = (double)sD1[tid];
   }
 }
 
@@ -500,7 +498,34 @@ __device__ void band_panel_rows(const DevSym &d, const SV &sv, int s, int f, int
         l = x[tp] * sI1[t] + x[t] * sI0[t];
       }
       F[i + (int64_t)(k + t) * f] = T(l);
-      xs[t * XS + tid] = l;  // own column of xs: no other thread reads it before the barrier
+      xs[t * XS + tid] = l;
+    }
+  }
+  __syncthreads();
+  {
+    // rows of later panels of this block (bands 0 and 1): apply this panel's
+    // contribution to their panel's diagonal block right away,
+    // A(i, j) -= sum_t W(i, t) L(j, t) for rows i >= j of one panel; both
+    // rows belong to this band (panels are nb-aligned from K0, bands
+    // 128-aligned, nb divides 128), their L in xs, W(i, .) in x
+    const int kend_blk = min(K0 + FACTOR_BLOCK, ns);
+    if (row_ok && i < kend_blk) {
+      const int pa = K0 + ((int)(i - K0) / nb) * nb;  // first row of the panel holding row i
+      const int pl = pa - rb0;                         // its local row in the band
+      const int ni = (int)i - pa;                      // columns pa .. i: ni + 1 of them
+      CT cur[NBT];
+#pragma unroll
+      for (int q = 0; q < NBT; ++q) cur[q] = q <= ni ? (CT)__ldcg(F + i + (int64_t)(pa + q) * f) : CT(0);
+#pragma unroll
+      for (int t = 0; t < NBT; ++t) {
+        if (t >= w) break;
+        const CT xt = x[t];
+#pragma unroll
+        for (int q = 0; q < NBT; ++q) cur[q] -= xt * xs[t * XS + min(pl + q, RB - 1)];
+      }
+#pragma unroll
+      for (int q = 0; q < NBT; ++q)
+        if (q <= ni) F[i + (int64_t)(pa + q) * f] = T(cur[q]);
     }
   }
   if (sv.wk0) {
@@ -555,9 +580,8 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
   T *L11T = Lp + 32 * NBT;                   // [NBT][NBT]
   T *xs = L11T + NBT * NBT;                  // [NBT][129]
   __shared__ T a[NBT][NBT + 1];
-  __shared__ T Wc[32][33], Lc[32][33];
-  __shared__ double bD0[NBT], bD1[NBT];
-  __shared__ int bperm[NBT], btype[NBT];
+  __shared__ T bD0[32], bD1[32];    // the warp's Bunch-Kaufman writes 32 entries
+  __shared__ int bperm[32], btype[32];
   __shared__ T sD0[NBT], sD1[NBT], sI0[NBT], sI1[NBT];
   __shared__ int sperm[NBT], stype[NBT];
   __shared__ int s_item, s_abort;
@@ -588,7 +612,7 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
       const bool owner = (k - K0) / BAND == it.band;
       if (!owner && rb1 <= k + w) break;  // no rows below this panel (nor below later ones)
       if (owner) {
-        owner_panel<T, NBT>(d, sv, s, f, ns, K0, k, w, nb, eps_rel, counters, a, Wc, Lc, bD0, bD1, bperm, btype);
+        owner_panel<T, NBT>(d, sv, s, f, k, w, nb, eps_rel, counters, a, bD0, bD1, bperm, btype);
         __syncthreads();
         if (tid == 0) {
           __threadfence();
