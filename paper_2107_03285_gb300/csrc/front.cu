@@ -185,6 +185,33 @@ __device__ __forceinline__ bool ge_alpha_sq(float a, float r, float c) {
 }
 __device__ __forceinline__ bool ge_alpha_sq(double a, double r, double c) { return a * r >= BK_ALPHA * (c * c); }
 
+// warp-wide max of non-negative magnitudes and the lowest lane holding it
+// (valid lanes only; none valid: m = -1, idx = none).  FP32 magnitudes
+// compare as their bit patterns, so one REDUX instruction each.
+__device__ __forceinline__ void warp_argmax(float v, bool valid, int none, float &m, int &idx) {
+  const unsigned key = valid ? __float_as_uint(v) + 1u : 0u;
+  const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+  if (mx == 0u) { m = -1.f; idx = none; return; }
+  m = __uint_as_float(mx - 1u);
+  idx = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)(threadIdx.x & 31) : 32u);
+}
+__device__ __forceinline__ void warp_argmax(double v, bool valid, int none, double &m, int &idx) {
+  m = valid ? v : -1.0;
+  idx = valid ? (int)(threadIdx.x & 31) : none;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, m, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > m || (ov == m && oi < idx)) { m = ov; idx = oi; }
+  }
+}
+__device__ __forceinline__ float warp_max0(float v) {  // v >= 0
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+}
+__device__ __forceinline__ double warp_max0(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // Bunch-Kaufman LDL^T of the w x w block a (w <= 32; a[j][i] = A(i, j), lower
 // triangle) by one warp, lane i holding row i: 1x1 / 2x2 pivots, alpha =
 // (1 + sqrt 17) / 8, pivot search restricted to the block, eliminations in
@@ -196,14 +223,14 @@ __device__ __forceinline__ bool ge_alpha_sq(double a, double r, double c) { retu
 // block's permutation (position -> original index).
 template <typename CT, int PITCH>
 __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel, int *sperm, int *stype,
-                               CT *sD0, CT *sD1, unsigned long long *counters) {
+                               CT *sD0, CT *sD1, CT *su, CT *sv, unsigned long long *counters) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   sperm[lane] = lane; stype[lane] = 0; sD0[lane] = CT(0); sD1[lane] = CT(0);
   CT bm = CT(0);
   for (int jj = 0; jj < w; ++jj)
     if (lane >= jj && lane < w) bm = max(bm, (CT)fabs(a[jj][lane]));
-  for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(FULL, bm, o));
+  bm = warp_max0(bm);
   const double thresh = eps_rel * fmax((double)bm, 1e-300);
   // the largest CT not above thresh: |x| > thresh  <=>  |x| > thresh_c
   CT thresh_c = (CT)thresh;
@@ -213,15 +240,10 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
   int j = 0;
   while (j < w) {
     // ---- pivot search: largest |A(i, j)|, i > j (ties to the lowest index)
-    CT cm = CT(-1);
-    int ci = w;
-    if (lane > j && lane < w) { cm = (CT)fabs(a[j][lane]); ci = lane; }
-    for (int o = 16; o > 0; o >>= 1) {
-      const CT ov = __shfl_xor_sync(FULL, cm, o);
-      const int oi = __shfl_xor_sync(FULL, ci, o);
-      if (ov > cm || (ov == cm && oi < ci)) { cm = ov; ci = oi; }
-    }
-    const int imax = ci;
+    CT cm;
+    int imax;
+    const bool below = lane > j && lane < w;
+    warp_argmax(below ? (CT)fabs(a[j][lane]) : CT(0), below, w, cm, imax);
     const CT akk = a[j][j];
     const CT colmax = max(cm, CT(0)), absakk = (CT)fabs(akk);
     // 0: 1x1 at j (every lane evaluates the same tests on the same values)
@@ -233,7 +255,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       // largest off-diagonal |A(imax, t)|, t in [j, w), t != imax
       CT rm = CT(0);
       if (lane >= j && lane < w && lane != imax) rm = (CT)(lane < imax ? fabs(a[lane][imax]) : fabs(a[imax][lane]));
-      for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL, rm, o));
+      rm = warp_max0(rm);
       const CT aii = (CT)fabs(a[imax][imax]);
       int dec = 0;  // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
       if (lane == 0) {
@@ -278,10 +300,13 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       }
       const CT rd = CT(1) / dj;
       const CT l = (lane > j && lane < w) ? a[j][lane] : CT(0);
-      for (int cc = j + 1; cc < w; ++cc) {
-        const CT fc = __shfl_sync(FULL, l, cc) * rd;
-        if (lane >= cc && lane < w) a[cc][lane] -= l * fc;
-      }
+      su[lane] = l * rd;
+      __syncwarp();
+      // every column cc > j of row lane at once: unrolled, predicated, the
+      // multipliers broadcast from shared memory
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc)
+        if (cc > j && cc <= lane && lane < w) a[cc][lane] -= l * su[cc];
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
@@ -295,10 +320,12 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       const bool in = lane > j + 1 && lane < w;
       const CT u = in ? a[j][lane] : CT(0), v = in ? a[j + 1][lane] : CT(0);
       const CT p = u * i11 + v * i21, q = u * i21 + v * i22;  // (L1, L2) of row lane
-      for (int cc = j + 2; cc < w; ++cc) {
-        const CT w1 = __shfl_sync(FULL, u, cc), w2 = __shfl_sync(FULL, v, cc);
-        if (lane >= cc && lane < w) a[cc][lane] -= p * w1 + q * w2;
-      }
+      su[lane] = u;
+      sv[lane] = v;
+      __syncwarp();
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc)
+        if (cc > j + 1 && cc <= lane && lane < w) a[cc][lane] -= p * su[cc] + q * sv[cc];
     }
     __syncwarp();
     j += kstep;
@@ -338,15 +365,17 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
 // arrays are written for the bands
 template <typename T, int NBT>
 __device__ void owner_panel(const DevSym &d, const SV &sv, int s, int f, int k, int w, int nb, double eps_rel,
-                            unsigned long long *counters, T (*a)[NBT + 1], T *sD0, T *sD1, int *sperm, int *stype) {
+                            unsigned long long *counters, T (*a)[NBT + 1], T *sD0, T *sD1, int *sperm, int *stype,
+                            T *su, T *svv) {
   const int tid = threadIdx.x;
   const T *F = (const T *)sv.F + sv.front_off[s];
+  __syncthreads();  // the band's right-looking updates of this block are complete
   for (int idx = tid; idx < NBT * NBT; idx += blockDim.x) {
     const int jj = idx / NBT, ii = idx - jj * NBT;
     a[jj][ii] = (ii >= jj && ii < w) ? __ldcg(F + (int64_t)(k + ii) + (int64_t)(k + jj) * f) : T(0);
   }
   __syncthreads();
-  if (tid < 32) bk_factor_warp<T, NBT + 1>(a, w, eps_rel, sperm, stype, sD0, sD1, counters);
+  if (tid < 32) bk_factor_warp<T, NBT + 1>(a, w, eps_rel, sperm, stype, sD0, sD1, su, svv, counters);
   __syncthreads();
   T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
@@ -580,7 +609,7 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
   T *L11T = Lp + 32 * NBT;                   // [NBT][NBT]
   T *xs = L11T + NBT * NBT;                  // [NBT][129]
   __shared__ T a[NBT][NBT + 1];
-  __shared__ T bD0[32], bD1[32];    // the warp's Bunch-Kaufman writes 32 entries
+  __shared__ T bD0[32], bD1[32], bU[32], bV[32];  // the warp's Bunch-Kaufman writes 32 entries
   __shared__ int bperm[32], btype[32];
   __shared__ T sD0[NBT], sD1[NBT], sI0[NBT], sI1[NBT];
   __shared__ int sperm[NBT], stype[NBT];
@@ -612,7 +641,7 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
       const bool owner = (k - K0) / BAND == it.band;
       if (!owner && rb1 <= k + w) break;  // no rows below this panel (nor below later ones)
       if (owner) {
-        owner_panel<T, NBT>(d, sv, s, f, k, w, nb, eps_rel, counters, a, bD0, bD1, bperm, btype);
+        owner_panel<T, NBT>(d, sv, s, f, k, w, nb, eps_rel, counters, a, bD0, bD1, bperm, btype, bU, bV);
         __syncthreads();
         if (tid == 0) {
           __threadfence();
