@@ -237,6 +237,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
   if ((double)thresh_c > thresh) thresh_c = nextafter(thresh_c, CT(0));
   const CT thresh_v = (CT)thresh;  // the static pivot's magnitude
   __syncwarp();
+  unsigned long long n_pert = 0, n_pair = 0;  // counted in lane 0, added once at the end
   int j = 0;
   while (j < w) {
     // ---- pivot search: largest |A(i, j)|, i > j (ties to the lowest index)
@@ -296,7 +297,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       if (perturb) dj = (dj >= CT(0)) ? thresh_v : -thresh_v;
       if (lane == 0) {
         sD0[j] = dj; stype[j] = 0;
-        if (perturb) atomicAdd(counters + 0, 1ull);
+        if (perturb) ++n_pert;
       }
       const CT rd = CT(1) / dj;
       const CT l = (lane > j && lane < w) ? a[j][lane] : CT(0);
@@ -315,7 +316,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       if (lane == 0) {
         sD0[j] = d11; sD1[j] = d21; sD0[j + 1] = d22;
         stype[j] = 1; stype[j + 1] = 2;
-        atomicAdd(counters + 1, 1ull);
+        ++n_pair;
       }
       const bool in = lane > j + 1 && lane < w;
       const CT u = in ? a[j][lane] : CT(0), v = in ? a[j + 1][lane] : CT(0);
@@ -329,6 +330,10 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
     }
     __syncwarp();
     j += kstep;
+  }
+  if (lane == 0) {
+    if (n_pert) atomicAdd(counters + 0, n_pert);
+    if (n_pair) atomicAdd(counters + 1, n_pair);
   }
 }
 
@@ -459,18 +464,29 @@ __device__ void band_panel_rows(const DevSym &d, const SV &sv, int s, int f, int
     sI0[t] = i0;
     sI1[t] = i1;
   }
-  // left-looking update
+  // left-looking update; the next chunk of L (and of W) is loaded into
+  // registers while the current one is applied
+  constexpr int LPER = KC * NBT / 128;
+  auto load_lp = [&](int cu, CT (&r)[LPER]) {
+    const int kc = min(KC, kp_in - cu);
+#pragma unroll
+    for (int m = 0; m < LPER; ++m) {
+      const int idx = tid + m * 128;
+      const int u = idx / NBT, t = idx - u * NBT;
+      r[m] = (u < kc && t < w) ? (CT)__ldcg(F + (int64_t)(k + t) + (int64_t)(K0 + cu + u) * f) : CT(0);
+    }
+  };
+  CT lpr[LPER];
+  if (kp_in > 0) load_lp(0, lpr);
   CT wr[KC];
 #pragma unroll
   for (int u = 0; u < KC; ++u) wr[u] = (row_ok && u < kp_in) ? (CT)__ldcg(W + (i - K0) + (int64_t)u * ldw) : CT(0);
   for (int cu = 0; cu < kp_in; cu += KC) {
-    const int kc = min(KC, kp_in - cu);
     __syncthreads();
-    for (int idx = tid; idx < KC * NBT; idx += blockDim.x) {
-      const int u = idx / NBT, t = idx - u * NBT;
-      Lp[idx] = (u < kc && t < w) ? (CT)__ldcg(F + (int64_t)(k + t) + (int64_t)(K0 + cu + u) * f) : CT(0);
-    }
+#pragma unroll
+    for (int m = 0; m < LPER; ++m) Lp[tid + m * 128] = lpr[m];
     __syncthreads();
+    if (cu + KC < kp_in) load_lp(cu + KC, lpr);
     CT wn[KC];
     const int nx = cu + KC;
 #pragma unroll
