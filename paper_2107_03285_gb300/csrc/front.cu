@@ -238,6 +238,7 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
   const CT thresh_v = (CT)thresh;  // the static pivot's magnitude
   __syncwarp();
   unsigned long long n_pert = 0, n_pair = 0;  // counted in lane 0, added once at the end
+  (void)su; (void)sv;
   int j = 0;
   while (j < w) {
     // ---- pivot search: largest |A(i, j)|, i > j (ties to the lowest index)
@@ -247,10 +248,9 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
     warp_argmax(below ? (CT)fabs(a[j][lane]) : CT(0), below, w, cm, imax);
     const CT akk = a[j][j];
     const CT colmax = max(cm, CT(0)), absakk = (CT)fabs(akk);
-    // 0: 1x1 at j (every lane evaluates the same tests on the same values)
-    int code = 0;
-    if (lane == 0) code = (!(max(absakk, colmax) > thresh_c) || ge_alpha(absakk, colmax)) ? 0 : 1;
-    code = __shfl_sync(FULL, code, 0);
+    // every lane takes the same decisions on the same (warp-uniform) values,
+    // so no broadcast is needed; 0: 1x1 at j, 1: needs the row of imax
+    const int code = (!(max(absakk, colmax) > thresh_c) || ge_alpha(absakk, colmax)) ? 0 : 1;
     int kstep = 1, kp = j;
     if (code == 1) {
       // largest off-diagonal |A(imax, t)|, t in [j, w), t != imax
@@ -258,13 +258,8 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       if (lane >= j && lane < w && lane != imax) rm = (CT)(lane < imax ? fabs(a[lane][imax]) : fabs(a[imax][lane]));
       rm = warp_max0(rm);
       const CT aii = (CT)fabs(a[imax][imax]);
-      int dec = 0;  // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
-      if (lane == 0) {
-        if (ge_alpha_sq(absakk, rm, colmax)) dec = 0;
-        else if (ge_alpha(aii, rm)) dec = 1;
-        else dec = 2;
-      }
-      dec = __shfl_sync(FULL, dec, 0);
+      // 0: 1x1 at j, 1: 1x1 at imax, 2: 2x2 with imax
+      const int dec = ge_alpha_sq(absakk, rm, colmax) ? 0 : (ge_alpha(aii, rm) ? 1 : 2);
       if (dec == 1) { kstep = 1; kp = imax; }
       else if (dec == 2) { kstep = 2; kp = imax; }
     }
@@ -301,13 +296,18 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       }
       const CT rd = CT(1) / dj;
       const CT l = (lane > j && lane < w) ? a[j][lane] : CT(0);
-      su[lane] = l * rd;
-      __syncwarp();
-      // every column cc > j of row lane at once: unrolled, predicated, the
-      // multipliers broadcast from shared memory
+      const CT lr = l * rd;
+      // every column cc > j of row lane at once: all loads first, the
+      // multipliers by shuffles, then the stores (unrolled, predicated)
+      const int row = lane < w ? lane : 0;
+      CT av[32];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc)
-        if (cc > j && cc <= lane && lane < w) a[cc][lane] -= l * su[cc];
+      for (int cc = 0; cc < 32; ++cc) av[cc] = cc < PITCH - 1 ? a[cc < PITCH - 1 ? cc : 0][row] : CT(0);
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) {
+        const CT m = __shfl_sync(FULL, lr, cc);
+        if (cc > j && cc <= lane && lane < w) a[cc < PITCH - 1 ? cc : 0][lane] = av[cc] - l * m;
+      }
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
       const CT det = d11 * d22 - d21 * d21;
@@ -321,12 +321,15 @@ __device__ void bk_factor_warp(CT (*a)[PITCH], const int w, const double eps_rel
       const bool in = lane > j + 1 && lane < w;
       const CT u = in ? a[j][lane] : CT(0), v = in ? a[j + 1][lane] : CT(0);
       const CT p = u * i11 + v * i21, q = u * i21 + v * i22;  // (L1, L2) of row lane
-      su[lane] = u;
-      sv[lane] = v;
-      __syncwarp();
+      const int row = lane < w ? lane : 0;
+      CT av[32];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc)
-        if (cc > j + 1 && cc <= lane && lane < w) a[cc][lane] -= p * su[cc] + q * sv[cc];
+      for (int cc = 0; cc < 32; ++cc) av[cc] = cc < PITCH - 1 ? a[cc < PITCH - 1 ? cc : 0][row] : CT(0);
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) {
+        const CT w1 = __shfl_sync(FULL, u, cc), w2 = __shfl_sync(FULL, v, cc);
+        if (cc > j + 1 && cc <= lane && lane < w) a[cc < PITCH - 1 ? cc : 0][lane] = av[cc] - (p * w1 + q * w2);
+      }
     }
     __syncwarp();
     j += kstep;
