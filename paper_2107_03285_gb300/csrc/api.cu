@@ -353,8 +353,8 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
       st_up(bi, s.h_blk_items); s.blk_items = bi;
     }
     if (fp32) {
-      for (int q = 0; q < 4; ++q) s.wk[q] = cv.take<float>(s.w_elems);
-      s.maps = cv.take<char>(S.sn.size() * sizeof(tc::Maps));
+      for (int q = 0; q < 8; ++q) s.wk[q] = cv.take<float>(s.w_elems);
+      s.maps = cv.take<char>(2 * S.sn.size() * sizeof(tc::Maps));
     }
     int64_t *p;
     st_up(p, s.h_front_off); s.front_off = p;
@@ -385,16 +385,18 @@ bool encode_maps(Ctx &c, Store &st, std::vector<tc::Maps> &out) {
       q != cudaDriverEntryPointSuccess || !fn)
     return false;
   EncodeTiledFn enc = (EncodeTiledFn)fn;
-  out.assign(c.S.sn.size(), tc::Maps());
-  for (size_t i = 0; i < c.S.sn.size(); ++i) {
+  const size_t nsn = c.S.sn.size();
+  out.assign(2 * nsn, tc::Maps());
+  for (size_t pi = 0; pi < 2 * nsn; ++pi) {
+    const size_t i = pi % nsn, par = pi / nsn;
     const cuuint64_t f = (cuuint64_t)c.S.sn[i].fnodes() * st.dpn;
     cuuint64_t dims[2] = {(cuuint64_t)FACTOR_BLOCK, f};
     cuuint64_t strides[1] = {(cuuint64_t)FACTOR_BLOCK * sizeof(float)};
     cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)tc::TILE};
     cuuint32_t estr[2] = {1, 1};
-    CUtensorMap *m[4] = {&out[i].whi, &out[i].wlo, &out[i].lhi, &out[i].llo};
+    CUtensorMap *m[4] = {&out[pi].whi, &out[pi].wlo, &out[pi].lhi, &out[pi].llo};
     for (int k = 0; k < 4; ++k) {
-      void *addr = st.wk[k] + st.h_w_off[i];
+      void *addr = st.wk[4 * par + k] + st.h_w_off[i];
       CUresult r = enc(m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr, dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -579,6 +581,9 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
   h->stores = stores;
   set_kernel_attributes();
   if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->side_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+  if (!h->ev_fork) CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   {
     const char *g = getenv("SGN_DISABLE_GRAPHS");
     h->use_graphs = !(g && g[0] == '1');
@@ -631,6 +636,9 @@ void sgn_destroy(sgn_t h) {
   destroy_graphs(h->kkt64); destroy_graphs(h->kkt32); destroy_graphs(h->kf); destroy_graphs(h->kf32);
   if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   delete h;
 }

@@ -70,8 +70,11 @@ struct Store {
   // FP32 fronts only: K-major copies of W and L21 of the current outer block,
   // split as hi (TF32-exact) + lo, rows = absolute front rows, for the
   // tensor-core trailing update; and one set of TMA tensor maps per front
-  float *wk[4] = {nullptr, nullptr, nullptr, nullptr};  // Whi, Wlo, Lhi, Llo
-  void *maps = nullptr;
+  // two sets (outer blocks alternate between them, so that one block's
+  // trailing update can still read its operands while the next block's
+  // panels write theirs): wk[4 * parity + q], q = Whi, Wlo, Lhi, Llo
+  float *wk[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void *maps = nullptr;     // [2][n_sn] tensor maps, one set per parity
   bool tc = false;          // tensor-core trailing update available
   double *rhs = nullptr;    // per-front solve buffers (f each)
   double *yz = nullptr;     // per fully-summed DOF: y, then z = D^{-1} y, then v (solves)
@@ -218,6 +221,10 @@ struct Ctx {
   int step_prec = -1, step_refine = -1;
   int64_t step_launches = 0, step_tc = 0;
   cudaStream_t cap_stream = nullptr;       // capture stream (the caller's may be the legacy stream)
+  // a second stream for the part of each trailing update that the next
+  // outer block's panels do not wait for, and the fork / join events
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<GraphEv> *capture_events = nullptr;  // non-null while capturing a profiled graph
   std::vector<GraphEv> *pending_events = nullptr;  // events of the last profiled replay, not yet read
   double gacc_sec[8] = {0}, gacc_fl[8] = {0};

@@ -864,10 +864,11 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
 }
 
 // persistent tensor-core trailing update: CTA x of front y walks tiles
-// x, x + gridDim.x, ... of that front's lower triangle
+// x, x + gridDim.x, ... of the window of tile columns [win0, win1) (win1 < 0:
+// to the end) of that front's lower triangle
 __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                                  int K0, int NB, const tc::Maps *__restrict__ maps,
-                                                                 int *status) {
+                                                                 int win0, int win1, int *status) {
   const int s = fronts[blockIdx.y];
   const int dpn = sv.dpn;
   const int ns = d.sn_nown[s] * dpn;
@@ -877,7 +878,11 @@ __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv,
   const int nrows = f - kend;
   const int nt = (nrows + tc::TILE - 1) / tc::TILE;
   tc::TileJob job;
-  job.ntiles = nt * (nt + 1) / 2;
+  job.win0 = win0;
+  job.m = min(win1 < 0 ? nt : win1, nt) - win0;
+  if (job.m <= 0) return;
+  const int n = nt - win0;  // tile rows of the window
+  job.ntiles = job.m * (job.m + 1) / 2 + (n - job.m) * job.m;
   if ((int)blockIdx.x >= job.ntiles) return;
   job.L = (float *)sv.F + sv.front_off[s];
   job.CB = (float *)sv.CB + sv.cb_off[s];
@@ -934,9 +939,12 @@ int n_active(const LevelInfo &li, int k) {
   return n;
 }
 
+// SMs the rest of a split trailing update leaves to the next block's panels
+constexpr int PANEL_RESERVE_SMS = 32;
+
 template <typename T>
 void factor_impl(Ctx &c, Store &st) {
-  SV sv = view(st);
+  const SV sv0 = view(st);
   const int nb = c.S.opts.panel;
   const int D = c.S.dim;
   const double eps_rel = sizeof(T) == 8 ? 1e-14 : 1e-7;
@@ -955,16 +963,19 @@ void factor_impl(Ctx &c, Store &st) {
       ProfScope ps(c, SGN_PROF_FRONT_ASSEMBLY);
       const dim3 ga((unsigned)nitems);
       const double ex = st.kkt ? st.eps_x : 0.0, el = st.kkt ? st.eps_l : 0.0;
-      if (D == 2 && st.dpn == 4) k_front_assemble<T, 2, 4><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
-      else if (D == 2) k_front_assemble<T, 2, 2><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
-      else if (st.dpn == 6) k_front_assemble<T, 3, 6><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
-      else k_front_assemble<T, 3, 3><<<ga, 256, 0, c.stream>>>(c.ds, sv, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      if (D == 2 && st.dpn == 4) k_front_assemble<T, 2, 4><<<ga, 256, 0, c.stream>>>(c.ds, sv0, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else if (D == 2) k_front_assemble<T, 2, 2><<<ga, 256, 0, c.stream>>>(c.ds, sv0, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else if (st.dpn == 6) k_front_assemble<T, 3, 6><<<ga, 256, 0, c.stream>>>(c.ds, sv0, li.i0, c.Kv, c.Gv, c.wA, ex, el);
+      else k_front_assemble<T, 3, 3><<<ga, 256, 0, c.stream>>>(c.ds, sv0, li.i0, c.Kv, c.Gv, c.wA, ex, el);
       c.count();
     }
     const int32_t *fronts = c.ds.lvl_fronts + li.f0;
     int max_ns = li.ns.empty() ? 0 : li.ns[0];
+    bool side_pending = false;  // the rest of the last trailing update runs on the side stream
     for (int K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
       const int kstop = std::min(K0 + FACTOR_BLOCK, max_ns);
+      const int parity = (K0 / FACTOR_BLOCK) & 1;  // which operand set this block writes
+      const SV sv = view(st, parity);
       {
         // every panel of the block in one launch (one CTA per 128-row band)
         int na = n_active(li, K0);
@@ -986,39 +997,86 @@ void factor_impl(Ctx &c, Store &st) {
         c.count();
       }
       int na = n_active(li, K0);
-      int max_rows = 0;
-      for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - std::min(K0 + FACTOR_BLOCK, li.ns[q]));
-      if (max_rows > 0) {
-        int nt = (max_rows + 63) / 64;
-        dim3 gu(nt * (nt + 1) / 2, na);
-        double fl = 0.0;
-        for (int q = 0; q < na; ++q) {
-          double kend = std::min(K0 + FACTOR_BLOCK, li.ns[q]), nr = li.f[q] - kend;
-          fl += nr * (nr + 1.0) * (kend - K0);  // 2 flops x lower triangle x k
-        }
-        ProfScope ps(c, SGN_PROF_UPDATE, fl);
-        if (std::is_same<T, float>::value && st.tc) {
-          // one CTA per SM (192 KB shared memory); spread the SMs over the
-          // active fronts and let every CTA loop over its front's tiles
-          int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
-          int tiles = nt128 * (nt128 + 1) / 2;
-          const int ctas = c.update_ctas > 0 ? c.update_ctas : c.num_sms;
-          int g = std::max(1, std::min(tiles, (ctas + na - 1) / na));
-          dim3 gtc(g, na);
-          k_update_tcp<<<gtc, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK,
-                                                                          (const tc::Maps *)st.maps, c.status);
-          c.tc_launches++;
-        } else {
-          k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
-        }
-        c.count();
-      }
       {
+        // the permutations of this block's panels (rows [K0, kend), columns
+        // left of each panel): independent of the trailing update
         ProfScope ps(c, SGN_PROF_PIVOT);
         dim3 gs((kstop + 63) / 64, na);
         k_row_swap<T><<<gs, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK, nb);
         c.count();
       }
+      int max_rows = 0;
+      for (int q = 0; q < na; ++q) max_rows = std::max(max_rows, li.f[q] - std::min(K0 + FACTOR_BLOCK, li.ns[q]));
+      if (max_rows > 0) {
+        auto flops_cols = [&](int c0, int c1) {  // trailing-update flops of tile columns [c0, c1) (c1 < 0: all)
+          double fl = 0.0;
+          for (int q = 0; q < na; ++q) {
+            const double kend = std::min(K0 + FACTOR_BLOCK, li.ns[q]), nr = li.f[q] - kend;
+            const double a = std::min<double>(nr, (double)c0 * tc::TILE);
+            const double b = c1 < 0 ? nr : std::min<double>(nr, (double)c1 * tc::TILE);
+            if (b <= a) continue;
+            // lower-triangle entries of columns [a, b): sum_{j=a}^{b-1} (nr - j)
+            fl += 2.0 * (kend - K0) * ((b - a) * nr - (b * (b - 1) - a * (a - 1)) / 2.0);
+          }
+          return fl;
+        };
+        if (std::is_same<T, float>::value && st.tc) {
+          // one CTA per SM (192 KB shared memory); spread the SMs over the
+          // active fronts and let every CTA loop over its front's tiles.  The
+          // tile columns holding the next outer block's columns go first on
+          // this stream; the rest runs on the side stream, next to the next
+          // block's panels (which write the other operand set), on fewer SMs
+          // so that those panels find room
+          const int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
+          const int ctas = c.update_ctas > 0 ? c.update_ctas : c.num_sms;
+          const int next_w = FACTOR_BLOCK / tc::TILE;
+          const tc::Maps *maps = (const tc::Maps *)st.maps + (size_t)parity * c.S.sn.size();
+          if (side_pending) cudaStreamWaitEvent(c.stream, c.ev_join, 0);  // the previous block's rest
+          const bool split = nt128 > next_w && c.side_stream && K0 + FACTOR_BLOCK < max_ns;
+          {
+            const int m = std::min(next_w, nt128);
+            const int tiles = m * (m + 1) / 2 + (nt128 - m) * m;
+            int g = std::max(1, std::min(split ? tiles : nt128 * (nt128 + 1) / 2, (ctas + na - 1) / na));
+            ProfScope ps(c, SGN_PROF_UPDATE, split ? flops_cols(0, next_w) : flops_cols(0, -1));
+            k_update_tcp<<<dim3(g, na), tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, c.status);
+            c.tc_launches++;
+            c.count();
+          }
+          if (split) {
+            cudaEventRecord(c.ev_fork, c.stream);
+            cudaStream_t main = c.stream;
+            c.stream = c.side_stream;
+            cudaStreamWaitEvent(c.stream, c.ev_fork, 0);
+            {
+              const int m = nt128 - next_w;
+              const int tiles = m * (m + 1) / 2;
+              const int rest = std::max(1, ctas - std::min(ctas / 4, PANEL_RESERVE_SMS));
+              int g = std::max(1, std::min(tiles, (rest + na - 1) / na));
+              ProfScope ps(c, SGN_PROF_UPDATE, flops_cols(next_w, -1));
+              k_update_tcp<<<dim3(g, na), tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, c.status);
+              c.tc_launches++;
+              c.count();
+            }
+            cudaEventRecord(c.ev_join, c.stream);
+            c.stream = main;
+            side_pending = true;
+          } else {
+            side_pending = false;
+          }
+        } else {
+          int nt = (max_rows + 63) / 64;
+          dim3 gu(nt * (nt + 1) / 2, na);
+          ProfScope ps(c, SGN_PROF_UPDATE, flops_cols(0, -1));
+          k_update<T><<<gu, 256, 0, c.stream>>>(c.ds, sv, fronts, K0, FACTOR_BLOCK);
+          c.count();
+        }
+      }
+    }
+    if (side_pending) {  // the level's contribution blocks are complete before the next level
+      cudaStreamWaitEvent(c.stream, c.ev_join, 0);
+      side_pending = false;
     }
     if (max_ns > 0) {
       ProfScope ps(c, SGN_PROF_SOLVE);

@@ -26,11 +26,13 @@ struct SV {  // store view passed to kernels
   int kkt;
 };
 
-inline SV view(Store &s) {
+inline SV view(Store &s, int parity = 0) {
   SV v;
   v.F = s.F; v.CB = s.CB; v.cb_off = s.cb_off; v.W = s.W; v.rhs = s.rhs; v.Ldg = s.Ldg;
   v.Xinv = s.Xinv; v.xinv_off = s.xinv_off; v.pub = s.pub; v.pflag = s.pflag; v.yz = s.yz; v.fflag = s.fflag;
-  v.wk0 = s.tc ? s.wk[0] : nullptr; v.wk1 = s.wk[1]; v.wk2 = s.wk[2]; v.wk3 = s.wk[3]; v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
+  const int o = 4 * (parity & 1);
+  v.wk0 = s.tc ? s.wk[o] : nullptr; v.wk1 = s.wk[o + 1]; v.wk2 = s.wk[o + 2]; v.wk3 = s.wk[o + 3];
+  v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
   return v;

@@ -142,11 +142,28 @@ struct TileJob {                 // one front's part of a trailing update
   int nrows;                     // f - kend
   int kend;                      // first trailing row (TMA row coordinate of tile row 0)
   int kchunks;                   // 32-wide K chunks
-  int ntiles;                    // lower-triangle 128-tiles
+  int ntiles;                    // tiles of the window
+  int win0, m;                   // the window: tile columns win0 .. win0 + m - 1 (rows >= columns)
 };
 
+// tile t of a job's window, row-major: the window's m x m triangle first,
+// then its rows below, m tiles each (absolute tile coordinates bi >= bj)
+__device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj);
+__device__ __forceinline__ void window_tile(const TileJob &job, int t, int &bi, int &bj) {
+  const int t0 = job.m * (job.m + 1) / 2;
+  int r, c;
+  if (t < t0) {
+    tile_coords(t, r, c);
+  } else {
+    r = job.m + (t - t0) / job.m;
+    c = (t - t0) % job.m;
+  }
+  bi = job.win0 + r;
+  bj = job.win0 + c;
+}
+
 __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
-  bi = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  bi = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);  // corrected below
   while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
   while (bi * (bi + 1) / 2 > tile) --bi;
   bj = tile - bi * (bi + 1) / 2;
@@ -190,7 +207,7 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
       bool stop = false;
       for (int lt = 0; lt < my_tiles && !stop; ++lt) {
         int bi, bj;
-        tile_coords(first + lt * stride, bi, bj);
+        window_tile(job, first + lt * stride, bi, bj);
         const int rw = job.kend + bi * TILE, rl = job.kend + bj * TILE;
         for (int kc = 0; kc < kch; ++kc, ++g) {
           const int s = g % PSTAGES;
@@ -261,7 +278,7 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
       int bi, bj;
-      tile_coords(first + lt * stride, bi, bj);
+      window_tile(job, first + lt * stride, bi, bj);
       const int rows = min(TILE, job.nrows - bi * TILE), cols = min(TILE, job.nrows - bj * TILE);
       const int roff = (bi - bj) * TILE;
       // element (gi, gj) of the front: factor column (gj < ns) or
