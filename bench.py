@@ -34,10 +34,43 @@ sys.path.insert(0, ROOT)
 METRIC = "SGN steps/sec (assemble+factor+solve)"
 UNIT = "steps/s"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 / FP64 pipe peaks measured on this machine's GB300 with an FMA-chain
-# kernel (152 SMs)
-FP32_SIMT_TFLOPS = 70.0
-FP64_TFLOPS = 1.20
+
+# DRAM bytes of the tensor-core trailing update per algorithmic byte, from the
+# ncu capture summarised in profiles/k_update_tcp_kuhn3d_24.md (the full-size
+# launches are too large to capture); None until a capture of the current
+# kernel exists
+UPDATE_DRAM_PER_ALGO_BYTE = None
+
+
+def measure_peaks(torch):
+    """Dense peaks of this GPU measured in this run with library GEMMs (CUDA
+    events, best of several after warm-up): FP32 inputs with TF32 allowed
+    (the tensor-core rate the FP32 fronts' tcgen05 kind::tf32 MMAs run at) and
+    FP64 (the rate the plain FP64 path's DFMA updates are bounded by)."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, reps, tf32 in (("tf32", torch.float32, 8192, 6, True), ("fp64", torch.float64, 4096, 3, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            c = a @ b
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name + "_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            out[name + "_how"] = f"torch.matmul {n}^3 {'fp32 with TF32 allowed' if tf32 else 'fp64'}, best of {reps}"
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+        torch.cuda.empty_cache()
+    return out
 
 
 def parse():
@@ -507,7 +540,6 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    s.profile(1)  # time the dominant kernel kind (trailing update) live
     launches0 = s.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -519,8 +551,6 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     launches = s.launch_count() - launches0
-    prof_launches, prof_seconds, prof_flops = s.profile_read()["update"]
-    s.profile(0)
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -529,8 +559,17 @@ def main():
         torch.distributed.barrier()
     value = ws * 1e3 / ms
     dp = out[1].clone()
-    # phase and per-kernel-kind breakdown of one extra (profiled) step
-    s.profile(0xFF)
+    # the dominant kernel kind (trailing update) timed in separate steps (CUDA
+    # events around every launch inside the captured factorization graph), so
+    # that the headline steps above run without profiling events
+    prof_steps = 2
+    s.profile(1)
+    for _ in range(prof_steps):
+        step(prec)
+    torch.cuda.synchronize()
+    prof_launches, prof_seconds, prof_flops = s.profile_read()["update"]
+    s.profile(0)
+    # phases of one unprofiled step (CUDA events between the calls)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     s.assemble(xeq, p)
@@ -541,7 +580,13 @@ def main():
     ev[3].record()
     torch.cuda.synchronize()
     phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "factor_ms": ev[1].elapsed_time(ev[2]),
-              "solve_ms": ev[2].elapsed_time(ev[3])}
+              "solve_ms": ev[2].elapsed_time(ev[3]), "source": "one unprofiled step, events between the calls"}
+    # per-kernel-kind breakdown of one extra (profiled) step
+    s.profile(0xFF)
+    s.assemble(xeq, p)
+    s.factor(prec, report=False)
+    s.solve(P.RHS_KKT, report=False, out=out)
+    torch.cuda.synchronize()
     kinds = {k: {"launches": v[0], "ms": 1e3 * v[1], "tflops": (v[2] / v[1] / 1e12) if v[1] > 0 and v[2] > 0 else None}
              for k, v in s.profile_read().items() if v[0] > 0}
     s.profile(0)
@@ -575,25 +620,56 @@ def main():
             torch.distributed.destroy_process_group()
         return
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    run_peaks = measure_peaks(torch)
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "of fallback 6.8 TB/s"
     fp32 = prec == P.MIXED
     achieved = prof_flops / prof_seconds / 1e12 if prof_seconds > 0 else None
+    upd_launch_flops = prof_flops / max(prof_launches, 1)
     if fp32:
-        # tcgen05 kind::tf32; TF32 dense peak = measured BF16 burst x nominal TF32/BF16 (1.1 / 2.25)
-        bf16 = peaks.get("bf16_tflops")
-        peak = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+        peak = run_peaks["tf32_tflops"]
         roofline = {"kernel": "k_update_tcp (tcgen05 3xTF32 trailing Schur update, TMEM accumulators)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak if achieved else None, "traffic": None,
-                    "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x 1.1/2.25" if bf16
-                                    else "of fallback 1.9 PFLOP/s bf16 x 1.1/2.25"),
+                    "frac": achieved / peak if achieved else None,
+                    "peak_source": "of measured in this run: " + run_peaks["tf32_how"],
                     "tensor_pipe_frac_3xtf32": 3 * achieved / peak if achieved else None,
-                    "note": "achieved counts useful FP32 flops; 3xTF32 issues three TF32 MMAs per product"}
+                    "note": "achieved counts useful FP32 flops (2 x lower-triangle entries x inner dimension per "
+                            "outer block, summed on the host) over the update launches' CUDA-event time in "
+                            f"{prof_steps} profiled steps; 3xTF32 issues three TF32 MMAs per product"}
+        # algorithmic bytes of an update launch: the C tile read and written
+        # (FP32) plus the four K-major operand arrays of the block (FP32)
+        if UPDATE_DRAM_PER_ALGO_BYTE is not None:
+            algo_b = upd_launch_flops / (2.0 * 256) * 8.0
+            roofline["traffic"] = UPDATE_DRAM_PER_ALGO_BYTE * algo_b
+            roofline["traffic_source"] = ("DRAM bytes per algorithmic byte from the ncu capture in "
+                                          "profiles/k_update_tcp_kuhn3d_24.md, scaled to this workload's mean launch")
+        else:
+            roofline["traffic"] = None
     else:
+        peak = run_peaks["fp64_tflops"]
         roofline = {"kernel": "k_update (FP64 DFMA trailing Schur update)", "bound": "alu", "achieved": achieved,
-                    "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_TFLOPS if achieved else None,
-                    "traffic": None, "peak_source": "measured FP64 FMA-chain probe on this pool's GB300"}
-    roofline["launches_per_step"] = prof_launches / args.steps
-    roofline["share_of_step"] = prof_seconds / (ms * 1e-3 * args.steps)
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                    "traffic": None, "peak_source": "of measured in this run: " + run_peaks["fp64_how"]}
+    roofline["launches_per_step"] = prof_launches / prof_steps
+    roofline["share_of_step"] = prof_seconds / prof_steps / (ms * 1e-3)
+    # HBM-bound phases: algorithmic bytes per step over their event-timed phase
+    d, ne, nn = prob.dim, prob.n_elem, prob.n_nodes
+    nnz_upper = (int(info.nnz_kkt) + int(info.n_kkt)) // 2
+    asm_bytes = ne * (4 * (d + 1) + 8 * (d * d + 2)) + nn * 8 * d + nnz_upper * 8 + int(info.n_kkt) * 8
+    n_solves = 1 + srep.refine_steps
+    solve_bytes = n_solves * 2 * int(info.nnz_factor) * (4 if fp32 else 8)
+    hbm_phases = {
+        "assembly": {"bytes_per_step": asm_bytes, "ms": phases["assemble_ms"],
+                     "gbs": asm_bytes / (phases["assemble_ms"] * 1e-3) / 1e9,
+                     "frac": asm_bytes / (phases["assemble_ms"] * 1e-3) / 1e9 / hbm, "peak_gbs": hbm,
+                     "peak_source": hbm_src,
+                     "bytes": "n_e (4 (d+1) + 8 (d^2 + 2)) + n_nodes 8 d + nnz_upper(KKT) 8 + N 8"},
+        "solves": {"bytes_per_step": solve_bytes, "solves_per_step": n_solves, "ms": phases["solve_ms"],
+                   "gbs": solve_bytes / (phases["solve_ms"] * 1e-3) / 1e9,
+                   "frac": solve_bytes / (phases["solve_ms"] * 1e-3) / 1e9 / hbm, "peak_gbs": hbm,
+                   "peak_source": hbm_src,
+                   "bytes": "solves x 2 nnz(L) x (4 FP32 | 8 FP64); the phase also holds the FP64 residuals"},
+    }
     if ws == 1:
         cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
         cpu_info["value"] = cpu_rate
@@ -618,6 +694,7 @@ def main():
                    "factor_flops": info.factor_flops,
                    "nnz_factor": info.nnz_factor, "fp64_path": fp64,
                    "phases": phases, "kernel_kinds_profiled_step": kinds, "setup_s": info.setup_seconds, "bind_s": t_setup,
+                   "hbm_phases": hbm_phases, "measured_peaks": run_peaks,
                    "equilibrium": equilibrium},
         "roofline": roofline,
         "cpu_baseline": cpu_info,
