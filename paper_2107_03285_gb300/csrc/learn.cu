@@ -19,8 +19,11 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/sgn_learn.h"
 #include "common.cuh"
+#include "tc_update.cuh"
 
 namespace {
 
@@ -42,6 +45,135 @@ template <typename ACC, typename T>
 __device__ __forceinline__ ACC as_acc(T v) {
   if constexpr (std::is_same_v<T, bf16>) return (ACC)__bfloat162float(v);
   else return (ACC)v;
+}
+
+// ------------------------------------------------ BF16 GEMM on tcgen05
+// C(m, n) = alpha sum_k A(m, k) B(k, n) + beta C(m, n) for the MLP layers:
+// both operands are first packed (converted to BF16, zero-padded) into
+// K-major tiles, A as [Mp][Kp] and B as [Np][Kp] (Mp a multiple of 128, Np
+// of 64, Kp of 64), then one CTA per 128 x 64 output tile streams 64-wide K
+// stages by TMA (128B swizzle) and accumulates in TMEM with
+// tcgen05.mma.kind::f16 (BF16 inputs, FP32 accumulation), 4 MMAs of K = 16
+// per stage.  Warp 0 lane 0 issues the copies, warp 1 lane 0 the MMAs, all
+// four warps read TMEM (32 lanes = 32 rows each) for the epilogue.  Every
+// wait is bounded and records DEV_TIMEOUT on expiry.
+constexpr int GM = 128, GN = 64, GK = 64, GSTAGES = 3;
+constexpr int GA_BYTES = GM * GK * 2, GB_BYTES = GN * GK * 2, GSTAGE_BYTES = GA_BYTES + GB_BYTES;
+constexpr int GSMEM = GSTAGES * GSTAGE_BYTES + 1024;
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = GN
+constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap ma,
+                                                          const __grid_constant__ CUtensorMap mb, int M, int N,
+                                                          int kchunks, float alpha, float beta, float *__restrict__ C,
+                                                          int64_t scm, int64_t scn, int *status) {
+  using namespace sgn::tc;
+  extern __shared__ __align__(1024) unsigned char g_smem_raw[];
+  __shared__ uint64_t full_bar[GSTAGES], empty_bar[GSTAGES], done_bar;
+  __shared__ uint32_t tmem_base;
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GSTAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(GN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  if (warp == 0 && lane == 0) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&ma) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&mb) : "memory");
+    int issued = 0;
+    for (int kc = 0; kc < kchunks; ++kc) {
+      const int s = kc % GSTAGES;
+      if (kc >= GSTAGES && !mbar_wait(&empty_bar[s], ((kc / GSTAGES) - 1) & 1, status, sgn::DEV_TIMEOUT)) break;
+      unsigned char *st = sm + s * GSTAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], GSTAGE_BYTES);
+      tma_load_2d(st, &ma, &full_bar[s], kc * GK, m0);
+      tma_load_2d(st + GA_BYTES, &mb, &full_bar[s], kc * GK, n0);
+      issued = kc + 1;
+    }
+    // the copies still in flight complete before the CTA can exit (bounded)
+    for (int q = (issued > GSTAGES ? issued - GSTAGES : 0); q < issued; ++q)
+      mbar_wait(&full_bar[q % GSTAGES], (q / GSTAGES) & 1, status, sgn::DEV_TIMEOUT);
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16();
+    for (int kc = 0; kc < kchunks; ++kc) {
+      const int s = kc % GSTAGES;
+      if (!mbar_wait(&full_bar[s], (kc / GSTAGES) & 1, status, sgn::DEV_TIMEOUT)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(sm + s * GSTAGE_BYTES);
+#pragma unroll
+      for (int k = 0; k < GK / 16; ++k) {
+        const uint64_t ad = umma_desc_sw128(base + k * 32);
+        const uint64_t bd = umma_desc_sw128(base + GA_BYTES + k * 32);
+        umma_bf16(tmem, ad, bd, idesc, (kc | k) != 0);
+      }
+      umma_commit(&empty_bar[s]);
+    }
+    umma_commit(&done_bar);  // also after an early exit, so the epilogue does not wait out its bound
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0, status, sgn::DEV_TIMEOUT));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < GN; cb += 32) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + cb + j;
+          if (n < N) {
+            float *c = C + (int64_t)m * scm + (int64_t)n * scn;
+            const float r = alpha * __uint_as_float(v[j]);
+            *c = beta != 0.f ? r + beta * *c : r;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GN) : "memory");
+}
+
+// dst[r][c] (rowsP x colsP, BF16) = src(r, c) = src[r srs + c scs] inside
+// rows x cols, zero outside
+template <typename TS>
+__global__ void k_pack_bf16(int rows, int cols, const TS *__restrict__ src, int64_t srs, int64_t scs,
+                            bf16 *__restrict__ dst, int rowsP, int colsP) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rowsP * colsP) return;
+  const int r = (int)(i / colsP), cc = (int)(i % colsP);
+  float v = 0.f;
+  if (r < rows && cc < cols) v = as_acc<float>(src[(int64_t)r * srs + (int64_t)cc * scs]);
+  dst[i] = __float2bfloat16_rn(v);
 }
 
 // ------------------------------------------------------------------- GEMMs
@@ -499,6 +631,8 @@ struct sgn_learn_ctx {
   bf16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr;
   float *Tb = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Yb = nullptr, *dY = nullptr, *dH = nullptr, *dZ = nullptr;
   float *part = nullptr;
+  bf16 *gA = nullptr, *gB = nullptr;  // packed K-major operands of the tensor-core GEMMs
+  int64_t g_elems = 0;                // elements of each
 };
 
 namespace {
@@ -548,6 +682,12 @@ size_t carve_learn(sgn_learn_ctx &L, char *base) {
   L.p16 = c.take<bf16>((size_t)L.n_params);
   L.fan_in = c.take<int32_t>((size_t)L.n_params);
   L.idx = c.take<int32_t>(ms);
+  {
+    const size_t D = std::max({B, nm, H, nr});
+    L.g_elems = (int64_t)(((D + 127) / 128) * 128 * ((D + 63) / 64) * 64);
+    L.gA = c.take<bf16>((size_t)L.g_elems);
+    L.gB = c.take<bf16>((size_t)L.g_elems);
+  }
   L.Xb = c.take<bf16>(B * nr);
   L.Tb = c.take<float>(B * nm);
   L.Z1 = c.take<float>(B * H);
@@ -642,17 +782,69 @@ int orthonormalise(sgn_learn_ctx &L, double *M, int64_t rows, int r, double *scr
 
 // ---- MLP
 // forward of the B rows in Xb; Yb receives the (normalised) outputs
+typedef CUresult (*EncodeTiledFnL)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA map of a packed [rows][kp] BF16 operand, box 64 (K) x box_rows, 128B swizzle
+bool encode_bf16(CUtensorMap *m, void *addr, int kp, int rows, int box_rows) {
+  static EncodeTiledFnL enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = (EncodeTiledFnL)fn;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C(m, n) = alpha sum_k A(m, k) B(k, n) + beta C(m, n) on the tensor cores
+// (same operand convention as gemm above; A and B converted to BF16)
+template <typename TA, typename TB>
+void gemm_tc(sgn_learn_ctx &L, int M, int N, int K, float alpha, const TA *A, int64_t sam, int64_t sak, const TB *B,
+             int64_t sbk, int64_t sbn, float beta, float *C, int64_t scm, int64_t scn) {
+  Ctx &c = *L.h;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+    attr = true;
+  }
+  const int Mp = ((M + GM - 1) / GM) * GM, Np = ((N + GN - 1) / GN) * GN, Kp = ((K + GK - 1) / GK) * GK;
+  if ((int64_t)Mp * Kp > L.g_elems || (int64_t)Np * Kp > L.g_elems) {
+    c.last_error = "tensor-core GEMM operands exceed their packing buffers";
+    return;
+  }
+  k_pack_bf16<TA><<<nblk((int64_t)Mp * Kp), TPB, 0, c.stream>>>(M, K, A, sam, sak, L.gA, Mp, Kp);
+  k_pack_bf16<TB><<<nblk((int64_t)Np * Kp), TPB, 0, c.stream>>>(N, K, B, sbn, sbk, L.gB, Np, Kp);
+  CUtensorMap ma, mb;
+  if (!encode_bf16(&ma, L.gA, Kp, Mp, GM) || !encode_bf16(&mb, L.gB, Kp, Np, GN)) {
+    c.last_error = "cuTensorMapEncodeTiled failed for a GEMM operand";
+    return;
+  }
+  k_gemm_bf16_tc<<<dim3(Np / GN, Mp / GM), 128, GSMEM, c.stream>>>(ma, mb, M, N, Kp / GK, alpha, beta, C, scm, scn,
+                                                                    c.status);
+  c.count(3);
+}
+
 void mlp_forward(sgn_learn_ctx &L, int B) {
   Ctx &c = *L.h;
   const int H = L.hidden, nr = L.n_rbf, nm = L.n_modes;
   const bf16 *W1 = L.p16 + L.off[0], *W2 = L.p16 + L.off[2], *W3 = L.p16 + L.off[4];
   const int64_t bh = (int64_t)B * H, bm = (int64_t)B * nm;
   // Z1[b][o] = sum_i X[b][i] W1[o][i]
-  gemm<bf16, bf16, float, float>(c, B, H, nr, 1.f, L.Xb, nr, 1, W1, 1, nr, 0.f, L.Z1, H, 1);
+  gemm_tc<bf16, bf16>(L, B, H, nr, 1.f, L.Xb, nr, 1, W1, 1, nr, 0.f, L.Z1, H, 1);
   k_bias_gelu<<<nblk(bh), TPB, 0, c.stream>>>(bh, H, L.Z1, L.p32 + L.off[1], L.H1);
-  gemm<bf16, bf16, float, float>(c, B, H, H, 1.f, L.H1, H, 1, W2, 1, H, 0.f, L.Z2, H, 1);
+  gemm_tc<bf16, bf16>(L, B, H, H, 1.f, L.H1, H, 1, W2, 1, H, 0.f, L.Z2, H, 1);
   k_bias_gelu<<<nblk(bh), TPB, 0, c.stream>>>(bh, H, L.Z2, L.p32 + L.off[3], L.H2);
-  gemm<bf16, bf16, float, float>(c, B, nm, H, 1.f, L.H2, H, 1, W3, 1, H, 0.f, L.Yb, nm, 1);
+  gemm_tc<bf16, bf16>(L, B, nm, H, 1.f, L.H2, H, 1, W3, 1, H, 0.f, L.Yb, nm, 1);
   k_bias_add<<<nblk(bm), TPB, 0, c.stream>>>(bm, nm, L.Yb, L.p32 + L.off[5]);
   c.count(3);
 }
@@ -668,17 +860,17 @@ void mlp_backward(sgn_learn_ctx &L, int B) {
   const bf16 *W2 = L.p16 + L.off[2], *W3 = L.p16 + L.off[4];
   float *g = L.g32;
   // output layer: dW3 = dY^T H2, db3 = column sums of dY, dH2 = dY W3
-  gemm<float, bf16, float, float>(c, nm, H, B, 1.f, L.dY, 1, nm, L.H2, H, 1, 0.f, g + L.off[4], H, 1);
+  gemm_tc<float, bf16>(L, nm, H, B, 1.f, L.dY, 1, nm, L.H2, H, 1, 0.f, g + L.off[4], H, 1);
   k_bias_grad<<<nblk(nm), TPB, 0, c.stream>>>(B, nm, L.dY, g + L.off[5]);
-  gemm<float, bf16, float, float>(c, B, H, nm, 1.f, L.dY, nm, 1, W3, H, 1, 0.f, L.dH, H, 1);
+  gemm_tc<float, bf16>(L, B, H, nm, 1.f, L.dY, nm, 1, W3, H, 1, 0.f, L.dH, H, 1);
   k_gelu_bwd<<<nblk(bh), TPB, 0, c.stream>>>(bh, L.dH, L.Z2, L.dZ);
   // hidden layer 2
-  gemm<float, bf16, float, float>(c, H, H, B, 1.f, L.dZ, 1, H, L.H1, H, 1, 0.f, g + L.off[2], H, 1);
+  gemm_tc<float, bf16>(L, H, H, B, 1.f, L.dZ, 1, H, L.H1, H, 1, 0.f, g + L.off[2], H, 1);
   k_bias_grad<<<nblk(H), TPB, 0, c.stream>>>(B, H, L.dZ, g + L.off[3]);
-  gemm<float, bf16, float, float>(c, B, H, H, 1.f, L.dZ, H, 1, W2, H, 1, 0.f, L.dH, H, 1);
+  gemm_tc<float, bf16>(L, B, H, H, 1.f, L.dZ, H, 1, W2, H, 1, 0.f, L.dH, H, 1);
   k_gelu_bwd<<<nblk(bh), TPB, 0, c.stream>>>(bh, L.dH, L.Z1, L.dZ);
   // hidden layer 1
-  gemm<float, bf16, float, float>(c, H, nr, B, 1.f, L.dZ, 1, H, L.Xb, nr, 1, 0.f, g + L.off[0], nr, 1);
+  gemm_tc<float, bf16>(L, H, nr, B, 1.f, L.dZ, 1, H, L.Xb, nr, 1, 0.f, g + L.off[0], nr, 1);
   k_bias_grad<<<nblk(H), TPB, 0, c.stream>>>(B, H, L.dZ, g + L.off[1]);
   c.count(6);
 }
