@@ -93,6 +93,7 @@ def parse():
                     help="largest single-GPU mixed-precision workload, timed once ('' skips)")
     ap.add_argument("--warm-snapshots", type=int, default=128)
     ap.add_argument("--warm-tests", type=int, default=6)
+    ap.add_argument("--warm-train-steps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -411,7 +412,7 @@ def form_warm_start(P, torch, args):
             cold_it.append(rep.iters)
             cold_t.append(dt)
         _, t_basis = _timed(torch, lambda: ws.fit_basis(snaps, seed=1))
-        steps = 3000
+        steps = args.warm_train_steps
         loss, t_train = _timed(torch, lambda: ws.train(thetas[:ns], snaps, steps=steps, lr=1e-3,
                                                        weight_decay=1e-5, seed=2))
         rng = np.random.default_rng(args.seed + 7)
@@ -454,8 +455,9 @@ def form_warm_start(P, torch, args):
         out = {k: summ(v) for k, v in res.items()}
         return {"workload": f"{args.warm_workload}: {prob.n_elem} tets, {prob.n_nodes} nodes, "
                             f"{prob.meta['n_rbf']} RBF coefficients",
-                "reduced": f"{ns} snapshots (not 4,096), {n_modes} modes, MLP {prob.meta['n_rbf']}-512-512-"
-                           f"{n_modes}, {steps} AdamW steps; held-out designs: {nt}",
+                "size": (f"{ns} snapshots" + (" (as configured)" if ns >= 4096 else " (reduced from 4,096)") +
+                         f", {n_modes} modes, MLP {prob.meta['n_rbf']}-512-512-{n_modes}, {steps} AdamW steps; "
+                         f"held-out designs: {nt}"),
                 "snapshots": {"mean_iters": float(np.mean(cold_it)), "mean_seconds": float(np.mean(cold_t))},
                 "basis_seconds": t_basis, "train_seconds": t_train, "train_final_loss": loss,
                 "newton_from": out,
