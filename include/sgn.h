@@ -349,6 +349,51 @@ sgn_status sgn_gradient(sgn_t h, double *g_d);
 /* sgn_factor_k: factor K alone at the assembled (x, p) (FP64). */
 sgn_status sgn_factor_k(sgn_t h);
 
+/* ---- SGN-initialised L-BFGS (Sec. 4, "Combination with L-BFGS") ----------
+ * The Gauss-Newton inverse Hessian initialises L-BFGS: each search direction
+ * is the two-loop recursion (Nocedal & Wright, Alg. 7.4) over the m most
+ * recent pairs s = p_{k+1} - p_k, y = g_{k+1} - g_k with H_0^{-1} q applied
+ * by one solve of Eq. sparseSystemGN (right-hand side [0; -q; 0]) with the
+ * saddle-point factor of the current iterate.
+ *
+ * sgn_objective_value: f(x, p) of Eq. leastSquaresObjective at node
+ * positions x_d and parameters p_d (synchronises). */
+sgn_status sgn_objective_value(sgn_t h, const double *x_d, const double *p_d, double *f_h);
+/* sgn_lbfgs_direction: d_d = -H_k g_d for the pairs s_d, y_d ([m][n_elem]
+ * each, oldest first, y.s > 0) with H_0 = H_GN of the last sgn_assemble +
+ * sgn_factor (ESTATE if that factor is not current).  m = 0 gives the SGN
+ * step itself. */
+sgn_status sgn_lbfgs_direction(sgn_t h, int32_t m, const double *s_d, const double *y_d, const double *g_d,
+                               double *d_d);
+typedef struct {
+  int32_t m;                 /* pairs kept (0: plain SGN steps with the same line search) */
+  int32_t max_iter;          /* outer iterations */
+  double tol_g;              /* stop once ||df/dp|| <= tol_g (0: run max_iter) */
+  int32_t precision;         /* saddle-point factor: SGN_FP64 or SGN_MIXED */
+  int32_t eq_precision;      /* equilibrium Newton: SGN_FP64 or SGN_MIXED */
+  double armijo;             /* sufficient-decrease constant (0: 1e-4) */
+  int32_t max_halvings;      /* line-search trials (0: 30) */
+} sgn_lbfgs_opts;
+typedef struct {
+  int32_t iters, converged, restarts;  /* restarts: steps that fell back to -g */
+  int32_t trials, equilibrium_iters;   /* line-search trials, Newton iterations in all equilibria */
+  double seconds;
+  double f[64], gnorm[64];             /* f and ||df/dp|| at iterate 0, 1, ... */
+  double step[64];                     /* accepted step length of iteration 1, 2, ... */
+} sgn_lbfgs_report;
+/* Device bytes sgn_optimize_lbfgs needs in work_d for m pairs. */
+sgn_status sgn_lbfgs_work_bytes(sgn_t h, int32_t m, size_t *bytes);
+/* sgn_optimize_lbfgs: L-BFGS iterations on p (device, in/out) for the
+ * external load fext_d: every iterate's equilibrium x(p) by sgn_equilibrium
+ * (x_d: initial guess in, the last iterate's equilibrium out), the adjoint
+ * gradient (sgn_factor_k + sgn_gradient), the direction above, and a
+ * backtracking line search on f(x(p), p) (Armijo; a trial whose Newton
+ * fails counts as no decrease).  Needs SGN_STORE_KFACT and the saddle-point
+ * store of opts->precision; work_d (caller-owned, sgn_lbfgs_work_bytes) holds
+ * the pairs and vectors, so the call allocates nothing.  Synchronises. */
+sgn_status sgn_optimize_lbfgs(sgn_t h, const double *fext_d, double *p_d, double *x_d, void *work_d,
+                              size_t work_bytes, const sgn_lbfgs_opts *opts, sgn_lbfgs_report *rep);
+
 /* ---- measurement support (no counterpart in the paper) ------------------
  * sgn_profile(h, mask) resets the per-kernel timers and enables CUDA-event
  * timing (on the context's stream) of every launch of the kernel kinds whose

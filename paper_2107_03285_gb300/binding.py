@@ -29,7 +29,8 @@ EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_se
             "sgn_solve", "sgn_step_host", "sgn_equilibrium", "sgn_gradient", "sgn_factor_k",
             "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
             "sgn_last_error", "sgn_selftest_wait_timeout", "sgn_batch_setup", "sgn_batch_info", "sgn_batch_residuals",
-            "sgn_factor_ex",
+            "sgn_factor_ex", "sgn_objective_value", "sgn_lbfgs_direction", "sgn_lbfgs_work_bytes",
+            "sgn_optimize_lbfgs",
             # learned warm start (include/sgn_learn.h)
             "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
             "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
@@ -80,6 +81,17 @@ class FactorOpts(C.Structure):
     _fields_ = [("eps_x", C.c_double), ("eps_lambda", C.c_double)]
 
 
+class LbfgsOpts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("max_iter", C.c_int32), ("tol_g", C.c_double), ("precision", C.c_int32),
+                ("eq_precision", C.c_int32), ("armijo", C.c_double), ("max_halvings", C.c_int32)]
+
+
+class LbfgsReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("restarts", C.c_int32), ("trials", C.c_int32),
+                ("equilibrium_iters", C.c_int32), ("seconds", C.c_double), ("f", C.c_double * 64),
+                ("gnorm", C.c_double * 64), ("step", C.c_double * 64)]
+
+
 class KernelProfile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("seconds", C.c_double), ("flops", C.c_double)]
 
@@ -119,6 +131,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_step_graph": (C.c_int, [VP, C.c_int, C.c_int32, VP, VP, VP, VP, VP, dp]),
         "sgn_factor": (C.c_int, [VP, C.c_int, P(FactorReport)]),
         "sgn_factor_ex": (C.c_int, [VP, C.c_int, P(FactorOpts), P(FactorReport)]),
+        "sgn_objective_value": (C.c_int, [VP, VP, VP, dp]),
+        "sgn_lbfgs_direction": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
+        "sgn_lbfgs_work_bytes": (C.c_int, [VP, C.c_int32, P(C.c_size_t)]),
+        "sgn_optimize_lbfgs": (C.c_int, [VP, VP, VP, VP, VP, C.c_size_t, P(LbfgsOpts), P(LbfgsReport)]),
         "sgn_solve": (C.c_int, [VP, C.c_int, VP, VP, VP, VP, P(SolveOpts), P(SolveReport)]),
         "sgn_step_host": (C.c_int, [VP, C.c_int, dp, dp, dp, dp, dp, P(SolveReport)]),
         "sgn_equilibrium": (C.c_int, [VP, VP, VP, VP, P(NewtonOpts), P(NewtonReport)]),

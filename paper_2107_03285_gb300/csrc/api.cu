@@ -317,6 +317,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
   c.xsave = cv.take<double>(nn); c.xrt = cv.take<double>(nx); c.ueq = cv.take<double>(nn);
   c.hx = cv.take<double>(nn); c.hdx = cv.take<double>(nn); c.hdl = cv.take<double>(nn);
   c.hp = cv.take<double>(ne); c.hdp = cv.take<double>(ne);
+  c.lbq = cv.take<double>(ne); c.lbr = cv.take<double>(ne);
   if (c.n_inst > 0) {
     int32_t *p_;
     st_up(p_, c.h_rank_inst); c.rank_inst = p_;
@@ -609,6 +610,7 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
   const Symbolic &S = h->S;
   const int d = S.dim;
   std::vector<double> w((size_t)S.n_free * d, 0.0), t((size_t)S.n_free * d, 0.0);
+  double wt2 = 0.0;  // sum w t^2 over the given entries
   for (int i = 0; i < obj->n_track; ++i) {
     int64_t g = obj->track_dof_h[i];
     if (g < 0 || g >= (int64_t)S.n_nodes * d) { g_err = "tracked DOF out of range"; return SGN_EINVAL; }
@@ -617,6 +619,7 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
     if (!(obj->weight_h[i] >= 0.0)) { g_err = "negative weight"; return SGN_EINVAL; }
     int64_t rd = (int64_t)r * d + g % d;
     // repeated DOFs add up: sum_t w_t (x - target_t)^2 = (sum w)(x - wavg)^2 + const
+    wt2 += obj->weight_h[i] * obj->target_h[i] * obj->target_h[i];
     double wn = w[rd] + obj->weight_h[i];
     t[rd] = wn > 0 ? (w[rd] * t[rd] + obj->weight_h[i] * obj->target_h[i]) / wn : 0.0;
     w[rd] = wn;
@@ -624,6 +627,9 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
   CUDA_TRY(h, cudaMemcpyAsync(h->wA, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(h->tgt, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  double merged = 0.0;
+  for (size_t i = 0; i < w.size(); ++i) merged += w[i] * t[i] * t[i];
+  h->f_const = 0.5 * (wt2 - merged);
   h->alpha = obj->alpha;
   h->have_objective = true;
   h->assembled = false;

@@ -164,7 +164,9 @@ struct Ctx {
   double *fx = nullptr, *fp = nullptr;   // df/dx [n_x], df/dp [n_elem] at the last assembly
   double *xr = nullptr;             // [n_x] positions at the last assembly (rank-DOF)
   double alpha = 0.0;
+  double f_const = 0.0;             // 1/2 sum w t^2 lost when repeated tracked DOFs are merged
   bool have_objective = false, assembled = false;
+  double *lbq = nullptr, *lbr = nullptr;  // [n_elem] scratch of the L-BFGS two-loop recursion
 
   // refinement vectors (rank-DOF for x and lambda, element order for p)
   double *bx = nullptr, *bp = nullptr, *bl = nullptr;
@@ -302,6 +304,9 @@ void destroy_graphs(Store &s);
 // ---- batch.cu: per-instance norms of a batched handle (no-ops otherwise)
 void batch_record_equilibrium(Ctx &c, const double *cr, const double *fr);
 void batch_record_solve(Ctx &c);
+
+// ---- lbfgs.cu: f(x, p) of the handle's objective (synchronises)
+double objective_value(Ctx &c, const double *x, const double *p);
 
 // ---- error reporting (api.cu): sets the handle's detail (if h) and the
 // message sgn_strerror returns for the status

@@ -252,6 +252,42 @@ class SGN:
     def launch_count(self):
         return int(self.lib.sgn_launch_count(self.h))
 
+    def objective(self, x, p):
+        """f(x, p) of the handle's objective (sgn_objective_value)."""
+        f = C.c_double()
+        B._check(self.lib.sgn_objective_value(self.h, self._p(self._dev(x, (self.n_nodes, self.dim))),
+                                              self._p(self._dev(p, (self.n_elem,))), C.byref(f)),
+                 "sgn_objective_value", self.h)
+        return f.value
+
+    def lbfgs_direction(self, S, Y, g):
+        """-H_k g over the pairs S, Y ([m][n_elem], oldest first) with the SGN
+        inverse of the current factor as H_0 (sgn_lbfgs_direction)."""
+        m = 0 if S is None else int(S.shape[0])
+        gd = self._dev(g, (self.n_elem,))
+        d = self._empty(self.n_elem)
+        Sd = self._dev(S, (m, self.n_elem)) if m else None
+        Yd = self._dev(Y, (m, self.n_elem)) if m else None
+        B._check(self.lib.sgn_lbfgs_direction(self.h, m, self._p(Sd), self._p(Yd), self._p(gd), self._p(d)),
+                 "sgn_lbfgs_direction", self.h)
+        return d
+
+    def optimize_lbfgs(self, p0, fext, x0=None, m=5, max_iter=10, tol_g=0.0, precision=B.MIXED,
+                       eq_precision=B.MIXED):
+        """SGN-initialised L-BFGS (sgn_optimize_lbfgs): returns (p, x, report)."""
+        p = self._dev(p0, (self.n_elem,)).clone()
+        x = self._dev(self.X if x0 is None else x0, (self.n_nodes, self.dim)).clone()
+        fd = self._dev(fext, (self.n_nodes, self.dim))
+        nbytes = C.c_size_t()
+        B._check(self.lib.sgn_lbfgs_work_bytes(self.h, int(m), C.byref(nbytes)), "sgn_lbfgs_work_bytes", self.h)
+        work = self._torch.empty(int(nbytes.value), dtype=self._torch.uint8, device=self.device)
+        rep = B.LbfgsReport()
+        opts = B.LbfgsOpts(int(m), int(max_iter), float(tol_g), int(precision), int(eq_precision), 0.0, 0)
+        B._check(self.lib.sgn_optimize_lbfgs(self.h, self._p(fd), self._p(p), self._p(x),
+                                             C.c_void_p(work.data_ptr()), int(nbytes.value), C.byref(opts),
+                                             C.byref(rep)), "sgn_optimize_lbfgs", self.h)
+        return p, x, rep
+
     def factor_k(self):
         B._check(self.lib.sgn_factor_k(self.h), "sgn_factor_k", self.h)
 
