@@ -399,18 +399,30 @@ def form_warm_start(P, torch, args):
     ws = P.WarmStart(s, prob.meta["rbf_centers"], prob.meta["rbf_width"], n_modes=n_modes, hidden=512,
                      max_snap=ns, batch=min(64, ns))
     try:
-        thetas = draw_thetas(prob, ns + nt, seed=args.seed + 101)
+        # designs whose Newton solve does not converge (the far tail of theta)
+        # are replaced by further draws, and counted
+        spare = max(8, ns // 16)
+        thetas_all = draw_thetas(prob, ns + nt + spare, seed=args.seed + 101)
         X = torch.as_tensor(prob.X, device="cuda")
         snaps = torch.empty((ns,) + tuple(X.shape), dtype=torch.float64, device="cuda")
-        cold_it, cold_t = [], []
-        for i in range(ns):
-            (x, rep), dt = _timed(torch, lambda: s.equilibrium(ws.rbf_params(thetas[i]), prob.fext,
+        cold_it, cold_t, kept, failed = [], [], [], []
+        for i in range(ns + spare):
+            if len(kept) == ns:
+                break
+            (x, rep), dt = _timed(torch, lambda: s.equilibrium(ws.rbf_params(thetas_all[i]), prob.fext,
                                                                precision=P.MIXED))
             if not rep.converged:
-                raise RuntimeError("snapshot equilibrium did not converge")
-            snaps[i] = x - X
+                failed.append({"iters": rep.iters, "residual": rep.residual})
+                continue
+            snaps[len(kept)] = x - X
+            kept.append(i)
             cold_it.append(rep.iters)
             cold_t.append(dt)
+        if len(kept) < ns:
+            raise RuntimeError(f"only {len(kept)} of {ns} snapshot equilibria converged: {failed[:4]}")
+        used = set(kept)
+        rest = [i for i in range(len(thetas_all)) if i not in used and i > kept[-1]]
+        thetas = np.concatenate([thetas_all[kept], thetas_all[rest[:nt]]])
         _, t_basis = _timed(torch, lambda: ws.fit_basis(snaps, seed=1))
         steps = args.warm_train_steps
         loss, t_train = _timed(torch, lambda: ws.train(thetas[:ns], snaps, steps=steps, lr=1e-3,
@@ -458,7 +470,8 @@ def form_warm_start(P, torch, args):
                 "size": (f"{ns} snapshots" + (" (as configured)" if ns >= 4096 else " (reduced from 4,096)") +
                          f", {n_modes} modes, MLP {prob.meta['n_rbf']}-512-512-{n_modes}, {steps} AdamW steps; "
                          f"held-out designs: {nt}"),
-                "snapshots": {"mean_iters": float(np.mean(cold_it)), "mean_seconds": float(np.mean(cold_t))},
+                "snapshots": {"mean_iters": float(np.mean(cold_it)), "mean_seconds": float(np.mean(cold_t)),
+                              "not_converged": len(failed), "not_converged_sample": failed[:4]},
                 "basis_seconds": t_basis, "train_seconds": t_train, "train_final_loss": loss,
                 "newton_from": out,
                 "iters_saved_vs_rest": out["rest"]["mean_iters"] - out["learned"]["mean_iters"],

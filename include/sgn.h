@@ -110,7 +110,8 @@ typedef struct {
   int32_t n_track;
   const int64_t *track_dof_h; /* global DOF ids node*dim+comp; must be free DOFs */
   const double *target_h;     /* [n_track] */
-  const double *weight_h;     /* [n_track] w_t > 0 */
+  const double *weight_h;     /* [n_track] weights (negative ones make A indefinite: see
+                                 sgn_factor_inertia) */
   double alpha;               /* Tikhonov weight, > 0 (C = alpha I) */
 } sgn_objective;
 
@@ -155,6 +156,8 @@ typedef struct {
                                      the FP64 round-off floor of the 40^3 system, ~1.4e-13) */
   int32_t method;                 /* sgn_solve_method (0: SGN_SOLVE_AUTO) */
   int32_t max_krylov;             /* BiCGSTAB iterations (default 0 -> 200) */
+  int32_t regularized;            /* 1: solve the factored matrix itself, M + diag(eps_x, 0, -eps_lambda)
+                                     (the step of an inertia-corrected factorization); 0: solve M */
 } sgn_solve_opts;
 
 typedef struct {
@@ -247,6 +250,23 @@ sgn_status sgn_factor(sgn_t h, sgn_precision prec, sgn_factor_report *report);
 /* sgn_factor_ex: sgn_factor of the stabilized matrix of sgn_factor_opts
  * (opts NULL: as sgn_factor).  EINVAL for a negative eps. */
 sgn_status sgn_factor_ex(sgn_t h, sgn_precision prec, const sgn_factor_opts *opts, sgn_factor_report *report);
+/* sgn_factor_inertia: the inertia test with diagonal regularization that
+ * Sec. 5 ("Solving the saddle point problem") uses for its Newton-type
+ * variants (after Han 1985): factor M, and while the inertia is not
+ * (n_x + n_p, n_x, 0) -- i.e. the reduced Hessian is not positive definite
+ * on the null space of the constraint Jacobian, as happens with an
+ * indefinite A (negative tracking weights) -- refactor with delta added to
+ * the x diagonal, delta = delta0, delta0 growth, delta0 growth^2, ...  The
+ * chosen delta goes to *delta_h (0: M itself was fine); solve the
+ * regularized system with sgn_solve_opts.regularized = 1.  EPIVOT if
+ * max_tries factorizations did not reach the inertia. */
+typedef struct {
+  double delta0;                  /* first regularization (0: 1e-4 x the largest |tracked weight|) */
+  double growth;                  /* factor between attempts (0: 10) */
+  int32_t max_tries;              /* factorizations at most (0: 30) */
+} sgn_inertia_opts;
+sgn_status sgn_factor_inertia(sgn_t h, sgn_precision prec, const sgn_inertia_opts *opts, double *delta_h,
+                              sgn_factor_report *report);
 /* sgn_solve: (dx, dp, dl) of Eq. sparseSystemGN by forward, diagonal and
  * backward substitution with the factor, followed by FP64 iterative
  * refinement against the assembled matrix.  g_d = df/dp for SGN_RHS_PAPER

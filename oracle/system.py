@@ -253,3 +253,30 @@ def inertia(M) -> tuple:
     ev = np.linalg.eigvalsh(M.toarray() if sp.issparse(M) else M)
     tol = 1e-10 * np.max(np.abs(ev))
     return int(np.sum(ev > tol)), int(np.sum(ev < -tol)), int(np.sum(np.abs(ev) <= tol))
+
+
+def regularized_blocks(b: Blocks, delta: float) -> Blocks:
+    """The blocks with delta added to A (x diagonal): the matrix M(delta) an
+    inertia-corrected factorization solves (Sec. 5, "Solving the saddle point
+    problem": diagonal regularization after an inertia test)."""
+    n_x = b.K.shape[0]
+    return Blocks(K=b.K, cp=b.cp, A=(b.A + delta * sp.identity(n_x)).tocsr(), C=b.C, fx=b.fx, fp=b.fp, c=b.c)
+
+
+def inertia_corrected(b: Blocks, delta0: float, growth: float = 10.0, max_tries: int = 30):
+    """The first delta of 0, delta0, delta0 growth, ... for which the reduced
+    Hessian H(delta) = S^T (A + delta I) S + C is positive definite (the
+    saddle-point inertia test), and the Gauss-Newton step there:
+    (delta, dp, H(delta))."""
+    S = sensitivity(b)
+    delta = 0.0
+    for _ in range(max_tries):
+        H = S.T @ ((b.A + delta * sp.identity(b.K.shape[0])) @ S) + b.C.toarray()
+        try:
+            c = sla.cho_factor(H)
+        except np.linalg.LinAlgError:
+            delta = delta0 if delta == 0.0 else delta * growth
+            continue
+        g = b.fp + S.T @ b.fx
+        return delta, -sla.cho_solve(c, g), H
+    raise RuntimeError("no regularization made the reduced Hessian positive definite")

@@ -30,7 +30,7 @@ EXPORTED = ["sgn_setup", "sgn_get_info", "sgn_device_bytes", "sgn_bind", "sgn_se
             "sgn_export_kkt", "sgn_profile", "sgn_profile_read", "sgn_launch_count", "sgn_assemble_static", "sgn_step_graph",
             "sgn_last_error", "sgn_selftest_wait_timeout", "sgn_batch_setup", "sgn_batch_info", "sgn_batch_residuals",
             "sgn_factor_ex", "sgn_objective_value", "sgn_lbfgs_direction", "sgn_lbfgs_work_bytes",
-            "sgn_optimize_lbfgs",
+            "sgn_optimize_lbfgs", "sgn_factor_inertia",
             # learned warm start (include/sgn_learn.h)
             "sgn_learn_create", "sgn_learn_device_bytes", "sgn_learn_bind", "sgn_learn_destroy",
             "sgn_rbf_params", "sgn_learn_basis", "sgn_learn_train", "sgn_learn_predict",
@@ -69,7 +69,12 @@ class FactorReport(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("max_refine", C.c_int32), ("tol", C.c_double), ("method", C.c_int32), ("max_krylov", C.c_int32)]
+    _fields_ = [("max_refine", C.c_int32), ("tol", C.c_double), ("method", C.c_int32), ("max_krylov", C.c_int32),
+                ("regularized", C.c_int32)]
+
+
+class InertiaOpts(C.Structure):
+    _fields_ = [("delta0", C.c_double), ("growth", C.c_double), ("max_tries", C.c_int32)]
 
 
 class SolveReport(C.Structure):
@@ -132,6 +137,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sgn_factor": (C.c_int, [VP, C.c_int, P(FactorReport)]),
         "sgn_factor_ex": (C.c_int, [VP, C.c_int, P(FactorOpts), P(FactorReport)]),
         "sgn_objective_value": (C.c_int, [VP, VP, VP, dp]),
+        "sgn_factor_inertia": (C.c_int, [VP, C.c_int, P(InertiaOpts), dp, P(FactorReport)]),
         "sgn_lbfgs_direction": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP]),
         "sgn_lbfgs_work_bytes": (C.c_int, [VP, C.c_int32, P(C.c_size_t)]),
         "sgn_optimize_lbfgs": (C.c_int, [VP, VP, VP, VP, VP, C.c_size_t, P(LbfgsOpts), P(LbfgsReport)]),

@@ -616,7 +616,7 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
     if (g < 0 || g >= (int64_t)S.n_nodes * d) { g_err = "tracked DOF out of range"; return SGN_EINVAL; }
     int r = S.node_rank[g / d];
     if (r < 0) { g_err = "tracked DOF is fixed"; return SGN_EINVAL; }
-    if (!(obj->weight_h[i] >= 0.0)) { g_err = "negative weight"; return SGN_EINVAL; }
+    if (!std::isfinite(obj->weight_h[i])) { g_err = "weight is not finite"; return SGN_EINVAL; }
     int64_t rd = (int64_t)r * d + g % d;
     // repeated DOFs add up: sum_t w_t (x - target_t)^2 = (sum w)(x - wavg)^2 + const
     wt2 += obj->weight_h[i] * obj->target_h[i] * obj->target_h[i];
@@ -630,6 +630,8 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
   double merged = 0.0;
   for (size_t i = 0; i < w.size(); ++i) merged += w[i] * t[i] * t[i];
   h->f_const = 0.5 * (wt2 - merged);
+  h->max_w = 0.0;
+  for (double v : w) h->max_w = std::max(h->max_w, std::fabs(v));
   h->alpha = obj->alpha;
   h->have_objective = true;
   h->assembled = false;
@@ -712,6 +714,35 @@ sgn_status sgn_factor_ex(sgn_t h, sgn_precision prec, const sgn_factor_opts *opt
   return SGN_OK;
 }
 
+sgn_status sgn_factor_inertia(sgn_t h, sgn_precision prec, const sgn_inertia_opts *opts, double *delta_h,
+                              sgn_factor_report *rep) {
+  if (!h) return SGN_EINVAL;
+  if (!h->assembled) return SGN_ESTATE;
+  const double d0 = opts && opts->delta0 > 0 ? opts->delta0 : 1e-4 * std::max(h->max_w, 1e-300);
+  const double grow = opts && opts->growth > 1 ? opts->growth : 10.0;
+  const int tries = opts && opts->max_tries > 0 ? opts->max_tries : 30;
+  const int64_t nx = (int64_t)h->S.n_free * h->S.dim, np = h->S.n_elem;
+  double delta = 0.0;
+  sgn_factor_report r{};
+  for (int t = 0; t < tries; ++t) {
+    sgn_factor_opts fo{delta, 0.0};
+    sgn_status s = sgn_factor_ex(h, prec, &fo, &r);
+    if (s != SGN_OK) return s;
+    // the inertia (n_x + n_p, n_x, 0) <=> the reduced Hessian is positive
+    // definite on the null space of the constraint Jacobian
+    if (r.n_pos == nx + np && r.n_neg == nx && r.n_zero == 0) {
+      if (delta_h) *delta_h = delta;
+      if (rep) *rep = r;
+      return SGN_OK;
+    }
+    delta = delta == 0.0 ? d0 : delta * grow;
+  }
+  set_error(h, "sgn_factor_inertia: no regularization up to the try limit gave the saddle-point inertia");
+  if (delta_h) *delta_h = delta;
+  if (rep) *rep = r;
+  return SGN_EPIVOT;
+}
+
 sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d, double *dp_d, double *dl_d,
                      const sgn_solve_opts *opts, sgn_solve_report *rep) {
   if (!h || !dp_d) return SGN_EINVAL;
@@ -725,6 +756,15 @@ sgn_status sgn_solve(sgn_t h, sgn_rhs_mode mode, const double *g_d, double *dx_d
   double tol = opts && opts->tol > 0 ? opts->tol : 1e-12;
   const int method = opts ? opts->method : SGN_SOLVE_AUTO;
   if (method < SGN_SOLVE_AUTO || method > SGN_SOLVE_BICGSTAB) return SGN_EINVAL;
+  // the system solved: M, or the factored M(delta) of an inertia correction
+  struct ResEps {
+    Ctx &c;
+    ~ResEps() { c.res_eps_x = c.res_eps_l = 0.0; }
+  } res_eps_reset{c};
+  if (opts && opts->regularized) {
+    c.res_eps_x = st.eps_x;
+    c.res_eps_l = st.eps_l;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (rep) {
     CUDA_TRY(h, cudaEventCreate(&e0)); CUDA_TRY(h, cudaEventCreate(&e1));

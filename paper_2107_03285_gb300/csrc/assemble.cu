@@ -277,14 +277,16 @@ __global__ void k_residual_nodes(int n_free, int ne, const int32_t *__restrict__
                                  const double *__restrict__ bx, const double *__restrict__ bl,
                                  const double *__restrict__ zx, const double *__restrict__ zp,
                                  const double *__restrict__ zl, double *__restrict__ rx,
-                                 double *__restrict__ rl) {
+                                 double *__restrict__ rl, double eps_x, double eps_l) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_free) return;
   double ax[D], al[D];
+  // the x and lambda diagonals carry eps_x and -eps_l when the regularized
+  // matrix of an inertia-corrected factorization is solved (else both 0)
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    ax[a] = bx[(int64_t)r * D + a] - wA[(int64_t)r * D + a] * zx[(int64_t)r * D + a];
-    al[a] = bl[(int64_t)r * D + a];
+    ax[a] = bx[(int64_t)r * D + a] - (wA[(int64_t)r * D + a] + eps_x) * zx[(int64_t)r * D + a];
+    al[a] = fma(eps_l, zl[(int64_t)r * D + a], bl[(int64_t)r * D + a]);
   }
   for (int k = bsr_ptr[r]; k < bsr_ptr[r + 1]; ++k) {
     int c = bsr_col[k];
@@ -548,7 +550,7 @@ void launch_residual(Ctx &c, const double *bx, const double *bp, const double *b
                      const double *zp, const double *zl, double *rx, double *rp, double *rl) {
   const DevSym &d = c.ds;
   SGN_DISPATCH_D(c, k_residual_nodes, nblk(d.n_free), TPB, 0, d.n_free, d.n_elem, d.bsr_ptr, d.bsr_col, c.Kv,
-                 d.inc_ptr, d.inc, c.cpv, c.wA, bx, bl, zx, zp, zl, rx, rl);
+                 d.inc_ptr, d.inc, c.cpv, c.wA, bx, bl, zx, zp, zl, rx, rl, c.res_eps_x, c.res_eps_l);
   SGN_DISPATCH_D(c, k_residual_p, nblk(d.n_elem), TPB, 0, d.n_elem, d.elem_rank, c.cpv, c.alpha, bp, zp, zl, rp);
 }
 

@@ -165,6 +165,8 @@ struct Ctx {
   double *xr = nullptr;             // [n_x] positions at the last assembly (rank-DOF)
   double alpha = 0.0;
   double f_const = 0.0;             // 1/2 sum w t^2 lost when repeated tracked DOFs are merged
+  double max_w = 0.0;               // largest |tracked weight|
+  double res_eps_x = 0.0, res_eps_l = 0.0;  // regularization the residuals include (solves of M(delta))
   bool have_objective = false, assembled = false;
   double *lbq = nullptr, *lbr = nullptr;  // [n_elem] scratch of the L-BFGS two-loop recursion
 

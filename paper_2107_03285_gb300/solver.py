@@ -166,11 +166,11 @@ class SGN:
         return rep
 
     def solve(self, mode=B.RHS_KKT, g=None, max_refine=0, tol=0.0, report=True, out=None, method=B.SOLVE_AUTO,
-              max_krylov=0):
+              max_krylov=0, regularized=False):
         dx, dp, dl = out if out is not None else (self._empty(self.n_nodes, self.dim), self._empty(self.n_elem),
                                                    self._empty(self.n_nodes, self.dim))
         gd = self._dev(g, (self.n_elem,)) if g is not None else None
-        opts = B.SolveOpts(int(max_refine), float(tol), int(method), int(max_krylov))
+        opts = B.SolveOpts(int(max_refine), float(tol), int(method), int(max_krylov), int(bool(regularized)))
         rep = B.SolveReport() if report else None
         B._check(self.lib.sgn_solve(self.h, int(mode), self._p(gd), self._p(dx), self._p(dp), self._p(dl),
                                     C.byref(opts), C.byref(rep) if report else None), "sgn_solve", self.h)
@@ -251,6 +251,17 @@ class SGN:
 
     def launch_count(self):
         return int(self.lib.sgn_launch_count(self.h))
+
+    def factor_inertia(self, precision=B.FP64, delta0=0.0, growth=0.0, max_tries=0):
+        """Inertia-corrected factorization (sgn_factor_inertia): returns
+        (delta, factor report)."""
+        rep = B.FactorReport()
+        delta = C.c_double()
+        B._check(self.lib.sgn_factor_inertia(self.h, int(precision), C.byref(B.InertiaOpts(float(delta0),
+                                                                                           float(growth),
+                                                                                           int(max_tries))),
+                                             C.byref(delta), C.byref(rep)), "sgn_factor_inertia", self.h)
+        return delta.value, rep
 
     def objective(self, x, p):
         """f(x, p) of the handle's objective (sgn_objective_value)."""

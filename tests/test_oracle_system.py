@@ -168,3 +168,36 @@ def test_newton_iterate_is_translation_invariant():
     assert ia["residual"] <= 1e-10 and ib["residual"] <= 1e-10
     np.testing.assert_array_equal(ia["u"], ib["u"])
     assert ia["history"] == ib["history"]
+
+
+def _indefinite_problem():
+    """tiny2d with its tracked weights made negative on one coordinate each:
+    A indefinite, and the reduced Hessian indefinite too."""
+    from sgn_inputs import problem_tiny_2d
+    prob = problem_tiny_2d()
+    w = prob.weight.copy()
+    w[::2] = -1e4
+    prob.weight = w
+    x, _ = EQ.newton(prob, prob.p0)
+    return prob, x
+
+
+def test_inertia_correction_finds_the_first_definite_regularization():
+    prob, x = _indefinite_problem()
+    b = S.blocks(prob, x, prob.p0)
+    S0 = S.sensitivity(b)
+    H0 = S0.T @ (b.A @ S0) + b.C.toarray()
+    assert np.linalg.eigvalsh(H0).min() < 0  # the unregularized step is not a descent one
+    delta, dp, H = S.inertia_corrected(b, delta0=1.0)
+    assert delta > 0
+    assert np.linalg.eigvalsh(H).min() > 0
+    Hprev = S0.T @ ((b.A + (delta / 10.0) * np.eye(b.K.shape[0])) @ S0) + b.C.toarray()
+    assert delta == 1.0 or np.linalg.eigvalsh(Hprev).min() <= 0
+    # the saddle-point inertia test agrees: (n_x + n_p, n_x, 0) exactly when H(delta) > 0
+    n_x, n_p = b.K.shape[0], prob.n_elem
+    bd = S.regularized_blocks(b, delta)
+    assert S.inertia(S.kkt_matrix(bd)) == (n_x + n_p, n_x, 0)
+    assert S.inertia(S.kkt_matrix(b)) != (n_x + n_p, n_x, 0)
+    # Theorem 1 at delta: the sparse saddle-point step of M(delta) is the dense one
+    _, dps, _ = S.sgn_step(bd, "kkt")
+    np.testing.assert_allclose(dps, dp, rtol=1e-9, atol=1e-12 * np.abs(dp).max())
