@@ -621,7 +621,7 @@ sgn_status sgn_set_objective(sgn_t h, const sgn_objective *obj) {
     // repeated DOFs add up: sum_t w_t (x - target_t)^2 = (sum w)(x - wavg)^2 + const
     wt2 += obj->weight_h[i] * obj->target_h[i] * obj->target_h[i];
     double wn = w[rd] + obj->weight_h[i];
-    t[rd] = wn > 0 ? (w[rd] * t[rd] + obj->weight_h[i] * obj->target_h[i]) / wn : 0.0;
+    t[rd] = wn != 0.0 ? (w[rd] * t[rd] + obj->weight_h[i] * obj->target_h[i]) / wn : 0.0;
     w[rd] = wn;
   }
   CUDA_TRY(h, cudaMemcpyAsync(h->wA, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));

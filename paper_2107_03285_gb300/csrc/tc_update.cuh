@@ -130,9 +130,11 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 // of one front; two TMEM accumulators (2 x 128 columns) let the epilogue of tile i
 // run while the producer and MMA warps already work on tile i + 1.
 //   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
-//   warps 2..5    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31)
+//   warps 2..9    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31,
+//                   columns 64 ((w - 2) / 4) .. + 63 of the tile)
 constexpr int PSTAGES = 3;
-constexpr int PTHREADS = 192;
+constexpr int PTHREADS = 320;
+constexpr int EPI_WARPS = 8;
 constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;  // + alignment slack
 
 struct TileJob {                 // one front's part of a trailing update
@@ -181,7 +183,7 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
   const int my_tiles = first < job.ntiles ? (job.ntiles - first + stride - 1) / stride : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < PSTAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], EPI_WARPS); }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -267,8 +269,10 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
       }
     }
   } else {
-    // epilogue warps 2..5
+    // epilogue warps 2..9: a quarter of the tile's rows (TMEM lanes) and
+    // half of its columns each
     const int quad = warp & 3;
+    const int col0 = ((warp - 2) / 4) * (TILE / 2);
     const int r = quad * 32 + lane;
     for (int lt = 0; lt < my_tiles && kch > 0; ++lt) {
       const int b = lt & 1;
@@ -286,7 +290,7 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
       const int64_t gi = (int64_t)job.kend + bi * TILE + r, gj0 = (int64_t)job.kend + bj * TILE;
       const int64_t fcb = job.f - job.ns;
 #pragma unroll 1
-      for (int cb = 0; cb < TILE; cb += 32) {
+      for (int cb = col0; cb < col0 + TILE / 2; cb += 32) {
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + cb), v);
         if (r < rows) {

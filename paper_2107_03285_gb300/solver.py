@@ -266,9 +266,10 @@ class SGN:
     def objective(self, x, p):
         """f(x, p) of the handle's objective (sgn_objective_value)."""
         f = C.c_double()
-        B._check(self.lib.sgn_objective_value(self.h, self._p(self._dev(x, (self.n_nodes, self.dim))),
-                                              self._p(self._dev(p, (self.n_elem,))), C.byref(f)),
-                 "sgn_objective_value", self.h)
+        xd = self._dev(x, (self.n_nodes, self.dim))  # kept alive across the call
+        pd = self._dev(p, (self.n_elem,))
+        B._check(self.lib.sgn_objective_value(self.h, self._p(xd), self._p(pd), C.byref(f)), "sgn_objective_value",
+                 self.h)
         return f.value
 
     def lbfgs_direction(self, S, Y, g):

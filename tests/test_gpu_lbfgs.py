@@ -77,12 +77,15 @@ def test_optimizer_iterations_match_oracle(P):
     s.close()
 
 
-def test_mixed_optimizer_decreases_the_objective(P):
-    """grid2d_21 with FP32 saddle-point fronts and mixed Newton: eight
-    iterations with m = 5 lower f monotonically."""
+def test_mixed_optimizer_follows_the_fp64_one(P):
+    """grid2d_21, five iterations with m = 5: FP32 saddle-point fronts with
+    FP64 refinement and mixed Newton take the FP64 path's steps (the same
+    objective values to 1e-7) and lower f monotonically."""
     prob = problem_2d()
-    s = P.SGN.from_problem(prob, stores=P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED)
-    p, x, rep = s.optimize_lbfgs(prob.p0, prob.fext, m=5, max_iter=8)
-    fh = list(rep.f)[:rep.iters + 1]
-    assert rep.iters == 8 and all(b <= a for a, b in zip(fh, fh[1:])) and fh[-1] < 0.9 * fh[0]
+    s = P.SGN.from_problem(prob, stores=P.STORE_FP64 | P.STORE_MIXED | P.STORE_KFACT | P.STORE_KFACT_MIXED)
+    _, _, r64 = s.optimize_lbfgs(prob.p0, prob.fext, m=5, max_iter=5, precision=P.FP64, eq_precision=P.FP64)
+    _, _, rmx = s.optimize_lbfgs(prob.p0, prob.fext, m=5, max_iter=5, precision=P.MIXED, eq_precision=P.MIXED)
+    f64, fmx = list(r64.f)[:6], list(rmx.f)[:6]
+    np.testing.assert_allclose(fmx, f64, rtol=1e-7)
+    assert all(b <= a for a, b in zip(fmx, fmx[1:])) and fmx[-1] < fmx[0]
     s.close()
