@@ -344,7 +344,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     s.yz = cv.take<double>(s.piv_elems);
     s.pub = cv.take<unsigned long long>(s.piv_elems);
     s.pflag = fp32 ? nullptr : cv.take<unsigned>(s.piv_elems);
-    s.fflag = cv.take<unsigned>(s.piv_elems);
+    s.fflag = cv.take<unsigned>(2 * s.piv_elems);  // panel-factored, then panel-rows-ready flags
     s.ctl = cv.take<unsigned>(16);
     {
       SolveItem *it;
@@ -573,7 +573,7 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
     if (!st->enabled) continue;
     CUDA_TRY(h, cudaMemsetAsync(st->pub, 0, (size_t)st->piv_elems * sizeof(unsigned long long), h->stream));
     if (st->pflag) CUDA_TRY(h, cudaMemsetAsync(st->pflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(st->fflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(st->fflag, 0, 2 * (size_t)st->piv_elems * sizeof(unsigned), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(st->ctl, 0, 16 * sizeof(unsigned), h->stream));
   }
   // uploads read host vectors owned by h->S or by the carve's thread-local

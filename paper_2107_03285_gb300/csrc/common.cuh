@@ -102,8 +102,11 @@ struct Store {
   std::vector<int64_t> h_fwd_lvl, h_bwd_lvl;  // per level: range in the item lists
   bool sched_ok = true;  // every item listed after the items it waits on
   // panel kernel of each (level, outer block): its bands, every front's
-  // bands 0 and 1 (the panels' owners) first; fflag: one flag per panel,
-  // set to the factorization's epoch (ctl[4]) once the panel is factored
+  // bands 0 and 1 (the panels' owners) first; fflag: two flags per pivot
+  // position (used at each panel's first pivot), set to the factorization's
+  // epoch (ctl[4]): [0, piv_elems) once the panel is factored, [piv_elems,
+  // 2 piv_elems) once the panel's rows are final in the outer block's
+  // earlier columns
   const BandItem *blk_items = nullptr;
   std::vector<BandItem> h_blk_items;
   std::vector<int64_t> h_blk_off;
