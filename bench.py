@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", default="kuhn3d_12", help="oracle sample workload")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle baseline time (0: skip it)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--batch-workload", default="batch2d_256",
                     help="batched form: many uneven 2D instances in one graph-captured step ('' skips)")
@@ -614,13 +614,15 @@ def main():
     ph = torch.empty(tuple(p.shape), dtype=torch.float64, pin_memory=True)
     ph.copy_(p)
     xnp, pnp = xh.numpy(), ph.numpy()
-    s.step_host(xnp, pnp, prec)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None  # --e2e-steps 0: not measured
+    if args.e2e_steps > 0:
         s.step_host(xnp, pnp, prec)
-    e2e_dt = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
-    e2e = {"value": ws / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(xnp.nbytes + pnp.nbytes),
-           "d2h_bytes_per_step": int(2 * xnp.nbytes + pnp.nbytes)}
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.step_host(xnp, pnp, prec)
+        e2e_dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": ws / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(xnp.nbytes + pnp.nbytes),
+               "d2h_bytes_per_step": int(2 * xnp.nbytes + pnp.nbytes)}
 
     sharded = None
     if ws > 1 and args.batch_workload:
@@ -685,12 +687,12 @@ def main():
                    "peak_source": hbm_src,
                    "bytes": "solves x 2 nnz(L) x (4 FP32 | 8 FP64); the phase also holds the FP64 residuals"},
     }
-    if ws == 1:
+    if ws == 1 and args.cpu_seconds > 0:
         cpu_rate, cpu_info = oracle_step_rate(args.cpu_sample, args.cpu_seconds, args.seed)
         cpu_info["value"] = cpu_rate
         cpu_info["unit"] = UNIT
     else:
-        cpu_info = None  # the oracle baseline is timed at N = 1 only
+        cpu_info = None  # the oracle baseline is timed at N = 1 only (--cpu-seconds 0: not at all)
     N = int(info.n_kkt)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

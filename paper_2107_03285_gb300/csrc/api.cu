@@ -201,6 +201,8 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   // owners of the block's panels (bands 0 and 1 of every front) come first
   s.h_blk_items.clear();
   s.h_blk_off.assign(1, 0);
+  s.h_upd_cum.clear();
+  s.h_upd_off.clear();
   for (const auto &lv : c.S.level_fronts) {
     int64_t max_ns = 0;
     for (int i : lv) max_ns = std::max<int64_t>(max_ns, (int64_t)c.S.sn[i].nown * dpn);
@@ -219,6 +221,24 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
         if (!any) break;
       }
       s.h_blk_off.push_back((int64_t)s.h_blk_items.size());
+      // the trailing update's tiles per active front (fronts sorted by ns,
+      // largest first, so the active ones come first), for each window
+      const int next_w = FACTOR_BLOCK / 128;
+      for (int wdw = 0; wdw < 3; ++wdw) {
+        const int win0 = wdw == 1 ? next_w : 0, win1 = wdw == 0 ? next_w : -1;
+        s.h_upd_off.push_back((int64_t)s.h_upd_cum.size());
+        int32_t acc = 0;
+        s.h_upd_cum.push_back(0);
+        for (int i : lv) {
+          const int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
+          if (ns <= K0) break;
+          const int64_t kend = std::min<int64_t>(K0 + FACTOR_BLOCK, ns);
+          const int nt = (int)((f - kend + 127) / 128);
+          const int m = std::min(win1 < 0 ? nt : win1, nt) - win0, n = nt - win0;
+          if (m > 0) acc += m * (m + 1) / 2 + (n - m) * m;
+          s.h_upd_cum.push_back(acc);
+        }
+      }
     }
   }
   // self-check (the substitutions' waits rely on it): an item of key k waits
@@ -352,6 +372,8 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
       st_up(it, s.h_bwd_items); s.bwd_items = it;
       BandItem *bi;
       st_up(bi, s.h_blk_items); s.blk_items = bi;
+      int32_t *uc;
+      st_up(uc, s.h_upd_cum); s.upd_cum = uc;
     }
     if (fp32) {
       for (int q = 0; q < 8; ++q) s.wk[q] = cv.take<float>(s.w_elems);

@@ -110,6 +110,13 @@ struct Store {
   const BandItem *blk_items = nullptr;
   std::vector<BandItem> h_blk_items;
   std::vector<int64_t> h_blk_off;
+  // tensor-core trailing update of each (level, outer block) b and tile
+  // window w (0: the next block's FACTOR_BLOCK / 128 tile columns, 1: the
+  // rest, 2: all): h_upd_off[3 b + w] = offset of its cumulative per-front
+  // tile counts (active fronts + 1 entries) in upd_cum / h_upd_cum
+  const int32_t *upd_cum = nullptr;
+  std::vector<int32_t> h_upd_cum;
+  std::vector<int64_t> h_upd_off;
   unsigned *fflag = nullptr;
   const int64_t *front_off = nullptr, *cb_off = nullptr, *w_off = nullptr, *rhs_off = nullptr, *piv_off = nullptr;
   const int64_t *xinv_off = nullptr;

@@ -295,37 +295,61 @@ __global__ void __launch_bounds__(256) k_update(DevSym d, SV sv, const int32_t *
                    Fm.L + (int64_t)(kend + cc) + (int64_t)K0 * f, f, min(64, nrows - cc), kw, r - cc);
 }
 
-// persistent tensor-core trailing update: CTA x of front y walks tiles
-// x, x + gridDim.x, ... of the window of tile columns [win0, win1) (win1 < 0:
-// to the end) of that front's lower triangle
+// The tiles of one trailing-update launch: every active front's window of
+// tile columns [win0, win1) (win1 < 0: to the end) of its lower triangle, in
+// one list ordered by front; cum[q] = tiles of the fronts before front q of
+// the level (cum[na] = all), so CTAs take equal shares of the list however
+// unevenly the tiles fall on fronts.
+struct UpdateTiles {
+  DevSym d;
+  SV sv;
+  const int32_t *fronts;
+  const tc::Maps *maps;
+  const int32_t *cum;
+  int na, K0, NB, win0, win1;
+  // list index g -> its front's job and tensor maps, and the tile's index in
+  // the front's window
+  __device__ __forceinline__ void get(int g, tc::TileJob &job, const tc::Maps *&mp, int &t) const {
+    int lo = 0, hi = na;  // the front holding g: the last q with cum[q] <= g
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(cum + mid) <= g) lo = mid;
+      else hi = mid;
+    }
+    t = g - __ldg(cum + lo);
+    const int s = __ldg(fronts + lo);
+    const int dpn = sv.dpn;
+    const int ns = d.sn_nown[s] * dpn;
+    const int f = front_order(d, s, dpn);
+    const int kend = min(K0 + NB, ns);
+    const int nrows = f - kend;
+    const int nt = (nrows + tc::TILE - 1) / tc::TILE;
+    job.win0 = win0;
+    job.m = min(win1 < 0 ? nt : win1, nt) - win0;
+    const int n = nt - win0;  // tile rows of the window
+    job.ntiles = job.m * (job.m + 1) / 2 + (n - job.m) * job.m;
+    job.L = (float *)sv.F + sv.front_off[s];
+    job.CB = (float *)sv.CB + sv.cb_off[s];
+    job.f = f;
+    job.ns = ns;
+    job.nrows = nrows;
+    job.kend = kend;
+    job.kchunks = (kend - K0 + 31) / 32;
+    mp = maps + s;
+  }
+};
+
+// persistent tensor-core trailing update: CTA x walks tiles x, x + gridDim.x,
+// ... of the launch's list (UpdateTiles)
 __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                                  int K0, int NB, const tc::Maps *__restrict__ maps,
-                                                                 int win0, int win1, int *status) {
-  const int s = fronts[blockIdx.y];
-  const int dpn = sv.dpn;
-  const int ns = d.sn_nown[s] * dpn;
-  if (K0 >= ns) return;
-  const int f = front_order(d, s, dpn);
-  const int kend = min(K0 + NB, ns);
-  const int nrows = f - kend;
-  const int nt = (nrows + tc::TILE - 1) / tc::TILE;
-  tc::TileJob job;
-  job.win0 = win0;
-  job.m = min(win1 < 0 ? nt : win1, nt) - win0;
-  if (job.m <= 0) return;
-  const int n = nt - win0;  // tile rows of the window
-  job.ntiles = job.m * (job.m + 1) / 2 + (n - job.m) * job.m;
-  if ((int)blockIdx.x >= job.ntiles) return;
-  job.L = (float *)sv.F + sv.front_off[s];
-  job.CB = (float *)sv.CB + sv.cb_off[s];
-  job.f = f;
-  job.ns = ns;
-  job.nrows = nrows;
-  job.kend = kend;
-  job.kchunks = (kend - K0 + 31) / 32;
-  tc::tile_loop_tc(&maps[s], job, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
+                                                                 int win0, int win1, const int32_t *__restrict__ cum,
+                                                                 int na, int *status) {
+  const int total = cum[na];
+  if ((int)blockIdx.x >= total) return;
+  const UpdateTiles src{d, sv, fronts, maps, cum, na, K0, NB, win0, win1};
+  tc::tile_loop_tc(src, total, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
 }
-
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
                                const double *__restrict__ D1, unsigned long long *counters) {
@@ -408,6 +432,7 @@ void factor_impl(Ctx &c, Store &st) {
     for (int K0 = 0; K0 < max_ns; K0 += FACTOR_BLOCK) {
       const int kstop = std::min(K0 + FACTOR_BLOCK, max_ns);
       const int parity = (K0 / FACTOR_BLOCK) & 1;  // which operand set this block writes
+      const int64_t bidx = blk;                     // this (level, outer block)
       const SV sv = view(st, parity);
       {
         // every panel of the block in one launch (one CTA per 128-row band)
@@ -466,25 +491,31 @@ void factor_impl(Ctx &c, Store &st) {
           return fl;
         };
         if (std::is_same<T, float>::value && st.tc) {
-          // one CTA per SM (192 KB shared memory); spread the SMs over the
-          // active fronts and let every CTA loop over its front's tiles.  The
-          // tile columns holding the next outer block's columns go first on
-          // this stream; the rest runs on the side stream, next to the next
-          // block's panels (which write the other operand set), on fewer SMs
-          // so that those panels find room
+          // one CTA per SM (192 KB shared memory), each taking an equal share
+          // of one list of the tiles of every active front.  The tile columns
+          // holding the next outer block's columns go first on this stream;
+          // the rest runs on the side stream, next to the next block's panels
+          // (which write the other operand set), on fewer SMs so that those
+          // panels find room
           const int nt128 = (max_rows + tc::TILE - 1) / tc::TILE;
           const int ctas = c.update_ctas > 0 ? c.update_ctas : c.num_sms;
           const int next_w = FACTOR_BLOCK / tc::TILE;
           const tc::Maps *maps = (const tc::Maps *)st.maps + (size_t)parity * c.S.sn.size();
           if (side_pending) cudaStreamWaitEvent(c.stream, c.ev_join, 0);  // the previous block's rest
           const bool split = nt128 > next_w && c.side_stream && K0 + FACTOR_BLOCK < max_ns;
+          // the tile list of window w: its cumulative counts and its length
+          auto tiles_of = [&](int wdw, const int32_t *&cum) {
+            const int64_t off = st.h_upd_off[3 * bidx + wdw];
+            cum = st.upd_cum + off;
+            return (int)st.h_upd_cum[off + na];
+          };
           {
-            const int m = std::min(next_w, nt128);
-            const int tiles = m * (m + 1) / 2 + (nt128 - m) * m;
-            int g = std::max(1, std::min(split ? tiles : nt128 * (nt128 + 1) / 2, (ctas + na - 1) / na));
+            const int32_t *cum;
+            const int tiles = tiles_of(split ? 0 : 2, cum);
+            const int g = std::max(1, std::min(tiles, ctas));
             ProfScope ps(c, SGN_PROF_UPDATE, split ? flops_cols(0, next_w) : flops_cols(0, -1));
-            k_update_tcp<<<dim3(g, na), tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, c.status);
+            k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, cum, na, c.status);
             c.tc_launches++;
             c.count();
           }
@@ -494,13 +525,13 @@ void factor_impl(Ctx &c, Store &st) {
             c.stream = c.side_stream;
             cudaStreamWaitEvent(c.stream, c.ev_fork, 0);
             {
-              const int m = nt128 - next_w;
-              const int tiles = m * (m + 1) / 2;
+              const int32_t *cum;
+              const int tiles = tiles_of(1, cum);
               const int rest = std::max(1, ctas - std::min(ctas / 4, PANEL_RESERVE_SMS));
-              int g = std::max(1, std::min(tiles, (rest + na - 1) / na));
+              const int g = std::max(1, std::min(tiles, rest));
               ProfScope ps(c, SGN_PROF_UPDATE, flops_cols(next_w, -1));
-              k_update_tcp<<<dim3(g, na), tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, c.status);
+              k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, cum, na, c.status);
               c.tc_launches++;
               c.count();
             }

@@ -126,9 +126,13 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised trailing update: each CTA walks a list of tiles
-// of one front; two TMEM accumulators (2 x 128 columns) let the epilogue of tile i
-// run while the producer and MMA warps already work on tile i + 1.
+// Persistent, warp-specialised trailing update: each CTA walks its share of
+// one flat list of tiles over every front of a level (tiles first, first +
+// stride, ...); two TMEM accumulators (2 x 128 columns) let the epilogue of
+// tile i run while the producer and MMA warps already work on tile i + 1.
+// The tile source maps a list index to its front's job, tensor maps and the
+// tile's index in that front's window (Src::get); every role walks the same
+// sequence.
 //   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
 //   warps 2..9    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31,
 //                   columns 64 ((w - 2) / 4) .. + 63 of the tile)
@@ -171,8 +175,9 @@ __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
   bj = tile - bi * (bi + 1) / 2;
 }
 
-__device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job, int first, int stride,
-                                             int *status, int flag_timeout) {
+template <typename Src>
+__device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int first, int stride, int *status,
+                                             int flag_timeout) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   __shared__ uint64_t full_bar[PSTAGES], empty_bar[PSTAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
@@ -180,7 +185,7 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int my_tiles = first < job.ntiles ? (job.ntiles - first + stride - 1) / stride : 0;
+  const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < PSTAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], EPI_WARPS); }
@@ -197,21 +202,28 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int kch = job.kchunks;
 
   if (warp == 0) {
-    if (lane == 0 && my_tiles > 0 && kch > 0) {
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->whi) : "memory");
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->wlo) : "memory");
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->lhi) : "memory");
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->llo) : "memory");
+    if (lane == 0 && my_tiles > 0) {
+      const Maps *cur = nullptr;
       int g = 0;  // global chunk counter over all of this CTA's tiles
       bool stop = false;
       for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+        TileJob job;
+        const Maps *maps;
+        int t;
+        src.get(first + lt * stride, job, maps, t);
+        if (maps != cur) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->whi) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->wlo) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->lhi) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->llo) : "memory");
+          cur = maps;
+        }
         int bi, bj;
-        window_tile(job, first + lt * stride, bi, bj);
+        window_tile(job, t, bi, bj);
         const int rw = job.kend + bi * TILE, rl = job.kend + bj * TILE;
-        for (int kc = 0; kc < kch; ++kc, ++g) {
+        for (int kc = 0; kc < job.kchunks; ++kc, ++g) {
           const int s = g % PSTAGES;
           if (g >= PSTAGES && !mbar_wait(&empty_bar[s], ((g / PSTAGES) - 1) & 1, status, flag_timeout)) {
             abort_flag = 1; stop = true; break;
@@ -230,11 +242,16 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
         mbar_wait(&full_bar[q % PSTAGES], (q / PSTAGES) & 1, status, flag_timeout);
     }
   } else if (warp == 1) {
-    if (lane == 0 && my_tiles > 0 && kch > 0) {
+    if (lane == 0 && my_tiles > 0) {
       const uint32_t idesc = idesc_tf32_128x128();
       int g = 0;
       bool stop = false;
       for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+        TileJob job;
+        const Maps *maps;
+        int t;
+        src.get(first + lt * stride, job, maps, t);
+        const int kch = job.kchunks;
         const int b = lt & 1;
         if (lt >= 2 && !mbar_wait(&acc_empty[b], ((lt >> 1) - 1) & 1, status, flag_timeout)) {
           abort_flag = 1; break;
@@ -274,15 +291,19 @@ __device__ __forceinline__ void tile_loop_tc(const Maps *maps, const TileJob job
     const int quad = warp & 3;
     const int col0 = ((warp - 2) / 4) * (TILE / 2);
     const int r = quad * 32 + lane;
-    for (int lt = 0; lt < my_tiles && kch > 0; ++lt) {
+    for (int lt = 0; lt < my_tiles; ++lt) {
       const int b = lt & 1;
       bool ok = mbar_wait(&acc_full[b], (lt >> 1) & 1, status, flag_timeout);
       // tcgen05.ld is warp-collective: the whole warp takes the same branch
       ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
+      TileJob job;
+      const Maps *maps;
+      int t;
+      src.get(first + lt * stride, job, maps, t);
       int bi, bj;
-      window_tile(job, first + lt * stride, bi, bj);
+      window_tile(job, t, bi, bj);
       const int rows = min(TILE, job.nrows - bi * TILE), cols = min(TILE, job.nrows - bj * TILE);
       const int roff = (bi - bj) * TILE;
       // element (gi, gj) of the front: factor column (gj < ns) or
