@@ -286,12 +286,16 @@ __device__ __forceinline__ void bk_factor_regs(CT (&r)[NBT], CT (*a)[NBT + 1], c
 // right-looking, band_rows_solve), factored by the calling warp alone; lane
 // c writes column c of stage (L11 with D on its diagonal, zeros above) and
 // the pivot arrays, and lane 0 publishes the panel (fflag = epoch) once
-// every lane's writes are ordered before it
+// every lane's writes are ordered before it.  The same values go to the
+// band's own solve buffers (Ls: L11 transposed, pD0 / pD1 / pperm / ptype /
+// pI0 / pI1, as band_rows_solve would load them), so that the band that
+// factored the panel solves its rows without a round trip to memory.
 template <typename T, int NBT>
 __device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int k, int w, int nb, double eps_rel,
                                                  unsigned long long *counters, T (*a)[NBT + 1], T *sD0, T *sD1,
                                                  int *sperm, int *stype, T *su, T *svv, unsigned *flag,
-                                                 unsigned epoch) {
+                                                 unsigned epoch, T *Ls, T *pD0, T *pD1, T *pI0, T *pI1, int *pperm,
+                                                 int *ptype) {
   const int lane = threadIdx.x & 31;
   const T *F = (const T *)sv.F + sv.front_off[s];
   T r[NBT];
@@ -321,6 +325,19 @@ __device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int
   // instruction covers one row of the block: L(ii, c) from the unscaled W
   // columns in a and the pivot's inverse (i0, i1), D on the diagonal
   T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
+  if (lane < NBT) {
+    const bool in = lane < w;
+    pD0[lane] = in ? sD0[lane] : T(1);
+    pD1[lane] = in ? sD1[lane] : T(0);
+    pperm[lane] = in ? sperm[lane] : lane;
+    ptype[lane] = in ? stype[lane] : 0;
+    pI0[lane] = i0;
+    pI1[lane] = i1;
+    if (!in) {
+#pragma unroll 4
+      for (int ii = 0; ii < NBT; ++ii) Ls[lane * NBT + ii] = T(0);
+    }
+  }
   if (lane < w) {
     const int ty = stype[lane];
     const int cp = ty == 1 ? lane + 1 : (ty == 2 ? lane - 1 : lane);  // the pair's other column
@@ -335,7 +352,9 @@ __device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int
         val = ty == 0 ? wc * i0 : wc * i0 + wo * i1;
       }
       stage[(int64_t)ii * nb + lane] = val;
+      Ls[lane * NBT + ii] = ii > lane ? val : T(0);
     }
+    for (int ii = w; ii < NBT; ++ii) Ls[lane * NBT + ii] = T(0);
     const int64_t po = sv.piv_off[s] + k;
     sv.piv_type[po + lane] = ty;
     sv.piv_perm[po + lane] = sperm[lane];
@@ -430,7 +449,7 @@ __device__ __forceinline__ void band_rows_left(const SV &sv, int s, int f, int K
 template <typename T, int NBT>
 __device__ __forceinline__ void band_rows_solve(const SV &sv, int s, int f, int ns, int K0, int k, int w, int nb,
                                                 int rb0, int rb1, T *L11T, T *xs, T *xw, T *sD0, T *sD1, T *sI0,
-                                                T *sI1, int *sperm, int *stype) {
+                                                T *sI1, int *sperm, int *stype, bool own) {
   using CT = T;
   constexpr int XS = PANEL_XS;
   T *F = (T *)sv.F + sv.front_off[s];
@@ -440,7 +459,7 @@ __device__ __forceinline__ void band_rows_solve(const SV &sv, int s, int f, int 
   const int64_t i = (int64_t)rb0 + tid;
   const bool row_ok = i >= k + w && i < rb1;
   const T *stage = (const T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
-  {
+  if (!own) {  // a band that factored the panel has L11 and the pivots here already
     constexpr int PER = (NBT * NBT + 127) / 128;
     CT lt[PER];
 #pragma unroll
@@ -460,26 +479,26 @@ __device__ __forceinline__ void band_rows_solve(const SV &sv, int s, int f, int 
 #pragma unroll
     for (int q = 0; q < PER; ++q)
       if (tid + q * 128 < NBT * NBT) L11T[tid + q * 128] = lt[q];
-  }
-  __syncthreads();
-  // D^{-1} per pivot: 1 / d for 1x1, the inverse of the 2x2 block for pairs
-  // (entry (0,0) in sI0 of the first, (1,1) in sI0 of the second, (0,1) in sI1)
-  if (tid < NBT) {
-    const int t = tid;
-    CT i0 = CT(1), i1 = CT(0);
-    if (stype[t] == 0) {
-      i0 = CT(1) / sD0[t];
-    } else {
-      const int a = stype[t] == 1 ? t : t - 1;
-      const CT d11 = sD0[a], d21 = sD1[a], d22 = sD0[a + 1];
-      const CT det = d11 * d22 - d21 * d21;
-      i0 = (stype[t] == 1 ? d22 : d11) / det;
-      i1 = -d21 / det;
+    __syncthreads();
+    // D^{-1} per pivot: 1 / d for 1x1, the inverse of the 2x2 block for pairs
+    // (entry (0,0) in sI0 of the first, (1,1) in sI0 of the second, (0,1) in sI1)
+    if (tid < NBT) {
+      const int t = tid;
+      CT i0 = CT(1), i1 = CT(0);
+      if (stype[t] == 0) {
+        i0 = CT(1) / sD0[t];
+      } else {
+        const int a = stype[t] == 1 ? t : t - 1;
+        const CT d11 = sD0[a], d21 = sD1[a], d22 = sD0[a + 1];
+        const CT det = d11 * d22 - d21 * d21;
+        i0 = (stype[t] == 1 ? d22 : d11) / det;
+        i1 = -d21 / det;
+      }
+      sI0[t] = i0;
+      sI1[t] = i1;
     }
-    sI0[t] = i0;
-    sI1[t] = i1;
+    __syncthreads();
   }
-  __syncthreads();
   // permutation and forward substitution, x in registers
   CT x[NBT];
 #pragma unroll
@@ -662,20 +681,22 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
           __syncthreads();
           if (s_abort) break;
           band_rows_solve<T, NBT>(sv, s, f, ns, K0, k, w, nb, rb0, rb1, L11T, xs, xw, sD0, sD1, sI0, sI1, sperm,
-                                  stype);
+                                  stype, owner);
         }
       }
       // the next panel's diagonal block lies in this band's rows when this
       // band owns that panel
+      // (warp 1 publishes that its rows are final in the earlier columns,
+      // so that warp 0 starts at once)
       const int kn = k + w;
-      if (warp == 0 && kn < kend && (kn - K0) / BAND == it.band) {
-        if (lane == 0 && kn > K0) {
-          __threadfence();
-          st_release_flag(pre + kn, epoch);
-        }
-        owner_panel_warp<T, NBT>(sv, s, f, kn, min(nb, ns - kn), nb, eps_rel, counters, a, bD0, bD1, bperm, btype,
-                                 bU, bV, flag, epoch);
+      const bool next_owner = kn < kend && (kn - K0) / BAND == it.band;
+      if (next_owner && warp == 1 && lane == 0 && kn > K0) {
+        __threadfence();
+        st_release_flag(pre + kn, epoch);
       }
+      if (next_owner && warp == 0)
+        owner_panel_warp<T, NBT>(sv, s, f, kn, min(nb, ns - kn), nb, eps_rel, counters, a, bD0, bD1, bperm, btype,
+                                 bU, bV, flag, epoch, L11T, sD0, sD1, sI0, sI1, sperm, stype);
       if (rows && sv.wk0) band_row_copies<T>(sv, s, ns, K0, k, w, rb0, rb1, xs, xw);
     }
   }
