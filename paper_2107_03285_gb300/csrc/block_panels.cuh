@@ -240,11 +240,13 @@ __device__ __forceinline__ void bk_factor_regs(CT (&r)[NBT], CT (*a)[NBT + 1], c
       __syncwarp();
       CT m[NBT];
       ld_bcast<CT, NBT>(su, m);
+      // rows <= j and columns <= j have l = 0 / m = 0, so they stay as they
+      // are; entries above the diagonal (c > lane) change but are never read
 #pragma unroll
       for (int c = 0; c < NBT; ++c)
-        if (c > j && c <= lane && lane < w) {
+        if (c > j) {
           r[c] -= l * m[c];
-          a[c][lane] = r[c];
+          a[c][row] = r[c];
         }
     } else {
       const CT d11 = a[j][j], d21 = a[j][j + 1], d22 = a[j + 1][j + 1];
@@ -265,11 +267,13 @@ __device__ __forceinline__ void bk_factor_regs(CT (&r)[NBT], CT (*a)[NBT + 1], c
       CT mu[NBT], mv[NBT];
       ld_bcast<CT, NBT>(su, mu);
       ld_bcast<CT, NBT>(sv, mv);
+      // as for a 1x1 pivot: rows <= j + 1 have p = q = 0, columns <= j + 1
+      // have u = v = 0, entries above the diagonal are never read
 #pragma unroll
       for (int c = 0; c < NBT; ++c)
-        if (c > j + 1 && c <= lane && lane < w) {
+        if (c > j + 1) {
           r[c] -= p * mu[c] + q * mv[c];
-          a[c][lane] = r[c];
+          a[c][row] = r[c];
         }
     }
     __syncwarp();

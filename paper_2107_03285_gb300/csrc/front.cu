@@ -340,7 +340,7 @@ struct UpdateTiles {
 };
 
 // persistent tensor-core trailing update: CTA x walks tiles x, x + gridDim.x,
-// ... of the launch's list (UpdateTiles)
+// ... of the launch's list (UpdateTiles).
 __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                                  int K0, int NB, const tc::Maps *__restrict__ maps,
                                                                  int win0, int win1, const int32_t *__restrict__ cum,

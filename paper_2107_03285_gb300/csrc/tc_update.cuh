@@ -122,6 +122,16 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // the hi / lo split used for the 3xTF32 products
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
@@ -293,11 +303,10 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
     const int r = quad * 32 + lane;
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int b = lt & 1;
-      bool ok = mbar_wait(&acc_full[b], (lt >> 1) & 1, status, flag_timeout);
-      // tcgen05.ld is warp-collective: the whole warp takes the same branch
-      ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (!ok) break;
+      // the tile and its C entries do not depend on the accumulator: the
+      // warp's 64 columns go in four 16-column chunks, the first two loaded
+      // before the wait and each later one while an earlier one is written,
+      // so that the loads' latency overlaps the MMAs
       TileJob job;
       const Maps *maps;
       int t;
@@ -310,42 +319,63 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
       // contribution block (gj >= ns, then gi >= gj >= ns)
       const int64_t gi = (int64_t)job.kend + bi * TILE + r, gj0 = (int64_t)job.kend + bj * TILE;
       const int64_t fcb = job.f - job.ns;
-#pragma unroll 1
-      for (int cb = col0; cb < col0 + TILE / 2; cb += 32) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + cb), v);
-        if (r < rows) {
-          const int64_t gjc = gj0 + cb;
-          if (gjc + 31 < job.ns || gjc >= job.ns) {
-            // the 32 columns lie in one region: one base pointer, one stride
-            const bool in_l = gjc < job.ns;
-            float *__restrict__ base = in_l ? job.L + gi + gjc * job.f : job.CB + (gi - job.ns) + (gjc - job.ns) * fcb;
-            const int64_t stride = in_l ? job.f : fcb;
-            float cv[32];
+      auto elem = [&](int cc) -> float * {
+        const int64_t gj = gj0 + cc;
+        return gj < job.ns ? job.L + gi + gj * job.f : job.CB + (gi - job.ns) + (gj - job.ns) * fcb;
+      };
+      // the 16 entries of chunk cb of this thread's row: in one region (one
+      // base pointer, one stride), or, for a chunk that straddles the last
+      // factor column ns, element by element
+      auto load_chunk = [&](int cb, float (&cv)[16]) {
+        if (r >= rows) return;
+        const int64_t gjc = gj0 + cb;
+        if (gjc + 15 < job.ns || gjc >= job.ns) {
+          const bool in_l = gjc < job.ns;
+          const float *__restrict__ base = in_l ? job.L + gi + gjc * job.f : job.CB + (gi - job.ns) + (gjc - job.ns) * fcb;
+          const int64_t st = in_l ? job.f : fcb;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int cc = cb + j;
-              cv[j] = (cc < cols && r + roff >= cc) ? __ldcg(base + j * stride) : 0.f;
-            }
+          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcg(base + j * st) : 0.f;
+        } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int cc = cb + j;
-              if (cc < cols && r + roff >= cc) __stcg(base + j * stride, cv[j] - __uint_as_float(v[j]));
-            }
-          } else {
-            // the chunk straddles the last factor column ns (one chunk per tile row)
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int cc = cb + j;
-              const int64_t gj = gjc + j;
-              if (cc < cols && r + roff >= cc) {
-                float *p = gj < job.ns ? job.L + gi + gj * job.f : job.CB + (gi - job.ns) + (gj - job.ns) * fcb;
-                __stcg(p, __ldcg(p) - __uint_as_float(v[j]));
-              }
-            }
-          }
+          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcg(elem(cb + j)) : 0.f;
         }
-      }
+      };
+      auto store_chunk = [&](int cb, const float (&cv)[16], const uint32_t (&v)[16]) {
+        if (r >= rows) return;
+        const int64_t gjc = gj0 + cb;
+        if (gjc + 15 < job.ns || gjc >= job.ns) {
+          const bool in_l = gjc < job.ns;
+          float *__restrict__ base = in_l ? job.L + gi + gjc * job.f : job.CB + (gi - job.ns) + (gjc - job.ns) * fcb;
+          const int64_t st = in_l ? job.f : fcb;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < cols && r + roff >= cb + j) __stcg(base + j * st, cv[j] - __uint_as_float(v[j]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < cols && r + roff >= cb + j) __stcg(elem(cb + j), cv[j] - __uint_as_float(v[j]));
+        }
+      };
+      float ca[16], cb2[16];
+      load_chunk(col0, ca);
+      load_chunk(col0 + 16, cb2);
+      bool ok = mbar_wait(&acc_full[b], (lt >> 1) & 1, status, flag_timeout);
+      // tcgen05.ld is warp-collective: the whole warp takes the same branch
+      ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) break;
+      uint32_t v[16];
+      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + col0);
+      tmem_ld_32x32b_x16(trow, v);
+      store_chunk(col0, ca, v);
+      load_chunk(col0 + 32, ca);
+      tmem_ld_32x32b_x16(trow + 16u, v);
+      store_chunk(col0 + 16, cb2, v);
+      load_chunk(col0 + 48, cb2);
+      tmem_ld_32x32b_x16(trow + 32u, v);
+      store_chunk(col0 + 32, ca, v);
+      tmem_ld_32x32b_x16(trow + 48u, v);
+      store_chunk(col0 + 48, cb2, v);
       // this warp's TMEM reads of buffer b are complete (tcgen05.wait::ld)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
