@@ -71,18 +71,22 @@ __device__ __forceinline__ bool wait_epoch(const unsigned *p, unsigned epoch, in
 // it, and only a near tie runs the FP64 arithmetic (the FP64 pipe of this
 // part issues a warp instruction every ~64 cycles).
 constexpr double BK_ALPHA = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+// the FP64 evaluations of near ties, out of line so that the common FP32
+// decision does not issue (predicated) FP64 instructions
+__device__ __noinline__ bool ge_alpha_fp64(double a, double c) { return a >= BK_ALPHA * c; }
+__device__ __noinline__ bool ge_alpha_sq_fp64(double a, double r, double c) { return a * r >= BK_ALPHA * (c * c); }
 __device__ __forceinline__ bool ge_alpha(float a, float c) {
   const float r = 0.64038820f * c;
   const float g = a - r;
   if (fabsf(g) > 0x1p-20f * fmaxf(a, r)) return g > 0.f;
-  return (double)a >= BK_ALPHA * (double)c;
+  return ge_alpha_fp64((double)a, (double)c);
 }
 __device__ __forceinline__ bool ge_alpha(double a, double c) { return a >= BK_ALPHA * c; }
 __device__ __forceinline__ bool ge_alpha_sq(float a, float r, float c) {
   const float lhs = a * r, rhs = (0.64038820f * c) * c;
   const float g = lhs - rhs;
   if (fabsf(g) > 0x1p-20f * fmaxf(lhs, rhs)) return g > 0.f;
-  return (double)a * (double)r >= BK_ALPHA * ((double)c * (double)c);
+  return ge_alpha_sq_fp64((double)a, (double)r, (double)c);
 }
 __device__ __forceinline__ bool ge_alpha_sq(double a, double r, double c) { return a * r >= BK_ALPHA * (c * c); }
 
@@ -287,25 +291,30 @@ __device__ __forceinline__ void bk_factor_regs(CT (&r)[NBT], CT (*a)[NBT + 1], c
 
 // the panel's diagonal block [k, k + w), already updated by every earlier
 // panel of the outer block (the band holding it applied those updates
-// right-looking, band_rows_solve), factored by the calling warp alone; lane
-// c writes column c of stage (L11 with D on its diagonal, zeros above) and
-// the pivot arrays, and lane 0 publishes the panel (fflag = epoch) once
-// every lane's writes are ordered before it.  The same values go to the
-// band's own solve buffers (Ls: L11 transposed, pD0 / pD1 / pperm / ptype /
-// pI0 / pI1, as band_rows_solve would load them), so that the band that
-// factored the panel solves its rows without a round trip to memory.
+// right-looking, band_rows_solve), factored by the calling warp alone.  The
+// block comes from the front, or (from_smem) from a, where the band's last
+// diagonal-block update left it.  The results go to the band's own solve
+// buffers (Ls: L11 transposed, pD0 / pD1 / pperm / ptype / pI0 / pI1, as
+// band_rows_solve would load them), so that the band that factored the panel
+// solves its rows without a round trip to memory; publish_panel_warp writes
+// them out for the other bands.
 template <typename T, int NBT>
-__device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int k, int w, int nb, double eps_rel,
-                                                 unsigned long long *counters, T (*a)[NBT + 1], T *sD0, T *sD1,
-                                                 int *sperm, int *stype, T *su, T *svv, unsigned *flag,
-                                                 unsigned epoch, T *Ls, T *pD0, T *pD1, T *pI0, T *pI1, int *pperm,
-                                                 int *ptype) {
+__device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int k, int w, double eps_rel,
+                                                 unsigned long long *counters, T (*a)[NBT + 1], bool from_smem,
+                                                 T *sD0, T *sD1, int *sperm, int *stype, T *su, T *svv, T *Ls,
+                                                 T *pD0, T *pD1, T *pI0, T *pI1, int *pperm, int *ptype) {
   const int lane = threadIdx.x & 31;
   const T *F = (const T *)sv.F + sv.front_off[s];
   T r[NBT];
+  if (from_smem) {
 #pragma unroll
-  for (int c = 0; c < NBT; ++c)
-    r[c] = (c <= lane && lane < w) ? __ldcg(F + (int64_t)(k + lane) + (int64_t)(k + c) * f) : T(0);
+    for (int c = 0; c < NBT; ++c) r[c] = (c <= lane && lane < w) ? a[c][lane] : T(0);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NBT; ++c)
+      r[c] = (c <= lane && lane < w) ? __ldcg(F + (int64_t)(k + lane) + (int64_t)(k + c) * f) : T(0);
+  }
+  __syncwarp();
 #pragma unroll
   for (int c = 0; c < NBT; ++c)
     if (lane < NBT) a[c][lane] = r[c];
@@ -325,10 +334,6 @@ __device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int
       i1 = -d21 / det;
     }
   }
-  // lane c writes column c of stage (row-major, nb per row), so every store
-  // instruction covers one row of the block: L(ii, c) from the unscaled W
-  // columns in a and the pivot's inverse (i0, i1), D on the diagonal
-  T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
   if (lane < NBT) {
     const bool in = lane < w;
     pD0[lane] = in ? sD0[lane] : T(1);
@@ -337,33 +342,43 @@ __device__ __forceinline__ void owner_panel_warp(const SV &sv, int s, int f, int
     ptype[lane] = in ? stype[lane] : 0;
     pI0[lane] = i0;
     pI1[lane] = i1;
-    if (!in) {
-#pragma unroll 4
-      for (int ii = 0; ii < NBT; ++ii) Ls[lane * NBT + ii] = T(0);
-    }
-  }
-  if (lane < w) {
-    const int ty = stype[lane];
+    // column lane of L11 (Ls[c NBT + t] = L(t, c), t > c; zeros elsewhere):
+    // from the unscaled W columns in a and the pivot's inverse
+    const int ty = in ? stype[lane] : 0;
     const int cp = ty == 1 ? lane + 1 : (ty == 2 ? lane - 1 : lane);  // the pair's other column
-    const T dl = sD0[lane];
 #pragma unroll 4
-    for (int ii = 0; ii < w; ++ii) {
+    for (int ii = 0; ii < NBT; ++ii) {
       T val = T(0);
-      if (ii == lane) {
-        val = dl;
-      } else if (ii > lane && !(ty == 1 && ii == lane + 1)) {
+      if (in && ii < w && ii > lane && !(ty == 1 && ii == lane + 1)) {
         const T wc = a[lane][ii], wo = a[cp][ii];
         val = ty == 0 ? wc * i0 : wc * i0 + wo * i1;
       }
-      stage[(int64_t)ii * nb + lane] = val;
-      Ls[lane * NBT + ii] = ii > lane ? val : T(0);
+      Ls[lane * NBT + ii] = val;
     }
-    for (int ii = w; ii < NBT; ++ii) Ls[lane * NBT + ii] = T(0);
+  }
+}
+
+// writes the panel [k, k + w) that this band factored to memory for the other
+// bands, from the band's buffers (owner_panel_warp): lane c column c of
+// stage (row-major, nb per row, L11 with D on its diagonal, zeros above; so
+// every store instruction covers one row of the block) and the pivot arrays;
+// lane 0 then publishes the panel (fflag = epoch) once every lane's writes
+// are ordered before it
+template <typename T, int NBT>
+__device__ __forceinline__ void publish_panel_warp(const SV &sv, int s, int k, int w, int nb, const T *Ls,
+                                                   const T *pD0, const T *pD1, const int *pperm, const int *ptype,
+                                                   unsigned *flag, unsigned epoch) {
+  const int lane = threadIdx.x & 31;
+  T *stage = (T *)sv.Ldg + (sv.piv_off[s] + k) * (int64_t)nb;
+  if (lane < w) {
+    const T dl = pD0[lane];
+#pragma unroll 4
+    for (int ii = 0; ii < w; ++ii) stage[(int64_t)ii * nb + lane] = ii == lane ? dl : Ls[lane * NBT + ii];
     const int64_t po = sv.piv_off[s] + k;
-    sv.piv_type[po + lane] = ty;
-    sv.piv_perm[po + lane] = sperm[lane];
+    sv.piv_type[po + lane] = ptype[lane];
+    sv.piv_perm[po + lane] = pperm[lane];
     sv.D0[po + lane] = (double)dl;
-    sv.D1[po + lane] = (double)sD1[lane];
+    sv.D1[po + lane] = (double)pD1[lane];
   }
   __syncwarp();
   if (lane == 0) {
@@ -448,12 +463,13 @@ __device__ __forceinline__ void band_rows_left(const SV &sv, int s, int f, int K
 // and forward substitution with L11 (x = F21 P^T L11^{-T} = L21 D); L21 =
 // x D^{-1}.  Writes L21 to the front and x to the block's W, leaves both in
 // xs / xw for the operand copies (band_row_copies), and applies the panel to
-// the diagonal blocks of the later panels in the band.  Reads of data other
+// the diagonal blocks of the later panels in the band (the next panel's one
+// also to anext, unless null).  Reads of data other
 // CTAs wrote go through L2 (ld.global.cg).
 template <typename T, int NBT>
 __device__ __forceinline__ void band_rows_solve(const SV &sv, int s, int f, int ns, int K0, int k, int w, int nb,
                                                 int rb0, int rb1, T *L11T, T *xs, T *xw, T *sD0, T *sD1, T *sI0,
-                                                T *sI1, int *sperm, int *stype, bool own) {
+                                                T *sI1, int *sperm, int *stype, bool own, T (*anext)[NBT + 1]) {
   using CT = T;
   constexpr int XS = PANEL_XS;
   T *F = (T *)sv.F + sv.front_off[s];
@@ -569,6 +585,11 @@ __device__ __forceinline__ void band_rows_solve(const SV &sv, int s, int f, int 
 #pragma unroll
       for (int q = 0; q < NBT; ++q)
         if (q <= ni) F[i + (int64_t)(pa + q) * f] = T(cur[q]);
+      if (anext && pa == k + w) {  // the next panel's block, for its factorization in this CTA
+#pragma unroll
+        for (int q = 0; q < NBT; ++q)
+          if (q <= ni) anext[q][ni] = T(cur[q]);
+      }
     }
   }
   // every row's right-looking updates are in the front (the next panel's
@@ -623,7 +644,7 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
   T *L11T = Lp + 4 * 32 * NBT;               // [NBT][NBT]
   T *xs = L11T + NBT * NBT;                  // [NBT][PANEL_XS] + 4: L of the band's rows
   T *xw = xs + NBT * PANEL_XS + 4;           // [NBT][PANEL_XS] + 4: W of the band's rows
-  __shared__ T a[NBT][NBT + 1];
+  __shared__ T a[2][NBT][NBT + 1];  // diagonal blocks of alternate panels
   __shared__ T bD0[32], bD1[32];  // the warp's Bunch-Kaufman writes 32 entries
   __shared__ __align__(16) T bU[32], bV[32];
   __shared__ int bperm[32], btype[32];
@@ -658,9 +679,18 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
     // the rows of panel k - w (iteration k - w); it first publishes that the
     // panel's rows are final in the block's earlier columns (pre).  Meanwhile
     // the other warps write those rows' operand copies and go on with the
-    // left-looking phase of panel k, which needs only pre.  Iteration
-    // K0 - nb has no rows and only factors the first panel's block (band 0).
+    // left-looking phase of panel k, which needs only pre.  Warp 0 writes the
+    // factored panel out for the other bands (and sets its fflag) after the
+    // CTA's next barrier, so that the band's own solve of the panel's rows
+    // does not wait for that.  Iteration K0 - nb has no rows and only factors
+    // the first panel's block (band 0).
     const int warp = tid >> 5, lane = tid & 31;
+    int pend = -1;  // warp 0: the panel factored here and not yet published
+    auto publish = [&]() {
+      if (pend >= 0)
+        publish_panel_warp<T, NBT>(sv, s, pend, min(nb, ns - pend), nb, L11T, sD0, sD1, sperm, stype, flag, epoch);
+      pend = -1;
+    };
     for (int k = K0 - nb; k < kend; k += nb) {
       const int w = k < K0 ? nb : min(nb, ns - k);
       bool rows = false;
@@ -683,26 +713,33 @@ __global__ void __launch_bounds__(128) k_block_panels(DevSym d, SV sv, const int
           // own warp 0, which reaches the __syncthreads below only after that
           if (!owner && tid == 0 && !s_abort && !wait_epoch(flag + k, epoch, status)) s_abort = 1;
           __syncthreads();
+          if (warp == 0) publish();
           if (s_abort) break;
+          const int kn = k + w;
+          const bool next_here = kn < kend && (kn - K0) / BAND == it.band;
           band_rows_solve<T, NBT>(sv, s, f, ns, K0, k, w, nb, rb0, rb1, L11T, xs, xw, sD0, sD1, sI0, sI1, sperm,
-                                  stype, owner);
+                                  stype, owner, next_here ? a[((kn - K0) / nb) & 1] : nullptr);
+        } else if (warp == 0) {
+          publish();
         }
       }
       // the next panel's diagonal block lies in this band's rows when this
-      // band owns that panel
-      // (warp 1 publishes that its rows are final in the earlier columns,
-      // so that warp 0 starts at once)
+      // band owns that panel (warp 1 publishes that its rows are final in
+      // the earlier columns, so that warp 0 starts at once)
       const int kn = k + w;
       const bool next_owner = kn < kend && (kn - K0) / BAND == it.band;
       if (next_owner && warp == 1 && lane == 0 && kn > K0) {
         __threadfence();
         st_release_flag(pre + kn, epoch);
       }
-      if (next_owner && warp == 0)
-        owner_panel_warp<T, NBT>(sv, s, f, kn, min(nb, ns - kn), nb, eps_rel, counters, a, bD0, bD1, bperm, btype,
-                                 bU, bV, flag, epoch, L11T, sD0, sD1, sI0, sI1, sperm, stype);
+      if (next_owner && warp == 0) {
+        owner_panel_warp<T, NBT>(sv, s, f, kn, min(nb, ns - kn), eps_rel, counters, a[((kn - K0) / nb) & 1],
+                                 k >= K0, bD0, bD1, bperm, btype, bU, bV, L11T, sD0, sD1, sI0, sI1, sperm, stype);
+        pend = kn;
+      }
       if (rows && sv.wk0) band_row_copies<T>(sv, s, ns, K0, k, w, rb0, rb1, xs, xw);
     }
+    if (warp == 0) publish();
   }
   // the last CTA to finish resets the ticket counters for the next launch
   __syncthreads();
