@@ -325,7 +325,9 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
       };
       // the 16 entries of chunk cb of this thread's row: in one region (one
       // base pointer, one stride), or, for a chunk that straddles the last
-      // factor column ns, element by element
+      // factor column ns, element by element.  C is touched once per outer
+      // block: streaming loads and stores (evict first), so that L2 keeps the
+      // operand tiles that other tiles reuse
       auto load_chunk = [&](int cb, float (&cv)[16]) {
         if (r >= rows) return;
         const int64_t gjc = gj0 + cb;
@@ -334,10 +336,10 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
           const float *__restrict__ base = in_l ? job.L + gi + gjc * job.f : job.CB + (gi - job.ns) + (gjc - job.ns) * fcb;
           const int64_t st = in_l ? job.f : fcb;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcg(base + j * st) : 0.f;
+          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcs(base + j * st) : 0.f;
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcg(elem(cb + j)) : 0.f;
+          for (int j = 0; j < 16; ++j) cv[j] = (cb + j < cols && r + roff >= cb + j) ? __ldcs(elem(cb + j)) : 0.f;
         }
       };
       auto store_chunk = [&](int cb, const float (&cv)[16], const uint32_t (&v)[16]) {
@@ -349,11 +351,11 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
           const int64_t st = in_l ? job.f : fcb;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (cb + j < cols && r + roff >= cb + j) __stcg(base + j * st, cv[j] - __uint_as_float(v[j]));
+            if (cb + j < cols && r + roff >= cb + j) __stcs(base + j * st, cv[j] - __uint_as_float(v[j]));
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (cb + j < cols && r + roff >= cb + j) __stcg(elem(cb + j), cv[j] - __uint_as_float(v[j]));
+            if (cb + j < cols && r + roff >= cb + j) __stcs(elem(cb + j), cv[j] - __uint_as_float(v[j]));
         }
       };
       float ca[16], cb2[16];
