@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
 template <typename T>
 __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
                                          SolveItem itm, int nb, unsigned tag, int *status, double *__restrict__ sol,
-                                         T (*U)[SB + 1], SolveShared<T> &sm) {
+                                         T (*U)[SB + 1], SolveShared<T> &sm, T *xall, int xcap) {
   using AT = T;
   const int s = lvl_fronts[itm.q];
   const int dpn = sv.dpn;
@@ -410,13 +410,40 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) sum[cc] = comp[cc] = AT(0);
   int ph = 0;  // alternates the value buffers across both loops
-  // struct rows: the solution there (the ancestors') is final; gathered 128
-  // rows a pass
+  // struct rows: the solution there (the ancestors') is final
   const int nown = d.sn_nown[s];
   const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
-  // the struct-rank index of the next pass is read one pass ahead
-  int sidx = (tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
-  for (int rs = ns; rs < f; rs += SB, ++ph) {
+  if (f - ns <= xcap) {
+    // all of it gathered into shared memory once, then 128 rows a pass
+    // without a barrier (the warps overlap)
+    for (int idx = tid; idx < f - ns; idx += blockDim.x)
+      xall[idx] = (AT)sol[(int64_t)sr[(ns + idx) / dpn - nown] * dpn + (ns + idx) % dpn];
+    __syncthreads();
+    for (int rs = ns; rs < f; rs += SB) {
+      const int nrs = min(SB, f - rs);
+      const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
+      T q[8][4];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          q[cc][m] = (c0 + cc < w && lane + 32 * m < nrs) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
+      AT xv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) xv[m] = lane + 32 * m < nrs ? xall[rs - ns + lane + 32 * m] : AT(0);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        AT a = AT(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
+        kahan_add(sum[cc], comp[cc], a);
+      }
+    }
+  }
+  // otherwise gathered 128 rows a pass; the struct-rank index of the next
+  // pass is read one pass ahead
+  int sidx = (f - ns > xcap && tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
+  for (int rs = ns; f - ns > xcap && rs < f; rs += SB, ++ph) {
     const int nrs = min(SB, f - rs);
     const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
     T q[8][4];
@@ -494,18 +521,27 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   }
 }
 
+// dynamic shared memory: the block inverse (SB x (SB + 1)), then xcap
+// solution values of the ancestor (struct) rows (0: gathered pass by pass)
 template <typename T>
 __global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
     k_bwd_level(DevSym d, SV sv, const int32_t *__restrict__ lvl_fronts, const SolveItem *__restrict__ items, int nb,
-                unsigned *ctl, int *status, double *__restrict__ sol) {
-  extern __shared__ unsigned char blk_raw[];
+                unsigned *ctl, int *status, double *__restrict__ sol, int xcap) {
+  extern __shared__ __align__(16) unsigned char blk_raw[];
   __shared__ SolveShared<T> sm;
   if (solve_item_begin(ctl, status, sm)) {
     const unsigned tag = 2u * *(volatile unsigned *)ctl + 1u;
     bwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, sol, reinterpret_cast<T(*)[SB + 1]>(blk_raw),
-                sm);
+                sm, reinterpret_cast<T *>(blk_raw) + SB * (SB + 1), xcap);
   }
   solve_item_end(ctl);
+}
+
+// the most ancestor rows a backward CTA keeps in shared memory (two FP32 CTAs,
+// one FP64 CTA per SM)
+template <typename T>
+constexpr int bwd_xcap_max() {
+  return sizeof(T) == 4 ? 9216 : 8192;
 }
 
 template <typename T>
@@ -532,8 +568,11 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
     const int64_t t0 = st.h_bwd_lvl[L], nt = st.h_bwd_lvl[L + 1] - t0;
     if (nt == 0) continue;
-    k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem, c.stream>>>(c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb,
-                                                              st.ctl, c.status, x);
+    int xs = 0;  // the level's most ancestor rows of a front
+    for (int s : c.S.level_fronts[L]) xs = std::max(xs, c.S.sn[s].nstruct * dpn);
+    const int xcap = xs <= bwd_xcap_max<T>() ? xs : 0;
+    k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem + (size_t)xcap * sizeof(T), c.stream>>>(
+        c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb, st.ctl, c.status, x, xcap);
     c.count();
   }
 }
@@ -593,8 +632,10 @@ void launch_diag_inverse(Ctx &c, Store &st, const int32_t *fronts, int max_ns, i
 void set_solve_attributes() {
   cudaFuncSetAttribute(k_fwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
   cudaFuncSetAttribute(k_fwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
-  cudaFuncSetAttribute(k_bwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
-  cudaFuncSetAttribute(k_bwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
+  cudaFuncSetAttribute(k_bwd_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((SB * (SB + 1) + bwd_xcap_max<double>()) * 8));
+  cudaFuncSetAttribute(k_bwd_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((SB * (SB + 1) + bwd_xcap_max<float>()) * 4));
   cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 8));
   cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SB * (SB + 1) * 4));
 }
