@@ -221,8 +221,10 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
         if (!any) break;
       }
       s.h_blk_off.push_back((int64_t)s.h_blk_items.size());
-      // the trailing update's tiles per active front (fronts sorted by ns,
-      // largest first, so the active ones come first), for each window
+      // the trailing update's units per active front (fronts sorted by ns,
+      // largest first, so the active ones come first), for each window: single
+      // tiles for the next outer block's columns (window 0, on the critical
+      // path: more CTAs), tile pairs for the rest (1) and the whole (2)
       const int next_w = FACTOR_BLOCK / 128;
       for (int wdw = 0; wdw < 3; ++wdw) {
         const int win0 = wdw == 1 ? next_w : 0, win1 = wdw == 0 ? next_w : -1;
@@ -235,7 +237,7 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
           const int64_t kend = std::min<int64_t>(K0 + FACTOR_BLOCK, ns);
           const int nt = (int)((f - kend + 127) / 128);
           const int m = std::min(win1 < 0 ? nt : win1, nt) - win0, n = nt - win0;
-          if (m > 0) acc += m * (m + 1) / 2 + (n - m) * m;
+          acc += tc::window_units(m, n, wdw != 0);
           s.h_upd_cum.push_back(acc);
         }
       }

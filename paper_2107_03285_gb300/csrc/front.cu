@@ -306,8 +306,8 @@ struct UpdateTiles {
   const int32_t *fronts;
   const tc::Maps *maps;
   const int32_t *cum;
-  int na, K0, NB, win0, win1;
-  // list index g -> its front's job and tensor maps, and the tile's index in
+  int na, K0, NB, win0, win1, pair;
+  // list index g -> its front's job and tensor maps, and the unit's index in
   // the front's window
   __device__ __forceinline__ void get(int g, tc::TileJob &job, const tc::Maps *&mp, int &t) const {
     int lo = 0, hi = na;  // the front holding g: the last q with cum[q] <= g
@@ -326,8 +326,8 @@ struct UpdateTiles {
     const int nt = (nrows + tc::TILE - 1) / tc::TILE;
     job.win0 = win0;
     job.m = min(win1 < 0 ? nt : win1, nt) - win0;
-    const int n = nt - win0;  // tile rows of the window
-    job.ntiles = job.m * (job.m + 1) / 2 + (n - job.m) * job.m;
+    job.pair = pair;
+    job.ntiles = tc::window_units(job.m, nt - win0, pair != 0);
     job.L = (float *)sv.F + sv.front_off[s];
     job.CB = (float *)sv.CB + sv.cb_off[s];
     job.f = f;
@@ -339,15 +339,15 @@ struct UpdateTiles {
   }
 };
 
-// persistent tensor-core trailing update: CTA x walks tiles x, x + gridDim.x,
-// ... of the launch's list (UpdateTiles).
+// persistent tensor-core trailing update: CTA x walks units x, x + gridDim.x,
+// ... of the launch's list (UpdateTiles); pair = the units are tile pairs.
 __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                                  int K0, int NB, const tc::Maps *__restrict__ maps,
-                                                                 int win0, int win1, const int32_t *__restrict__ cum,
-                                                                 int na, int *status) {
+                                                                 int win0, int win1, int pair,
+                                                                 const int32_t *__restrict__ cum, int na, int *status) {
   const int total = cum[na];
   if ((int)blockIdx.x >= total) return;
-  const UpdateTiles src{d, sv, fronts, maps, cum, na, K0, NB, win0, win1};
+  const UpdateTiles src{d, sv, fronts, maps, cum, na, K0, NB, win0, win1, pair};
   tc::tile_loop_tc(src, total, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
 }
 
@@ -492,8 +492,9 @@ void factor_impl(Ctx &c, Store &st) {
         };
         if (std::is_same<T, float>::value && st.tc) {
           // one CTA per SM (192 KB shared memory), each taking an equal share
-          // of one list of the tiles of every active front.  The tile columns
-          // holding the next outer block's columns go first on this stream;
+          // of one list of the units of every active front.  The tile columns
+          // holding the next outer block's columns go first on this stream, in
+          // single tiles so that more SMs share that critical step;
           // the rest runs on the side stream, next to the next block's panels
           // (which write the other operand set), on fewer SMs so that those
           // panels find room
@@ -515,7 +516,8 @@ void factor_impl(Ctx &c, Store &st) {
             const int g = std::max(1, std::min(tiles, ctas));
             ProfScope ps(c, SGN_PROF_UPDATE, split ? flops_cols(0, next_w) : flops_cols(0, -1));
             k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, cum, na, c.status);
+                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, split ? 0 : 1, cum, na,
+                c.status);
             c.tc_launches++;
             c.count();
           }
@@ -531,7 +533,7 @@ void factor_impl(Ctx &c, Store &st) {
               const int g = std::max(1, std::min(tiles, rest));
               ProfScope ps(c, SGN_PROF_UPDATE, flops_cols(next_w, -1));
               k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, cum, na, c.status);
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, 1, cum, na, c.status);
               c.tc_launches++;
               c.count();
             }

@@ -2,15 +2,15 @@
 //     C[kend:, kend:] -= W L^T      (lower triangle, FP32 fronts)
 // where W = L21 D and L = L21 of one outer block (inner dimension <= 256).
 //
-// Each CTA owns one 128 x 128 output tile.  W and L are kept in K-major
-// global arrays split as x = hi + lo with hi = x with its low 13 mantissa bits
-// cleared (exactly representable in TF32) and lo = x - hi; the tile is
-// accumulated in TMEM (FP32) as Whi Lhi^T + Whi Llo^T + Wlo Lhi^T
-// ("3xTF32"), which keeps FP32-level accuracy on the TF32 tensor path.
+// Each CTA owns one 128-row output unit: one 128 x 128 tile, or two tiles of
+// the same tile row side by side (128 x 256, one N = 256 MMA), which share
+// the W operand and so cut the operand bytes per output entry by a quarter.
+// W and L are kept in K-major global arrays split as x = hi + lo with hi = x
+// with its low 13 mantissa bits cleared (exactly representable in TF32) and
+// lo = x - hi; the unit is accumulated in TMEM (FP32) as
+// Whi Lhi^T + Whi Llo^T + Wlo Lhi^T ("3xTF32"), which keeps FP32-level
+// accuracy on the TF32 tensor path.
 //
-//   warp 0 / lane 0 : TMA producer  (cp.async.bulk.tensor, 128B swizzle)
-//   warp 1 / lane 0 : MMA issuer    (tcgen05.mma.cta_group::1.kind::tf32)
-//   warps 0..3      : epilogue      (tcgen05.ld 32x32b, C -= D in global)
 // Every mbarrier wait is bounded; on expiry the CTA records DEV_TIMEOUT in
 // the status word, drains the copies it issued (bounded again), frees its
 // TMEM and returns.
@@ -25,7 +25,7 @@ namespace tc {
 constexpr int TILE = 128;          // output tile (M = N)
 constexpr int KCH = 32;            // K per stage: 32 FP32 = one 128-byte swizzle row
 constexpr int TILE_BYTES = TILE * KCH * 4;           // 16 KB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // Whi, Wlo, Lhi, Llo
+constexpr int STAGE_BYTES = 6 * TILE_BYTES;          // Whi, Wlo, Lhi x 2, Llo x 2
 constexpr long long WAIT_CYCLES = 1ll << 31;         // ~1 s at 2 GHz
 
 struct Maps {                      // one set of tensor maps per front
@@ -89,9 +89,9 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D FP32, A and B TF32, both K-major, M = N = 128
-__host__ __device__ constexpr uint32_t idesc_tf32_128x128() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TILE >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
+// instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_tf32_128xn(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -137,16 +137,16 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised trailing update: each CTA walks its share of
-// one flat list of tiles over every front of a level (tiles first, first +
-// stride, ...); two TMEM accumulators (2 x 128 columns) let the epilogue of
-// tile i run while the producer and MMA warps already work on tile i + 1.
-// The tile source maps a list index to its front's job, tensor maps and the
-// tile's index in that front's window (Src::get); every role walks the same
+// one flat list of units over every front of a level (units first, first +
+// stride, ...); two TMEM accumulators (2 x 256 columns) let the epilogue of
+// unit i run while the producer and MMA warps already work on unit i + 1.
+// The unit source maps a list index to its front's job, tensor maps and the
+// unit's index in that front's window (Src::get); every role walks the same
 // sequence.
 //   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
-//   warps 2..9    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31,
-//                   columns 64 ((w - 2) / 4) .. + 63 of the tile)
-constexpr int PSTAGES = 3;
+//   warps 2..9    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//                   half of the unit's columns, (w - 2) / 4 naming the half)
+constexpr int PSTAGES = 2;
 constexpr int PTHREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;  // + alignment slack
@@ -158,24 +158,22 @@ struct TileJob {                 // one front's part of a trailing update
   int nrows;                     // f - kend
   int kend;                      // first trailing row (TMA row coordinate of tile row 0)
   int kchunks;                   // 32-wide K chunks
-  int ntiles;                    // tiles of the window
+  int ntiles;                    // units of the window
   int win0, m;                   // the window: tile columns win0 .. win0 + m - 1 (rows >= columns)
+  int pair;                      // units are tile pairs (else single tiles)
 };
 
-// tile t of a job's window, row-major: the window's m x m triangle first,
-// then its rows below, m tiles each (absolute tile coordinates bi >= bj)
-__device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj);
-__device__ __forceinline__ void window_tile(const TileJob &job, int t, int &bi, int &bj) {
-  const int t0 = job.m * (job.m + 1) / 2;
-  int r, c;
-  if (t < t0) {
-    tile_coords(t, r, c);
-  } else {
-    r = job.m + (t - t0) / job.m;
-    c = (t - t0) % job.m;
-  }
-  bi = job.win0 + r;
-  bj = job.win0 + c;
+// Units of a window of m tile columns over n tile rows (rows >= columns
+// within the window's m x m triangle, then n - m full rows).  Single tiles:
+// m (m + 1) / 2 + (n - m) m.  Pairs (tile columns 2u, 2u + 1 of one tile row,
+// the last one of a row single when the row has an odd number of tiles):
+// triangle row r holds floor(r / 2) + 1 units, a full row ceil(m / 2).
+__host__ __device__ __forceinline__ int window_units(int m, int n, bool pair) {
+  if (m <= 0) return 0;
+  if (!pair) return m * (m + 1) / 2 + (n - m) * m;
+  const int q = m / 2;
+  const int tri = (m & 1) ? (q + 1) * (q + 1) : q * (q + 1);
+  return tri + (n - m) * ((m + 1) / 2);
 }
 
 __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
@@ -183,6 +181,42 @@ __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
   while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
   while (bi * (bi + 1) / 2 > tile) --bi;
   bj = tile - bi * (bi + 1) / 2;
+}
+
+// unit t of a job's window, row-major: the window's triangle first, then its
+// rows below.  (bi, bj) is the unit's first tile (absolute tile coordinates,
+// bi >= bj); two = the unit also holds tile (bi, bj + 1)
+__device__ __forceinline__ void window_unit(const TileJob &job, int t, int &bi, int &bj, bool &two) {
+  int r, c;
+  if (!job.pair) {
+    const int t0 = job.m * (job.m + 1) / 2;
+    if (t < t0) {
+      tile_coords(t, r, c);
+    } else {
+      r = job.m + (t - t0) / job.m;
+      c = (t - t0) % job.m;
+    }
+    two = false;
+  } else {
+    const int t0 = window_units(job.m, job.m, true);
+    if (t < t0) {
+      // triangle rows 2q and 2q + 1 hold q + 1 units each: units q (q + 1) ..
+      int q = (int)((sqrtf(4.f * (float)t + 1.f) - 1.f) * 0.5f);  // corrected below
+      while ((q + 1) * (q + 2) <= t) ++q;
+      while (q * (q + 1) > t) --q;
+      const int o = t - q * (q + 1);
+      r = o <= q ? 2 * q : 2 * q + 1;
+      c = 2 * (o <= q ? o : o - q - 1);
+      two = c + 1 <= r;
+    } else {
+      const int per = (job.m + 1) / 2;
+      r = job.m + (t - t0) / per;
+      c = 2 * ((t - t0) % per);
+      two = c + 1 < job.m;
+    }
+  }
+  bi = job.win0 + r;
+  bj = job.win0 + c;
 }
 
 template <typename Src>
@@ -204,7 +238,7 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(2 * TILE)
+                 "r"(4 * TILE)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -213,10 +247,13 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
+  // stage layout: Whi | Wlo | Lhi (tile bj) | Lhi (tile bj + 1) | Llo (bj) |
+  // Llo (bj + 1): the two L tiles of a pair sit back to back, so that one
+  // K-major 256-row operand (8-row groups 1 KB apart) covers both
   if (warp == 0) {
     if (lane == 0 && my_tiles > 0) {
       const Maps *cur = nullptr;
-      int g = 0;  // global chunk counter over all of this CTA's tiles
+      int g = 0;  // global chunk counter over all of this CTA's units
       bool stop = false;
       for (int lt = 0; lt < my_tiles && !stop; ++lt) {
         TileJob job;
@@ -231,7 +268,8 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
           cur = maps;
         }
         int bi, bj;
-        window_tile(job, t, bi, bj);
+        bool two;
+        window_unit(job, t, bi, bj, two);
         const int rw = job.kend + bi * TILE, rl = job.kend + bj * TILE;
         for (int kc = 0; kc < job.kchunks; ++kc, ++g) {
           const int s = g % PSTAGES;
@@ -240,11 +278,15 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
           }
           if (*(volatile int *)&abort_flag) { stop = true; break; }
           unsigned char *st = sm + s * STAGE_BYTES;
-          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+          mbar_expect_tx(&full_bar[s], (two ? 6 : 4) * TILE_BYTES);
           tma_load_2d(st + 0 * TILE_BYTES, &maps->whi, &full_bar[s], kc * KCH, rw);
           tma_load_2d(st + 1 * TILE_BYTES, &maps->wlo, &full_bar[s], kc * KCH, rw);
           tma_load_2d(st + 2 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, rl);
-          tma_load_2d(st + 3 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl);
+          tma_load_2d(st + 4 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl);
+          if (two) {
+            tma_load_2d(st + 3 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, rl + TILE);
+            tma_load_2d(st + 5 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl + TILE);
+          }
         }
       }
       // drain the copies still in flight (bounded)
@@ -253,7 +295,6 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
     }
   } else if (warp == 1) {
     if (lane == 0 && my_tiles > 0) {
-      const uint32_t idesc = idesc_tf32_128x128();
       int g = 0;
       bool stop = false;
       for (int lt = 0; lt < my_tiles && !stop; ++lt) {
@@ -261,13 +302,17 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
         const Maps *maps;
         int t;
         src.get(first + lt * stride, job, maps, t);
+        int bi, bj;
+        bool two;
+        window_unit(job, t, bi, bj, two);
+        const uint32_t idesc = idesc_tf32_128xn(two ? 2 * TILE : TILE);
         const int kch = job.kchunks;
         const int b = lt & 1;
         if (lt >= 2 && !mbar_wait(&acc_empty[b], ((lt >> 1) - 1) & 1, status, flag_timeout)) {
           abort_flag = 1; break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc_tmem = tmem + (uint32_t)(b * TILE);
+        const uint32_t acc_tmem = tmem + (uint32_t)(b * 2 * TILE);
         for (int kc = 0; kc < kch; ++kc, ++g) {
           const int s = g % PSTAGES;
           if (!mbar_wait(&full_bar[s], (g / PSTAGES) & 1, status, flag_timeout)) { abort_flag = 1; stop = true; break; }
@@ -279,7 +324,7 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
             const uint64_t ahi = umma_desc_sw128(base + 0 * TILE_BYTES + off);
             const uint64_t alo = umma_desc_sw128(base + 1 * TILE_BYTES + off);
             const uint64_t bhi = umma_desc_sw128(base + 2 * TILE_BYTES + off);
-            const uint64_t blo = umma_desc_sw128(base + 3 * TILE_BYTES + off);
+            const uint64_t blo = umma_desc_sw128(base + 4 * TILE_BYTES + off);
             umma_tf32(acc_tmem, ahi, bhi, idesc, (kc | k) != 0);
             umma_tf32(acc_tmem, ahi, blo, idesc, 1);
             umma_tf32(acc_tmem, alo, bhi, idesc, 1);
@@ -296,24 +341,31 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
       }
     }
   } else {
-    // epilogue warps 2..9: a quarter of the tile's rows (TMEM lanes) and
-    // half of its columns each
+    // epilogue warps 2..9: a quarter of the unit's rows (TMEM lanes) and
+    // half of its columns each (64 of a single-tile list's tiles, 128 of a
+    // pair list's units)
     const int quad = warp & 3;
-    const int col0 = ((warp - 2) / 4) * (TILE / 2);
+    const int half = (warp - 2) / 4;
     const int r = quad * 32 + lane;
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int b = lt & 1;
-      // the tile and its C entries do not depend on the accumulator: the
-      // warp's 64 columns go in four 16-column chunks, the first two loaded
-      // before the wait and each later one while an earlier one is written,
-      // so that the loads' latency overlaps the MMAs
+      // the unit and its C entries do not depend on the accumulator: the
+      // warp's columns go in 16-column chunks, the first two loaded before
+      // the wait and each later one while an earlier one is written, so
+      // that the loads' latency overlaps the MMAs
       TileJob job;
       const Maps *maps;
       int t;
       src.get(first + lt * stride, job, maps, t);
       int bi, bj;
-      window_tile(job, t, bi, bj);
-      const int rows = min(TILE, job.nrows - bi * TILE), cols = min(TILE, job.nrows - bj * TILE);
+      bool two;
+      window_unit(job, t, bi, bj, two);
+      const int wcols = job.pair ? TILE : TILE / 2;  // this warp's column span
+      const int col0 = half * wcols;
+      const int nch = wcols / 16;
+      const int rows = min(TILE, job.nrows - bi * TILE);
+      const int cols = min(two ? 2 * TILE : TILE, job.nrows - bj * TILE);
+      const bool active = col0 < cols;  // warp-uniform
       const int roff = (bi - bj) * TILE;
       // element (gi, gj) of the front: factor column (gj < ns) or
       // contribution block (gj >= ns, then gi >= gj >= ns)
@@ -327,7 +379,7 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
       // base pointer, one stride), or, for a chunk that straddles the last
       // factor column ns, element by element.  C is touched once per outer
       // block: streaming loads and stores (evict first), so that L2 keeps the
-      // operand tiles that other tiles reuse
+      // operand tiles that other units reuse
       auto load_chunk = [&](int cb, float (&cv)[16]) {
         if (r >= rows) return;
         const int64_t gjc = gj0 + cb;
@@ -359,25 +411,27 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
         }
       };
       float ca[16], cb2[16];
-      load_chunk(col0, ca);
-      load_chunk(col0 + 16, cb2);
+      if (active) {
+        load_chunk(col0, ca);
+        load_chunk(col0 + 16, cb2);
+      }
       bool ok = mbar_wait(&acc_full[b], (lt >> 1) & 1, status, flag_timeout);
       // tcgen05.ld is warp-collective: the whole warp takes the same branch
       ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
-      uint32_t v[16];
-      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TILE + col0);
-      tmem_ld_32x32b_x16(trow, v);
-      store_chunk(col0, ca, v);
-      load_chunk(col0 + 32, ca);
-      tmem_ld_32x32b_x16(trow + 16u, v);
-      store_chunk(col0 + 16, cb2, v);
-      load_chunk(col0 + 48, cb2);
-      tmem_ld_32x32b_x16(trow + 32u, v);
-      store_chunk(col0 + 32, ca, v);
-      tmem_ld_32x32b_x16(trow + 48u, v);
-      store_chunk(col0 + 48, cb2, v);
+      if (active) {
+        uint32_t v[16];
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * TILE + col0);
+        for (int q = 0; q < nch; q += 2) {
+          tmem_ld_32x32b_x16(trow + 16u * q, v);
+          store_chunk(col0 + 16 * q, ca, v);
+          if (q + 2 < nch) load_chunk(col0 + 16 * (q + 2), ca);
+          tmem_ld_32x32b_x16(trow + 16u * (q + 1), v);
+          store_chunk(col0 + 16 * (q + 1), cb2, v);
+          if (q + 3 < nch) load_chunk(col0 + 16 * (q + 3), cb2);
+        }
+      }
       // this warp's TMEM reads of buffer b are complete (tcgen05.wait::ld)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -387,7 +441,7 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * TILE) : "memory");
   }
 }
 
