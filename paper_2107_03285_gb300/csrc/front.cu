@@ -340,15 +340,16 @@ struct UpdateTiles {
 };
 
 // persistent tensor-core trailing update: CTA x walks units x, x + gridDim.x,
-// ... of the launch's list (UpdateTiles); pair = the units are tile pairs.
+// ... of the launch's list (UpdateTiles); PAIR = the units are tile pairs.
+template <bool PAIR>
 __global__ void __launch_bounds__(tc::PTHREADS, 1) k_update_tcp(DevSym d, SV sv, const int32_t *__restrict__ fronts,
                                                                  int K0, int NB, const tc::Maps *__restrict__ maps,
-                                                                 int win0, int win1, int pair,
-                                                                 const int32_t *__restrict__ cum, int na, int *status) {
+                                                                 int win0, int win1, const int32_t *__restrict__ cum,
+                                                                 int na, int *status) {
   const int total = cum[na];
   if ((int)blockIdx.x >= total) return;
-  const UpdateTiles src{d, sv, fronts, maps, cum, na, K0, NB, win0, win1, pair};
-  tc::tile_loop_tc(src, total, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
+  const UpdateTiles src{d, sv, fronts, maps, cum, na, K0, NB, win0, win1, PAIR ? 1 : 0};
+  tc::tile_loop_tc<PAIR>(src, total, blockIdx.x, gridDim.x, status, DEV_TIMEOUT);
 }
 
 __global__ void k_pivot_counts(int64_t n, const int32_t *__restrict__ type, const double *__restrict__ D0,
@@ -515,9 +516,12 @@ void factor_impl(Ctx &c, Store &st) {
             const int tiles = tiles_of(split ? 0 : 2, cum);
             const int g = std::max(1, std::min(tiles, ctas));
             ProfScope ps(c, SGN_PROF_UPDATE, split ? flops_cols(0, next_w) : flops_cols(0, -1));
-            k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, split ? next_w : -1, split ? 0 : 1, cum, na,
-                c.status);
+            if (split)
+              k_update_tcp<false><<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, next_w, cum, na, c.status);
+            else
+              k_update_tcp<true><<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, 0, -1, cum, na, c.status);
             c.tc_launches++;
             c.count();
           }
@@ -532,8 +536,8 @@ void factor_impl(Ctx &c, Store &st) {
               const int rest = std::max(1, ctas - std::min(ctas / 4, PANEL_RESERVE_SMS));
               const int g = std::max(1, std::min(tiles, rest));
               ProfScope ps(c, SGN_PROF_UPDATE, flops_cols(next_w, -1));
-              k_update_tcp<<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
-                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, 1, cum, na, c.status);
+              k_update_tcp<true><<<g, tc::PTHREADS, tc::PSMEM_BYTES, c.stream>>>(
+                  c.ds, sv, fronts, K0, FACTOR_BLOCK, maps, next_w, -1, cum, na, c.status);
               c.tc_launches++;
               c.count();
             }
@@ -679,7 +683,8 @@ void set_kernel_attributes() {
   set_block_panels_smem<float, 32>((int)block_panels_smem(32, sizeof(float)));
   set_block_panels_smem<double, 16>((int)block_panels_smem(16, sizeof(double)));
   set_block_panels_smem<double, 32>((int)block_panels_smem(32, sizeof(double)));
-  cudaFuncSetAttribute(k_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
+  cudaFuncSetAttribute(k_update_tcp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
+  cudaFuncSetAttribute(k_update_tcp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::PSMEM_BYTES);
   set_solve_attributes();
 }
 

@@ -25,7 +25,13 @@ namespace tc {
 constexpr int TILE = 128;          // output tile (M = N)
 constexpr int KCH = 32;            // K per stage: 32 FP32 = one 128-byte swizzle row
 constexpr int TILE_BYTES = TILE * KCH * 4;           // 16 KB
-constexpr int STAGE_BYTES = 6 * TILE_BYTES;          // Whi, Wlo, Lhi x 2, Llo x 2
+// operand stages: single-tile units stage Whi, Wlo, Lhi, Llo (64 KB, three
+// stages); pair units Whi, Wlo, Lhi x 2, Llo x 2 (96 KB, two stages)
+template <bool PAIR> struct Stages {
+  static constexpr int N = PAIR ? 2 : 3;
+  static constexpr int BYTES = (PAIR ? 6 : 4) * TILE_BYTES;
+  static constexpr int LLO = PAIR ? 4 : 3;  // tile slot of Llo
+};
 constexpr long long WAIT_CYCLES = 1ll << 31;         // ~1 s at 2 GHz
 
 struct Maps {                      // one set of tensor maps per front
@@ -146,10 +152,12 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 //   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ TMEM alloc)
 //   warps 2..9    : epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and
 //                   half of the unit's columns, (w - 2) / 4 naming the half)
-constexpr int PSTAGES = 2;
 constexpr int PTHREADS = 320;
 constexpr int EPI_WARPS = 8;
-constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr int PSMEM_BYTES = (Stages<true>::N * Stages<true>::BYTES > Stages<false>::N * Stages<false>::BYTES
+                                 ? Stages<true>::N * Stages<true>::BYTES
+                                 : Stages<false>::N * Stages<false>::BYTES) +
+                            1024;  // + alignment slack
 
 struct TileJob {                 // one front's part of a trailing update
   float *L;                      // the front's factor columns (f x ns, column-major)
@@ -219,10 +227,11 @@ __device__ __forceinline__ void window_unit(const TileJob &job, int t, int &bi, 
   bj = job.win0 + c;
 }
 
-template <typename Src>
+template <bool PAIR, typename Src>
 __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int first, int stride, int *status,
                                              int flag_timeout) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  constexpr int PSTAGES = Stages<PAIR>::N, STAGE_BYTES = Stages<PAIR>::BYTES, LLO = Stages<PAIR>::LLO;
   __shared__ uint64_t full_bar[PSTAGES], empty_bar[PSTAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
@@ -247,9 +256,10 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  // stage layout: Whi | Wlo | Lhi (tile bj) | Lhi (tile bj + 1) | Llo (bj) |
-  // Llo (bj + 1): the two L tiles of a pair sit back to back, so that one
-  // K-major 256-row operand (8-row groups 1 KB apart) covers both
+  // stage layout of a pair list: Whi | Wlo | Lhi (tile bj) | Lhi (tile bj + 1)
+  // | Llo (bj) | Llo (bj + 1): the two L tiles of a pair sit back to back, so
+  // that one K-major 256-row operand (8-row groups 1 KB apart) covers both;
+  // of a single-tile list: Whi | Wlo | Lhi | Llo
   if (warp == 0) {
     if (lane == 0 && my_tiles > 0) {
       const Maps *cur = nullptr;
@@ -282,8 +292,8 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
           tma_load_2d(st + 0 * TILE_BYTES, &maps->whi, &full_bar[s], kc * KCH, rw);
           tma_load_2d(st + 1 * TILE_BYTES, &maps->wlo, &full_bar[s], kc * KCH, rw);
           tma_load_2d(st + 2 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, rl);
-          tma_load_2d(st + 4 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl);
-          if (two) {
+          tma_load_2d(st + LLO * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl);
+          if (PAIR && two) {
             tma_load_2d(st + 3 * TILE_BYTES, &maps->lhi, &full_bar[s], kc * KCH, rl + TILE);
             tma_load_2d(st + 5 * TILE_BYTES, &maps->llo, &full_bar[s], kc * KCH, rl + TILE);
           }
@@ -324,7 +334,7 @@ __device__ __forceinline__ void tile_loop_tc(const Src &src, int ntiles, int fir
             const uint64_t ahi = umma_desc_sw128(base + 0 * TILE_BYTES + off);
             const uint64_t alo = umma_desc_sw128(base + 1 * TILE_BYTES + off);
             const uint64_t bhi = umma_desc_sw128(base + 2 * TILE_BYTES + off);
-            const uint64_t blo = umma_desc_sw128(base + 4 * TILE_BYTES + off);
+            const uint64_t blo = umma_desc_sw128(base + LLO * TILE_BYTES + off);
             umma_tf32(acc_tmem, ahi, bhi, idesc, (kc | k) != 0);
             umma_tf32(acc_tmem, ahi, blo, idesc, 1);
             umma_tf32(acc_tmem, alo, bhi, idesc, 1);
