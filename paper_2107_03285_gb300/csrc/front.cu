@@ -397,7 +397,7 @@ int n_active(const LevelInfo &li, int k) {
 }
 
 // SMs the rest of a split trailing update leaves to the next block's panels
-constexpr int PANEL_RESERVE_SMS = 32;
+constexpr int PANEL_RESERVE_SMS = 16;
 
 template <typename T>
 void factor_impl(Ctx &c, Store &st) {
