@@ -38,7 +38,7 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes of the tensor-core trailing update per algorithmic byte (the
 # trailing triangle read and written once in FP32), from the ncu capture of
 # every update launch of a kuhn3d_24 step summarised in
-# profiles/k_update_tcp_kuhn3d_24.md (4.515 GB / 2.949 GB; the full-size
+# profiles/k_update_tcp_kuhn3d_24.md (4.513 GB / 2.949 GB; the full-size
 # launches are too large to capture); set to None when the kernel changes
 UPDATE_DRAM_PER_ALGO_BYTE = 1.53
 
