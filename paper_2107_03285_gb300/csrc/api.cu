@@ -147,13 +147,15 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   const int n_sn = (int)c.S.sn.size();
   s.h_front_off.assign(n_sn, 0); s.h_w_off.assign(n_sn, 0);
   s.h_rhs_off.assign(n_sn, 0); s.h_piv_off.assign(n_sn, 0); s.h_xinv_off.assign(n_sn, 0);
-  int64_t fo = 0, ro = 0, po = 0, xo = 0;
+  s.h_part_off.assign(n_sn, 0);
+  int64_t fo = 0, ro = 0, po = 0, xo = 0, pa = 0;
   constexpr int64_t SBK = 128;  // solve block width
   for (int i = 0; i < n_sn; ++i) {
     int64_t f = (int64_t)c.S.sn[i].fnodes() * dpn, ns = (int64_t)c.S.sn[i].nown * dpn;
     s.h_front_off[i] = fo; fo += ((f * ns + 63) / 64) * 64;
     s.h_rhs_off[i] = ro; ro += f;
     s.h_piv_off[i] = po; po += ns;
+    s.h_part_off[i] = pa; pa += s.fp32 ? (int64_t)bwd_parts(f - ns) * ns : 0;
     // full blocks of SBK^2, the last one (w < SBK) of w^2, 16-byte aligned
     const int64_t nfull = ns / SBK, wl = ns - nfull * SBK;
     s.h_xinv_off[i] = xo; xo += nfull * SBK * SBK + ((wl * wl + 3) / 4) * 4;
@@ -173,8 +175,10 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
   // substitution schedules (one CTA per item): forward items are the
   // front's 128-row bands, own bands (key b) before its struct bands (key
   // nbo + j), except that a front with one own block is a single item;
-  // backward items its 128-column blocks, last first (key nbo - 1 - b).
-  // Sorting a level's items by key puts every dependency first.
+  // backward items its 128-column blocks, last first (key nbo - 1 - b),
+  // and for an FP32 front with many ancestor rows the parts of each block's
+  // ancestor-row product (key -1 - (b BWD_PARTS_MAX + h), which wait on
+  // nothing).  Sorting a level's items by key puts every dependency first.
   s.h_fwd_items.clear(); s.h_bwd_items.clear();
   s.h_fwd_lvl.assign(1, 0); s.h_bwd_lvl.assign(1, 0);
   int32_t q = 0;
@@ -188,6 +192,9 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
         const int32_t nfw = nbo > 1 ? nbo + nbs : 1;
         for (int32_t k = 0; k < nfw; ++k) s.h_fwd_items.push_back({q, k});
         for (int32_t k = 0; k < nbo; ++k) s.h_bwd_items.push_back({q, k});
+        const int nparts = s.fp32 ? bwd_parts(f - ns) : 0;
+        for (int32_t b = 0; b < nbo; ++b)
+          for (int h = 0; h < nparts; ++h) s.h_bwd_items.push_back({q, -1 - (b * BWD_PARTS_MAX + h)});
       }
       ++q;
     }
@@ -243,9 +250,11 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
       }
     }
   }
-  // self-check (the substitutions' waits rely on it): an item of key k waits
-  // only on keys 0 .. k - 1 of its own front, so each front's items must
-  // appear with keys 0, 1, 2, ... in list order within their level
+  // self-check (the substitutions' waits rely on it): an item of key k >= 0
+  // waits only on keys 0 .. k - 1 and the negative keys (the parts, which
+  // wait on nothing) of its own front, so within their level each front's
+  // parts must come first and its other items with keys 0, 1, 2, ... in
+  // list order
   s.sched_ok = true;
   for (const auto *lst : {&s.h_fwd_items, &s.h_bwd_items}) {
     const auto &lvl = lst == &s.h_fwd_items ? s.h_fwd_lvl : s.h_bwd_lvl;
@@ -253,11 +262,13 @@ void store_offsets(Ctx &c, Store &s, int dpn) {
     for (size_t L = 0; L + 1 < lvl.size(); ++L)
       for (int64_t t = lvl[L]; t < lvl[L + 1]; ++t) {
         const SolveItem &it = (*lst)[t];
-        if (it.q < 0 || it.q >= q || it.key != next[it.q]) s.sched_ok = false;
+        if (it.q < 0 || it.q >= q) s.sched_ok = false;
+        else if (it.key < 0) s.sched_ok = s.sched_ok && lst == &s.h_bwd_items && next[it.q] == 0;
+        else if (it.key != next[it.q]) s.sched_ok = false;
         else ++next[it.q];
       }
   }
-  s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po;
+  s.front_elems = fo; s.w_elems = wmax; s.rhs_elems = ro; s.piv_elems = po; s.part_elems = pa;
   s.cb_elems = plan_cb_arena(c.S, dpn, s.h_cb_off, &s.cb_sum);
 }
 
@@ -366,6 +377,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     s.yz = cv.take<double>(s.piv_elems);
     s.pub = cv.take<unsigned long long>(s.piv_elems);
     s.pflag = fp32 ? nullptr : cv.take<unsigned>(s.piv_elems);
+    s.bpart = s.part_elems > 0 ? cv.take<unsigned long long>((size_t)s.part_elems) : nullptr;
     s.fflag = cv.take<unsigned>(2 * s.piv_elems);  // panel-factored, then panel-rows-ready flags
     s.ctl = cv.take<unsigned>(16);
     {
@@ -388,6 +400,7 @@ size_t carve(Ctx &c, char *base, int stores, std::vector<Upload> *up) {
     st_up(p, s.h_w_off); s.w_off = p;
     st_up(p, s.h_rhs_off); s.rhs_off = p;
     st_up(p, s.h_piv_off); s.piv_off = p;
+    st_up(p, s.h_part_off); s.part_off = p;
   };
   store(c.kkt64, (stores & SGN_STORE_FP64) != 0, 2 * d, true, false);
   store(c.kkt32, (stores & SGN_STORE_MIXED) != 0, 2 * d, true, true);
@@ -597,6 +610,8 @@ sgn_status sgn_bind(sgn_t h, void *dev_buf, size_t bytes, int32_t stores, void *
     if (!st->enabled) continue;
     CUDA_TRY(h, cudaMemsetAsync(st->pub, 0, (size_t)st->piv_elems * sizeof(unsigned long long), h->stream));
     if (st->pflag) CUDA_TRY(h, cudaMemsetAsync(st->pflag, 0, (size_t)st->piv_elems * sizeof(unsigned), h->stream));
+    if (st->bpart)
+      CUDA_TRY(h, cudaMemsetAsync(st->bpart, 0, (size_t)st->part_elems * sizeof(unsigned long long), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(st->fflag, 0, 2 * (size_t)st->piv_elems * sizeof(unsigned), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(st->ctl, 0, 16 * sizeof(unsigned), h->stream));
   }

@@ -48,9 +48,37 @@ struct DevSym {
 
 // one band or block of a front in a level's substitution schedule: q indexes
 // the level-ordered front list, key orders the work inside the front
+// (backward: key < 0 is a part of an ancestor-row product, see bwd_parts)
 struct SolveItem {
   int32_t q, key;
 };
+
+// Backward substitution of an FP32 front with many ancestor (struct) rows:
+// the product of each 128-column block with those rows' solution values is
+// split into bwd_parts(rows) parts of bwd_part_rows(rows) rows (the last one
+// shorter), each computed by its own CTA and published for the block's CTA,
+// so that the rows stream on many SMs instead of one.  0: the block's CTA
+// computes the product itself.  Part h of block b has backward key
+// -1 - (b BWD_PARTS_MAX + h).
+constexpr int BWD_PARTS_MAX = 8;
+constexpr int BWD_PART_MIN_ROWS = 1024;
+#if defined(__CUDACC__)
+#define SGN_HD __host__ __device__
+#else
+#define SGN_HD
+#endif
+SGN_HD inline int bwd_part_rows(int64_t rows) {
+  int64_t h = (rows + BWD_PART_MIN_ROWS - 1) / BWD_PART_MIN_ROWS;
+  if (h > BWD_PARTS_MAX) h = BWD_PARTS_MAX;
+  const int64_t rp = (rows + h - 1) / h;
+  return (int)((rp + 127) / 128 * 128);
+}
+SGN_HD inline int bwd_parts(int64_t rows) {
+  if (rows <= BWD_PART_MIN_ROWS) return 0;
+  const int64_t rp = bwd_part_rows(rows);
+  return (int)((rows + rp - 1) / rp);
+}
+#undef SGN_HD
 
 // one CTA of an outer block's panel kernel: a 128-row band of front q (q
 // indexes the level-ordered front list)
@@ -97,6 +125,14 @@ struct Store {
   // block's first position); ctl = {solve counter, ticket, finished CTAs}
   unsigned long long *pub = nullptr;
   unsigned *pflag = nullptr, *ctl = nullptr;
+  // FP32 fronts: the published parts of the backward ancestor-row products,
+  // part h of front s's block at column k at bpart[part_off[s] + h ns + k + t]
+  // (value bits and tag in one 64-bit word, as in pub; only fronts whose
+  // product is split hold parts)
+  unsigned long long *bpart = nullptr;
+  const int64_t *part_off = nullptr;
+  std::vector<int64_t> h_part_off;
+  int64_t part_elems = 0;
   const SolveItem *fwd_items = nullptr, *bwd_items = nullptr;
   std::vector<SolveItem> h_fwd_items, h_bwd_items;
   std::vector<int64_t> h_fwd_lvl, h_bwd_lvl;  // per level: range in the item lists

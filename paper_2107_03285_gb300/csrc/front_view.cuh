@@ -20,6 +20,8 @@ struct SV {  // store view passed to kernels
   double *yz;                    // y, z = D^{-1} y, v of the substitutions (pivot order)
   unsigned long long *pub;       // published block values of the substitutions
   unsigned *pflag;               // their tags (FP64 fronts)
+  unsigned long long *bpart;     // published parts of the backward ancestor-row products (FP32)
+  const int64_t *part_off;       // each front's first part word in bpart
   unsigned *fflag;               // panel-factored flags of the factorization (epoch tags)
   unsigned *fpre;                // panel-rows-ready flags (epoch tags)
   const int64_t *front_off, *cb_off, *w_off, *rhs_off, *piv_off, *xinv_off;
@@ -37,6 +39,7 @@ inline SV view(Store &s, int parity = 0) {
   v.piv_type = s.piv_type; v.piv_perm = s.piv_perm;
   v.D0 = s.D0; v.D1 = s.D1; v.front_off = s.front_off; v.w_off = s.w_off; v.rhs_off = s.rhs_off;
   v.piv_off = s.piv_off; v.dpn = s.dpn; v.kkt = s.kkt ? 1 : 0;
+  v.bpart = s.bpart; v.part_off = s.part_off;
   return v;
 }
 

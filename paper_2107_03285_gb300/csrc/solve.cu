@@ -182,28 +182,36 @@ __device__ __forceinline__ void publish_block(const SV &sv, int64_t p, int w, un
 // w values to dst[0, w) (zeros up to SB); every thread calls it, and it ends
 // with a barrier.  False (DEV_TIMEOUT recorded) when the wait bound expires
 // or another CTA already gave up.
+// FP32 form of the wait: the w words at a[0, w), each a value's bits with
+// its tag, into dst[0, w) (zeros up to SB); thread t polls word t.  No
+// barrier.
+__device__ __forceinline__ void wait_words(const unsigned long long *a, int w, unsigned tag, float *dst,
+                                           int *status, int *abort) {
+  const int t = threadIdx.x;
+  if (t < w) {
+    unsigned long long v = ld_relaxed_u64(a + t);
+    if ((unsigned)(v >> 32) != tag) {
+      const long long t0 = clock64();
+      for (int n = 1; (unsigned)((v = ld_relaxed_u64(a + t)) >> 32) != tag; ++n) {
+        if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
+          atomicOr(status, DEV_TIMEOUT);
+          *abort = 1;
+          break;
+        }
+      }
+    }
+    dst[t] = __uint_as_float((unsigned)v);
+  } else if (t < SB) {
+    dst[t] = 0.f;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ bool wait_block(const SV &sv, int64_t p, int w, unsigned tag, T *dst, int *status,
                                            int *abort) {
   const int t = threadIdx.x;
   if constexpr (sizeof(T) == 4) {
-    if (t < w) {
-      const unsigned long long *a = sv.pub + p + t;
-      unsigned long long v = ld_relaxed_u64(a);
-      if ((unsigned)(v >> 32) != tag) {
-        const long long t0 = clock64();
-        for (int n = 1; (unsigned)((v = ld_relaxed_u64(a)) >> 32) != tag; ++n) {
-          if ((n & 255) == 0 && (timed_out(status) || clock64() - t0 > SOLVE_WAIT_CYCLES)) {
-            atomicOr(status, DEV_TIMEOUT);
-            *abort = 1;
-            break;
-          }
-        }
-      }
-      dst[t] = __uint_as_float((unsigned)v);
-    } else if (t < SB) {
-      dst[t] = 0.f;
-    }
+    wait_words(sv.pub + p, w, tag, dst, status, abort);
   } else {
     if (t == 0 && ld_acquire_u32(sv.pflag + p) != tag) {
       const long long t0 = clock64();
@@ -413,7 +421,20 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   // struct rows: the solution there (the ancestors') is final
   const int nown = d.sn_nown[s];
   const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
-  if (f - ns <= xcap) {
+  const int nparts = sizeof(T) == 4 ? bwd_parts(f - ns) : 0;
+  // the product's parts, published by their own CTAs (listed first)
+  for (int h = 0; h < nparts; ++h, ++ph) {
+    AT *x = sm.xs[ph & 1];
+    wait_words(sv.bpart + sv.part_off[s] + (int64_t)h * ns + k, w, tag, reinterpret_cast<float *>(x), status,
+               &sm.abort);
+    __syncthreads();
+    if (sm.abort) return;
+    if (lane == 0) {
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) kahan_add(sum[cc], comp[cc], x[c0 + cc]);
+    }
+  }
+  if (nparts == 0 && f - ns <= xcap) {
     // all of it gathered into shared memory once, then 128 rows a pass
     // without a barrier (the warps overlap)
     for (int idx = tid; idx < f - ns; idx += blockDim.x)
@@ -442,8 +463,9 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   }
   // otherwise gathered 128 rows a pass; the struct-rank index of the next
   // pass is read one pass ahead
-  int sidx = (f - ns > xcap && tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
-  for (int rs = ns; f - ns > xcap && rs < f; rs += SB, ++ph) {
+  const bool by_pass = nparts == 0 && f - ns > xcap;
+  int sidx = (by_pass && tid < SB && ns + tid < f) ? sr[(ns + tid) / dpn - nown] : 0;
+  for (int rs = ns; by_pass && rs < f; rs += SB, ++ph) {
     const int nrs = min(SB, f - rs);
     const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
     T q[8][4];
@@ -521,6 +543,73 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
   }
 }
 
+// one part of a backward block's ancestor-row product (FP32 fronts, key < 0):
+// rows [r0, r0 + rn) of the front's struct rows times their solution values,
+// for the block's w columns, gathered into shared memory xcap rows at a time;
+// published at bpart[part_off[s] + h ns + k + t] for the block's CTA
+template <typename T>
+__device__ __noinline__ void bwd_part(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
+                                         SolveItem itm, unsigned tag, const double *__restrict__ sol,
+                                         SolveShared<T> &sm, T *xall, int xcap) {
+  using AT = T;
+  const int s = lvl_fronts[itm.q];
+  const int dpn = sv.dpn;
+  const int ns = d.sn_nown[s] * dpn;
+  const int f = front_order(d, s, dpn);
+  const int j = -1 - itm.key, b = j / BWD_PARTS_MAX, h = j % BWD_PARTS_MAX;
+  const int k = b * SB, w = min(SB, ns - k);
+  const int rp = bwd_part_rows(f - ns);
+  const int r0 = h * rp, rn = min(rp, f - ns - r0);
+  const T *F = (const T *)sv.F + sv.front_off[s];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, c0 = 8 * warp;
+  const int nown = d.sn_nown[s];
+  const int32_t *sr = d.struct_ranks + d.sn_struct_off[s];
+  AT sum[8], comp[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) sum[cc] = comp[cc] = AT(0);
+  for (int g0 = 0; xcap > 0 && g0 < rn; g0 += xcap) {
+    const int gn = min(xcap, rn - g0);
+    if (g0 > 0) __syncthreads();  // the previous chunk's reads are done
+    for (int idx = tid; idx < gn; idx += blockDim.x) {
+      const int ii = ns + r0 + g0 + idx;
+      xall[idx] = (AT)sol[(int64_t)sr[ii / dpn - nown] * dpn + ii % dpn];
+    }
+    __syncthreads();
+    for (int rs = ns + r0 + g0; rs < ns + r0 + g0 + gn; rs += SB) {
+      const int nrs = min(SB, ns + r0 + g0 + gn - rs);
+      const T *Fc = F + (int64_t)(k + c0) * f + rs + lane;
+      T q[8][4];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          q[cc][m] = (c0 + cc < w && lane + 32 * m < nrs) ? Fc[(int64_t)cc * f + 32 * m] : T(0);
+      AT xv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        xv[m] = lane + 32 * m < nrs ? xall[rs - (ns + r0 + g0) + lane + 32 * m] : AT(0);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        AT a = AT(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) a += (AT)q[cc][m] * xv[m];
+        kahan_add(sum[cc], comp[cc], a);
+      }
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    AT t = sum[cc] - comp[cc];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sm.dp[0][c0 + cc] = t;
+  }
+  __syncthreads();
+  if (tid < w)
+    st_relaxed_u64(sv.bpart + sv.part_off[s] + (int64_t)h * ns + k + tid,
+                   ((unsigned long long)tag << 32) | __float_as_uint((float)sm.dp[0][tid]));
+}
+
 // dynamic shared memory: the block inverse (SB x (SB + 1)), then xcap
 // solution values of the ancestor (struct) rows (0: gathered pass by pass)
 template <typename T>
@@ -531,8 +620,17 @@ __global__ void __launch_bounds__(SBT, sizeof(T) == 4 ? 2 : 1)
   __shared__ SolveShared<T> sm;
   if (solve_item_begin(ctl, status, sm)) {
     const unsigned tag = 2u * *(volatile unsigned *)ctl + 1u;
-    bwd_item<T>(d, sv, lvl_fronts, items[sm.item], nb, tag, status, sol, reinterpret_cast<T(*)[SB + 1]>(blk_raw),
-                sm, reinterpret_cast<T *>(blk_raw) + SB * (SB + 1), xcap);
+    const SolveItem itm = items[sm.item];
+    bool part = false;
+    if constexpr (sizeof(T) == 4) {
+      if (itm.key < 0) {
+        bwd_part<T>(d, sv, lvl_fronts, itm, tag, sol, sm, reinterpret_cast<T *>(blk_raw) + SB * (SB + 1), xcap);
+        part = true;
+      }
+    }
+    if (!part)
+      bwd_item<T>(d, sv, lvl_fronts, itm, nb, tag, status, sol, reinterpret_cast<T(*)[SB + 1]>(blk_raw), sm,
+                  reinterpret_cast<T *>(blk_raw) + SB * (SB + 1), xcap);
   }
   solve_item_end(ctl);
 }
@@ -568,9 +666,15 @@ void solve_impl(Ctx &c, Store &st, const double *b, double *x) {
   for (int L = c.S.n_levels - 1; L >= 0; --L) {
     const int64_t t0 = st.h_bwd_lvl[L], nt = st.h_bwd_lvl[L + 1] - t0;
     if (nt == 0) continue;
-    int xs = 0;  // the level's most ancestor rows of a front
-    for (int s : c.S.level_fronts[L]) xs = std::max(xs, c.S.sn[s].nstruct * dpn);
-    const int xcap = xs <= bwd_xcap_max<T>() ? xs : 0;
+    // the most ancestor rows one CTA of the level gathers (a front's, or a
+    // part's where the product is split); FP64 fronts beyond the shared
+    // memory cap gather them 128 a pass (0)
+    int xs = 0;
+    for (int s : c.S.level_fronts[L]) {
+      const int r = c.S.sn[s].nstruct * dpn;
+      xs = std::max(xs, sizeof(T) == 4 && bwd_parts(r) > 0 ? bwd_part_rows(r) : r);
+    }
+    const int xcap = sizeof(T) == 4 ? std::min(xs, bwd_xcap_max<T>()) : (xs <= bwd_xcap_max<T>() ? xs : 0);
     k_bwd_level<T><<<(unsigned)nt, SBT, blk_smem + (size_t)xcap * sizeof(T), c.stream>>>(
         c.ds, sv, c.ds.lvl_fronts, st.bwd_items + t0, nb, st.ctl, c.status, x, xcap);
     c.count();
