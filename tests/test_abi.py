@@ -107,12 +107,14 @@ def test_calls_before_bind_are_rejected(B):
     lib.sgn_destroy(h)
 
 
-@pytest.mark.parametrize("which", ["kuhn3d_9", "batch2d_12"])
+@pytest.mark.parametrize("which", ["kuhn3d_9", "batch2d_12", "kuhn3d_16"])
 def test_contribution_block_arena_plan_is_consistent(B, which):
     """sgn_device_bytes replays the contribution-block lifetimes and fails if
     two live blocks would share memory, and checks that every substitution
-    schedule lists each front's items after the items they wait on; the
-    arena must also need less than keeping every front whole."""
+    schedule lists each front's items after the items they wait on (on the
+    16^3 cube also the parts of split backward ancestor-row products: fronts
+    below the root have 1,536 ancestor rows); the arena must also need less
+    than keeping every front whole."""
     from sgn_inputs import make_preset
     prob = make_preset(which)
     lib, code, h, keep = _setup(B, prob)
