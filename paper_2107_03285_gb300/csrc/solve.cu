@@ -549,8 +549,8 @@ __device__ __forceinline__ void bwd_item(const DevSym &d, const SV &sv, const in
 // published at bpart[part_off[s] + h ns + k + t] for the block's CTA
 template <typename T>
 __device__ __noinline__ void bwd_part(const DevSym &d, const SV &sv, const int32_t *__restrict__ lvl_fronts,
-                                         SolveItem itm, unsigned tag, const double *__restrict__ sol,
-                                         SolveShared<T> &sm, T *xall, int xcap) {
+                                      SolveItem itm, unsigned tag, const double *__restrict__ sol,
+                                      SolveShared<T> &sm, T *xall, int xcap) {
   using AT = T;
   const int s = lvl_fronts[itm.q];
   const int dpn = sv.dpn;
