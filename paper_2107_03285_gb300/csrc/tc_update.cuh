@@ -184,7 +184,7 @@ __host__ __device__ __forceinline__ int window_units(int m, int n, bool pair) {
   return tri + (n - m) * ((m + 1) / 2);
 }
 
-__device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
+__host__ __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
   bi = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);  // corrected below
   while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
   while (bi * (bi + 1) / 2 > tile) --bi;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void tile_coords(int tile, int &bi, int &bj) {
 // unit t of a job's window, row-major: the window's triangle first, then its
 // rows below.  (bi, bj) is the unit's first tile (absolute tile coordinates,
 // bi >= bj); two = the unit also holds tile (bi, bj + 1)
-__device__ __forceinline__ void window_unit(const TileJob &job, int t, int &bi, int &bj, bool &two) {
+__host__ __device__ __forceinline__ void window_unit(const TileJob &job, int t, int &bi, int &bj, bool &two) {
   int r, c;
   if (!job.pair) {
     const int t0 = job.m * (job.m + 1) / 2;
