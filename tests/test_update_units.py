@@ -4,7 +4,9 @@ The update kernel walks one flat list of units per launch: single 128 x 128
 tiles for the next outer block's columns, pairs of tiles of one tile row
 (128 x 256, sharing the W operand) elsewhere.  tests/units_check.cu compiles
 the enumeration the kernel uses (tc_update.cuh) into a host program that
-checks every window shape covers each tile of its lower part exactly once.
+checks every window shape covers each tile of its lower part exactly once,
+and that the backward substitution's split of an ancestor-row product into
+parts covers every row with at most BWD_PARTS_MAX non-empty parts.
 """
 import os
 import shutil

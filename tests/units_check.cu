@@ -3,10 +3,14 @@
 // single tiles and in tile pairs, the units cover each tile of the window's
 // lower part (rows >= columns in its m x m triangle, all m columns below)
 // exactly once, a pair's second tile lies in the same tile row next to the
-// first, and the unit count equals the closed form the set-up uses.
+// first, and the unit count equals the closed form the set-up uses.  Also
+// the split of a backward block's ancestor-row product (bwd_parts,
+// bwd_part_rows): at most BWD_PARTS_MAX parts of 128-row multiples, none
+// empty, together covering every ancestor row.
 #include <cstdio>
 #include <vector>
 
+#include "../paper_2107_03285_gb300/csrc/common.cuh"
 #include "../paper_2107_03285_gb300/csrc/tc_update.cuh"
 
 int main() {
@@ -40,6 +44,16 @@ int main() {
           for (int c = 0; c < m; ++c)
             if (hits[(size_t)r * m + c] != (c <= r ? 1 : 0)) ++bad;
       }
+  for (int64_t rows = 0; rows <= 200000; rows += rows < 20000 ? 1 : 97) {
+    const int h = sgn::bwd_parts(rows);
+    if (rows <= sgn::BWD_PART_MIN_ROWS) {
+      if (h != 0) ++bad;
+      continue;
+    }
+    const int64_t rp = sgn::bwd_part_rows(rows);
+    if (h < 1 || h > sgn::BWD_PARTS_MAX || rp % 128 != 0 || (int64_t)(h - 1) * rp >= rows || (int64_t)h * rp < rows)
+      ++bad;
+  }
   std::printf("%s %d\n", bad ? "FAIL" : "ok", bad);
   return bad ? 1 : 0;
 }
