@@ -2,9 +2,10 @@
 //     C[kend:, kend:] -= W L^T      (lower triangle, FP32 fronts)
 // where W = L21 D and L = L21 of one outer block (inner dimension <= 256).
 //
-// Each CTA owns one 128-row output unit: one 128 x 128 tile, or two tiles of
-// the same tile row side by side (128 x 256, one N = 256 MMA), which share
-// the W operand and so cut the operand bytes per output entry by a quarter.
+// The output is cut into 128-row units, each accumulated by one CTA: one
+// 128 x 128 tile, or two tiles of the same tile row side by side (128 x 256,
+// one N = 256 MMA), which share the W operand and so cut the operand bytes
+// per output entry by a quarter.
 // W and L are kept in K-major global arrays split as x = hi + lo with hi = x
 // with its low 13 mantissa bits cleared (exactly representable in TF32) and
 // lo = x - hi; the unit is accumulated in TMEM (FP32) as
